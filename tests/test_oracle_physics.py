@@ -1,0 +1,191 @@
+"""Pins of the whole oracle time step: invariants, a textbook special case,
+Galilean invariance of the viscosity, and the thermodynamics the paper
+predicts (coexistence densities, interface thickness, Laplace's law)."""
+import numpy as np
+import pytest
+
+from oracle import params as op
+from oracle import thermo
+from paper_1809_02390_gb300 import inputs
+
+RNG = np.random.default_rng(7)
+
+
+def test_rest_state_is_a_fixed_point(orc):
+    p = op.from_physical()
+    f0 = orc.init_feq(p, np.full((12, 16), p.rho_l))
+    f = orc.step(p, f0, 1000)
+    assert np.abs(f - f0).max() <= 2e-14 * np.abs(f0).max()
+
+
+def test_mass_and_momentum_conservation(orc):
+    """Collision rows 0, 3, 5 act on zero and the pairwise force sums to zero on a
+    periodic lattice, so total mass and total momentum are invariants."""
+    p = op.from_physical()
+    rho = inputs.droplet(32, 24, 7, 5, p.rho_g, p.rho_l, center=(14.3, 11.1))
+    f = orc.init_eq(p, rho, RNG.uniform(-0.02, 0.02, rho.shape), RNG.uniform(-0.02, 0.02, rho.shape))
+    ex, ey = orc.velocities()
+    mass0 = f.sum()
+    jx0, jy0 = np.tensordot(ex, f, 1).sum(), np.tensordot(ey, f, 1).sum()
+    f = orc.step(p, f, 400)
+    assert abs(f.sum() - mass0) <= 1e-13 * mass0
+    assert abs(np.tensordot(ex, f, 1).sum() - jx0) <= 1e-12 * mass0
+    assert abs(np.tensordot(ey, f, 1).sum() - jy0) <= 1e-12 * mass0
+    assert abs(jx0) > 1e-3  # the check is not vacuous
+
+
+def test_classical_limit_is_bgk_with_product_equilibrium(orc):
+    """varpi = 1 with eta = 0 (ideal gas), no interaction force, the plain collision
+    (Eq. 2) and equal relaxation rates: the model reduces to D2Q9 BGK with the
+    product-form equilibrium (main text after Eq. 9).  BGK written out here."""
+    om = 1.3
+    p = dict(eos=2, form=2, eos_a=0.0, eos_b=0.0, R_gas=1.0, T=1.0, lam=1.0, G2=0.0, varpi=1.0,
+             s0=om, se=om, seps=om, sj=om, sq=om, sp=om)
+    ny, nx = 10, 12
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    f = (np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+         * (1 + 0.1 * RNG.uniform(-1, 1, (9, ny, nx))))
+
+    def w(c, u):
+        return np.where(c == 0, 2 / 3 - u * u, (1 + 3 * c * u + 3 * u * u) / 6)
+
+    ref = f.copy()
+    for _ in range(25):
+        g = np.stack([np.roll(np.roll(ref[i], ey[i], 0), ex[i], 1) for i in range(9)])  # pull
+        rho = g.sum(0)
+        ux, uy = np.tensordot(ex, g, 1) / rho, np.tensordot(ey, g, 1) / rho
+        feq = np.stack([rho * w(ex[i], ux) * w(ey[i], uy) for i in range(9)])
+        ref = g - om * (g - feq)
+    out = orc.step(p, f, 25)
+    assert np.abs(out - ref).max() < 1e-13
+
+
+def _shear_viscosity(orc, p, U, direction, L=32, amp=1e-3, n=200):
+    """Decay rate of a small shear wave on a background flow U (lattice units)."""
+    k = 2 * np.pi / L
+    if direction == "x":      # wave vector along x, background along x
+        ny, nx = 2, L
+        x = np.arange(nx)[None, :] * np.ones((ny, 1))
+        ux, uy = np.full((ny, nx), U), amp * np.sin(k * x)
+        pick = lambda vx, vy: vy
+    elif direction == "xperp":  # wave vector along x, background along y
+        ny, nx = 2, L
+        x = np.arange(nx)[None, :] * np.ones((ny, 1))
+        ux, uy = np.zeros((ny, nx)), U + amp * np.sin(k * x)
+        pick = lambda vx, vy: vy - U
+    else:                     # diagonal wave on an L x L lattice, background along the wave vector
+        ny = nx = L
+        y, x = np.mgrid[0:ny, 0:nx]
+        ph = k * (x + y)
+        ux = U / np.sqrt(2) + amp * np.sin(ph) / np.sqrt(2)
+        uy = U / np.sqrt(2) - amp * np.sin(ph) / np.sqrt(2)
+        k = k * np.sqrt(2)
+        pick = lambda vx, vy: (vx - vy) / np.sqrt(2)
+    y, x = np.mgrid[0:ny, 0:nx]
+    phase = np.exp(-2j * np.pi * (x + (y if direction == "diag" else 0)) / L)
+    f = orc.init_eq(p, np.full((ny, nx), p.rho_l), ux, uy)
+
+    def amp_of(f):
+        _, vx, vy = orc.macro(p, f)
+        return abs(np.sum(pick(vx, vy) * phase))
+
+    f = orc.step(p, f, 20)
+    a1 = amp_of(f)
+    f = orc.step(p, f, n)
+    return -np.log(amp_of(f) / a1) / (k * k * n)
+
+
+@pytest.mark.parametrize("direction", ["x", "xperp", "diag"])
+def test_galilean_invariance_of_shear_viscosity(orc, direction):
+    """With the non-diagonal S and the cubic correction R, T, X (Eq. 10), the shear
+    viscosity of the self-tuning-EOS fluid (eta != 0) does not depend on the
+    background velocity to O(Ma^4) (supplement Eqs. 42-44); without them
+    (Eq. 2 alone) it shifts by ~6 b U^2.  This is the pin for R."""
+    p13 = op.from_physical(Tr=0.85, form=13)
+    p2 = op.from_physical(Tr=0.85, form=2)
+    U = 0.06 if direction != "diag" else 0.05
+    nu0 = _shear_viscosity(orc, p13, 0.0, direction)
+    nu13 = _shear_viscosity(orc, p13, U, direction)
+    nu2 = _shear_viscosity(orc, p2, U, direction)
+    assert abs(nu13 / nu0 - 1) < 2e-3
+    assert abs(nu2 / nu0 - 1) > 5 * abs(nu13 / nu0 - 1) and abs(nu2 / nu0 - 1) > 5e-3
+    # Kinematic viscosity of Eq. 9: nu = c_s^2 (1/s_p - 1/2) (finite-k correction < 1%).
+    assert nu0 == pytest.approx((1 / p13.sp - 0.5) / 3, rel=1e-2)
+
+
+@pytest.mark.parametrize("Tr,W,tol_g", [(0.8, 5.0, 5e-3), (0.9, 5.0, 5e-3), (0.7, 8.0, 1e-2)])
+def test_flat_interface_coexistence_matches_maxwell(orc, Tr, W, tol_g):
+    """Supplement Sec. V / main-text Fig. 1: the flat-interface coexistence densities
+    follow the Maxwell construction of the prescribed EOS (vdW here)."""
+    e = thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, Tr)
+    K_int = W / thermo.interface(e, 1.0)["W"]
+    p = op.from_physical(Tr=Tr, K_int=K_int)
+    f = orc.init_feq(p, inputs.slab(128, 2, 64, W, p.rho_g, p.rho_l))
+    f = orc.step(p, f, 8000)
+    rho, ux, _ = orc.macro(p, f)
+    assert rho[0, 0] == pytest.approx(p.rho_g, rel=tol_g)
+    assert rho[0, 64] == pytest.approx(p.rho_l, rel=2e-3)
+    assert np.abs(ux).max() < 5e-4
+
+
+def _thickness(profile, rg, rl):
+    """Distance between the 5% and 95% levels of one interface (linear interpolation)."""
+    lo, hi = 0.95 * rg + 0.05 * rl, 0.05 * rg + 0.95 * rl
+
+    def cross(level):
+        i = np.nonzero((profile[:-1] < level) & (profile[1:] >= level))[0][0]
+        return i + (level - profile[i]) / (profile[i + 1] - profile[i])
+
+    return cross(hi) - cross(lo)
+
+
+def test_interface_thickness_matches_pressure_tensor(orc):
+    """W of a simulated flat interface against the pressure-tensor prediction
+    (Eq. 23 / supplement Fig. 1: agreement within ~0.5%).  K_INT = 2 gives W = 10,
+    wide enough that linear interpolation of the 5%/95% crossings is accurate."""
+    p = op.from_physical(Tr=0.85, K_int=2.0)
+    W = thermo.interface(thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, 0.85), 2.0)["W"]
+    f = orc.init_feq(p, inputs.slab(160, 2, 80, W, p.rho_g, p.rho_l))
+    f = orc.step(p, f, 8000)
+    rho = orc.macro(p, f)[0][0]
+    rg, rl = rho[0], rho[80]
+    assert _thickness(rho[:80], rg, rl) == pytest.approx(W, rel=1e-2)
+
+
+def test_laplace_law(orc):
+    """Laplace's law dp = sigma / R with sigma from the pressure tensor (Eq. 17):
+    a droplet of radius 12 (64 x 64, W = 5) relaxed for 4,000 steps; pressures
+    from p_EOS at the centre and the far field, R from the area above the mid
+    density (supplement Sec. V).  Converged to 1% (curvature corrections at R/W ~ 2.4)."""
+    p = op.from_physical(Tr=0.85, K_int=1.0)
+    e = thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, 0.85)
+    sigma = thermo.interface(e, 1.0)["sigma"] * p.lam   # lattice units (p / c^2)
+    f = orc.init_feq(p, inputs.droplet(64, 64, 12.0, 5.0, p.rho_g, p.rho_l))
+    f = orc.step(p, f, 4000)
+    rho = orc.macro(p, f)[0]
+    dp = orc.eos(p, rho[32, 32])[0] - orc.eos(p, rho[0, 0])[0]
+    radius = np.sqrt((rho > 0.5 * (p.rho_g + p.rho_l)).sum() / np.pi)
+    assert dp * radius == pytest.approx(sigma, rel=2e-2)
+
+
+def test_complex_step_matches_finite_differences(orc):
+    """The complex-step variant of the oracle step agrees with central differences
+    (for the state and for the parameters T, G2, lam)."""
+    p = op.from_physical()
+    rho = inputs.droplet(12, 10, 3.5, 3, p.rho_g, p.rho_l)
+    f = orc.init_eq(p, rho, 0.01 * RNG.uniform(-1, 1, rho.shape), 0.0)
+    v = RNG.standard_normal(f.shape) * 1e-2
+    th = np.array([0.3, 0.2, 0.1])
+    h = 1e-20
+    _, im = orc.step_cs(p, f, h * v, h * th, nsteps=3)
+    jvp = im / h
+    eps = 1e-6
+    pp, pm = p.as_dict(), p.as_dict()
+    for key, d in zip(("T", "G2", "lam"), th):
+        pp[key] += eps * d
+        pm[key] -= eps * d
+    fd = (orc.step(pp, f + eps * v, 3) - orc.step(pm, f - eps * v, 3)) / (2 * eps)
+    assert np.abs(jvp - fd).max() < 1e-7 * np.abs(jvp).max()
+    re, _ = orc.step_cs(p, f, None, (0, 0, 0), nsteps=3)
+    assert np.array_equal(re, orc.step(p, f, 3))
