@@ -1,0 +1,170 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) implementation of the per-node time step
+ * of the multiphase lattice Boltzmann model with self-tuning equation of state
+ * (R. Huang, H. Wu, N. A. Adams, "Lattice Boltzmann model with self-tuning
+ * equation of state for multiphase flows", arXiv:1809.02390).
+ *
+ * One time step on a periodic D2Q9 lattice (delta_x = 1) is: pull streaming
+ * f_i(x) = fbar_i(x - e_i) (supplement Eq. 2), density rho = sum_i f_i,
+ * the pairwise interaction force F = G^2 rho sum_i omega_i rho(x + e_i) e_i
+ * (Eq. 12), and the collision of Eq. 13 in moment space (moment transform
+ * of supplement Eq. 4, equilibrium of Eq. 3 with the self-tuning eta, forcing
+ * of Eq. 4, non-diagonal collision matrix of Eq. 6, cubic-velocity correction
+ * of Eq. 10-11 and the eps^3 term S Q_m of Eq. 14), executed in the sequence
+ * of supplement Sec. IV, followed by the inverse transform.
+ *
+ * Units.  The library runs with lattice speed c = 1: pressures are carried as
+ * p / c^2 and the interaction strength as G2 = G^2 / c^2 (the model is
+ * invariant under this rescaling).  The physical -> lattice derivation follows
+ * Eqs. 21-22 (G = K_INT sqrt(2 K_EOS a), c_s = K_INT sqrt(d(p_EOS + K_EOS a rho^2)/drho)
+ * at rho_l, c = sqrt(3) c_s) unless the caller gives `lam` / `G2` directly.
+ *
+ * Memory.  The caller owns every buffer: the library never allocates device
+ * memory for the lattice and never frees caller memory.  Populations are stored
+ * structure-of-arrays, f[i][y][x], i = 0..8 in the velocity order of
+ * supplement Eq. 3 (rest, +x, +y, -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1)),
+ * x fastest, no padding, as the deviation fbar_i - w_i rho_ref from the rest
+ * state (w = 4/9, 1/9 x4, 1/36 x4; rho_ref = 0 stores plain populations).
+ * Element type: double (LB_FP64), float (LB_FP32) or IEEE half (LB_FP16S).
+ * The stored state is always post-collision (after the last completed step).
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void*; every call enqueues
+ * its kernels on it and returns without synchronising (except where stated).
+ *
+ * Errors.  Every int-returning call returns LB_OK (0) or a negative code;
+ * lb_last_error() gives a message.  Invalid parameters never reach the GPU.
+ * There is no CPU fallback: without a CUDA device the calls fail with LB_ECUDA.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_OK 0
+#define LB_EINVAL (-1)     /* invalid argument or parameter */
+#define LB_ECUDA (-2)      /* CUDA runtime error (message has the CUDA error string) */
+#define LB_ENOMEM (-3)     /* caller-provided scratch too small */
+#define LB_ENONFINITE (-4) /* non-finite density found by lb_status / lb_reduce */
+#define LB_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define LB_ENOTSUP (-6)    /* combination not supported */
+
+enum lb_precision { LB_FP64 = 0, LB_FP32 = 1, LB_FP16S = 2 };
+enum lb_eos_kind { LB_EOS_VDW = 0, LB_EOS_CS = 1 };
+enum lb_variant { LB_AUTO = 0, LB_FUSED = 1, LB_TWO_PASS = 2 };
+
+/* Problem statement (main text Eqs. 6, 7, 16, 20-22; supplement Sec. V). */
+typedef struct lb_params {
+  int32_t nx, ny;    /* periodic lattice size, each >= 3 */
+  int32_t precision; /* enum lb_precision: storage type; FP16S computes in FP32 */
+  int32_t eos;       /* enum lb_eos_kind: van der Waals p = rho R T/(1 - b rho) - a rho^2,
+                        or Carnahan-Starling (Eq. 20); both times K_EOS */
+  int32_t variant;   /* enum lb_variant: fused single-kernel step or density pass + collision */
+  int32_t reserved0;
+  double eos_a, eos_b, R_gas; /* EOS constants a, b, R (> 0) */
+  double Tr;                  /* reduced temperature T/Tc, in (0, 1) for two phases */
+  double K_eos, K_int;        /* scaling factors of Eqs. 20-22 (> 0) */
+  double G2;    /* > 0: interaction strength G^2/c^2 given directly; <= 0: Eq. 21-22 */
+  double lam;   /* > 0: pressure scale K_EOS/c^2 given directly; <= 0: c_s rule of Eq. 22 */
+  double varpi; /* bulk-viscosity coefficient of Eq. 7; 0 selects the paper's 1/6;
+                   1 and 1/3 are singular (main text after Eq. 9) and rejected */
+  double s_p;   /* shear relaxation rate, in (0, 2) (relaxation time tau = 1/s_p) */
+  double s_q, s_e, s_eps; /* <= 0: s_q and s_e from tau_p tau_q = (k+1) tau_e tau_q = 1/12
+                             (Eq. 16), s_eps = s_e; otherwise in (0, 2) */
+  double s_0, s_j;        /* rates of the conserved moments (act on zero); <= 0 selects 1 */
+  double rho_ref;         /* storage shift: populations stored as fbar_i - w_i rho_ref */
+} lb_params;
+
+/* Derived lattice-unit quantities (all FP64, computed on the host). */
+typedef struct lb_derived {
+  double Tc, T;          /* critical and actual temperature */
+  double rho_g, rho_l;   /* Maxwell-construction coexistence densities of p_EOS */
+  double p_star;         /* coexistence pressure (physical units, with K_EOS) */
+  double lam, G2;        /* lattice pressure scale K_EOS/c^2 and G^2/c^2 in use */
+  double c2;             /* c^2 = 3 c_s^2 of Eq. 22 (physical lattice speed squared) */
+  double s_0, s_e, s_eps, s_j, s_q, s_p; /* relaxation rates in use */
+  double k, h, b, beta2; /* coefficients of Eq. 7 with alpha_1 = -1, beta_1 = 1 */
+  double W1, sigma1;     /* flat-interface thickness and surface tension predicted by the
+                            pressure tensor (Eq. 17) at K_INT = 1, physical units */
+} lb_derived;
+
+typedef struct lb_handle lb_handle;
+
+/* Version of this ABI (incremented on incompatible change). */
+int lb_abi_version(void);
+
+/* Derives the lattice-unit parameters of `p` on the host (FP64, no GPU use):
+ * Maxwell construction for rho_g, rho_l (from the closed-form free energy
+ * psi with p_EOS = rho psi' - psi, below Eq. 19), Eq. 21-22 for G2 and lam,
+ * Eq. 16 for the rates, Eq. 7 for k, h, b, beta_2, and the pressure-tensor
+ * interface thickness W1 and surface tension sigma1 (Eq. 17, 23) at K_INT = 1.
+ * Returns LB_EINVAL for invalid parameters (message in lb_last_error(NULL)). */
+int lb_derive(const lb_params* p, lb_derived* out);
+
+/* Bytes of one population buffer: 9 * nx * ny * element size. */
+size_t lb_state_bytes(const lb_params* p);
+
+/* Bytes of device scratch memory the step needs (0 for the fused variant, one
+ * density plane for the two-pass variant) plus the reduction workspace. */
+size_t lb_scratch_bytes(const lb_params* p);
+
+/* Creates a handle bound to the caller's buffers and stream and initialises the
+ * lattice at rest: fbar_i = (M^-1 m_eq(rho0, u = 0))_i - w_i rho_ref, with eta
+ * from the EOS at rho0 (the stated initial condition; the paper does not give
+ * one).  f_a, f_b: device buffers of lb_state_bytes() each (ping-pong; f_a holds
+ * the state after init).  scratch: device buffer of lb_scratch_bytes() bytes,
+ * or NULL when that is 0.  rho0: nx*ny doubles, row-major [y][x], on the host
+ * (rho0_on_device = 0; copied through f_b, synchronously) or the device (1).
+ * The handle keeps the pointers; the caller keeps ownership and must keep the
+ * buffers alive until lb_free.  Fails with LB_EINVAL for bad parameters or
+ * non-positive densities on the host path, LB_ENOMEM for a short scratch. */
+int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scratch,
+            size_t scratch_bytes, const double* rho0, int rho0_on_device, void* stream);
+
+/* Advances nsteps >= 0 time steps (Eq. 13 + supplement Eq. 2) on the stream. */
+int lb_step(lb_handle* h, int64_t nsteps);
+
+/* Device pointer of the buffer holding the current state. */
+void* lb_state(lb_handle* h);
+
+/* Number of steps taken since lb_init. */
+int64_t lb_steps_done(const lb_handle* h);
+
+/* Macroscopic fields at the time level of the last collision (Eq. 5): the
+ * collision conserves mass and adds F to the momentum, so
+ * rho = sum_i fbar_i and rho u = sum_i e_i fbar_i - F/2.  rho, ux, uy: device
+ * arrays of nx*ny elements ([y][x]), double for LB_FP64, float otherwise; ux and
+ * uy may be NULL. */
+int lb_moments(lb_handle* h, void* rho, void* ux, void* uy);
+
+/* FP64 reductions of the current state, synchronous (waits on the stream):
+ * out[0] = total mass, out[1..2] = total momentum sum_x rho u,
+ * out[3] = p_EOS/c^2 at the lattice centre (nx/2, ny/2), out[4] = p_EOS/c^2 at
+ * node (0, 0), out[5] = number of nodes with rho > (rho_g + rho_l)/2,
+ * out[6] = min rho, out[7] = max rho.  Returns LB_ENONFINITE if any density is
+ * not finite (the values are still written). */
+int lb_reduce(lb_handle* h, double out[8]);
+
+/* Copies the current state to / from a caller device buffer of lb_state_bytes(). */
+int lb_get_state(lb_handle* h, void* dst);
+int lb_set_state(lb_handle* h, const void* src);
+
+/* Derived parameters in use by the handle. */
+int lb_get_derived(const lb_handle* h, lb_derived* out);
+
+/* Message of the last error on this handle (h = NULL: of the last failed
+ * lb_derive / lb_init on this thread).  Never NULL. */
+const char* lb_last_error(const lb_handle* h);
+
+/* Releases the handle (not the caller's buffers). */
+void lb_free(lb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H_ */

@@ -1,0 +1,128 @@
+"""GB300-native (sm_103a) multiphase lattice Boltzmann with self-tuning EOS.
+
+Implements the per-node time step of Huang, Wu & Adams, "Lattice Boltzmann
+model with self-tuning equation of state for multiphase flows"
+(arXiv:1809.02390) as hand-written CUDA behind the C ABI of include/lbm.h.
+PyTorch only provides device memory and streams.
+
+    lat = Lattice(rho0, precision="fp32", Tr=0.85)
+    lat.step(1000)
+    rho, ux, uy = lat.moments()
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import capi
+from .capi import LB_FP16S, LB_FP32, LB_FP64, LB_FUSED, LB_TWO_PASS, LBError  # noqa: F401
+
+PRECISIONS = {"fp64": capi.LB_FP64, "fp32": capi.LB_FP32, "fp16s": capi.LB_FP16S}
+VARIANTS = {"fused": capi.LB_FUSED, "two_pass": capi.LB_TWO_PASS}
+EOS = {"vdw": capi.LB_EOS_VDW, "cs": capi.LB_EOS_CS}
+# Rest-state weights w_i of the storage shift, in the velocity order of the ABI.
+W_REST = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+    return torch
+
+
+def derive(nx: int = 64, ny: int = 64, **kw) -> dict:
+    """Host-side derived parameters (lb_derive): coexistence densities, lattice
+    pressure scale, G^2/c^2, relaxation rates, pressure-tensor W1 and sigma1."""
+    return capi.lb_derive(params(nx, ny, **kw))
+
+
+def params(nx: int, ny: int, precision: str = "fp32", eos: str = "vdw", variant: str = "fused",
+           **kw) -> capi.lb_params:
+    return capi.make_params(nx, ny, precision=PRECISIONS[precision], eos=EOS[eos], variant=VARIANTS[variant],
+                            **kw)
+
+
+class Lattice:
+    """One periodic lattice on the current CUDA device and stream.
+
+    rho0: initial density [ny, nx] (numpy array on the host, or a float64 CUDA
+    tensor).  Keyword arguments are the fields of ``lb_params`` (Tr, K_int,
+    s_p, rho_ref, ...).  ``rho_ref=None`` stores deviations from the rest state
+    at the mean initial density for reduced-precision storage."""
+
+    def __init__(self, rho0, precision: str = "fp32", eos: str = "vdw", variant: str = "fused",
+                 rho_ref: float | None = None, stream=None, **kw):
+        torch = _torch()
+        if isinstance(rho0, np.ndarray):
+            rho_host = np.ascontiguousarray(rho0, dtype=np.float64)
+            ny, nx = rho_host.shape
+            rho_t = torch.from_numpy(rho_host).pin_memory()
+            on_device = False
+        else:
+            rho_t = rho0.to(dtype=torch.float64).contiguous()
+            ny, nx = rho_t.shape
+            on_device = rho_t.is_cuda
+            if not on_device:
+                rho_t = rho_t.pin_memory()
+        if rho_ref is None:
+            rho_ref = 0.0 if precision == "fp64" else float(rho_t.double().mean())
+        if precision != "fp64":
+            rho_ref = float(np.float32(rho_ref))  # the library stores the shift in float
+        self.p = params(nx, ny, precision=precision, eos=eos, variant=variant, rho_ref=rho_ref, **kw)
+        self.nx, self.ny, self.precision = nx, ny, precision
+        self.rho_ref = rho_ref
+        self.dtype = {"fp64": torch.float64, "fp32": torch.float32, "fp16s": torch.float16}[precision]
+        self.real = torch.float64 if precision == "fp64" else torch.float32
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.f_a = torch.empty((9, ny, nx), dtype=self.dtype, device=dev)
+        self.f_b = torch.empty((9, ny, nx), dtype=self.dtype, device=dev)
+        nscr = capi.lb_scratch_bytes(self.p)
+        self.scratch = torch.empty(nscr, dtype=torch.uint8, device=dev)
+        self._rho0_keep = rho_t
+        self.h = capi.lb_init(self.p, self.f_a.data_ptr(), self.f_b.data_ptr(), self.scratch.data_ptr(), nscr,
+                              rho_t.data_ptr(), on_device, self.stream.cuda_stream)
+        self.derived = capi.lb_get_derived(self.h)
+
+    def step(self, nsteps: int = 1) -> None:
+        capi.lb_step(self.h, nsteps)
+
+    @property
+    def steps_done(self) -> int:
+        return capi.lb_steps_done(self.h)
+
+    def state(self):
+        """The current (post-collision) state buffer, stored as deviations f_i - w_i rho_ref."""
+        return self.f_a if capi.lb_state(self.h) == self.f_a.data_ptr() else self.f_b
+
+    def populations(self):
+        """Post-collision populations in FP64 (storage shift added back)."""
+        torch = _torch()
+        w = torch.tensor(W_REST, dtype=torch.float64, device=self.f_a.device)
+        return self.state().double() + self.rho_ref * w[:, None, None]
+
+    def moments(self, velocity: bool = True):
+        torch = _torch()
+        rho = torch.empty((self.ny, self.nx), dtype=self.real, device=self.f_a.device)
+        ux = torch.empty_like(rho) if velocity else None
+        uy = torch.empty_like(rho) if velocity else None
+        capi.lb_moments(self.h, rho.data_ptr(), ux.data_ptr() if velocity else None,
+                        uy.data_ptr() if velocity else None)
+        return (rho, ux, uy) if velocity else rho
+
+    def reduce(self) -> dict:
+        v = capi.lb_reduce(self.h)
+        keys = ("mass", "mom_x", "mom_y", "p_center", "p_corner", "n_liquid", "rho_min", "rho_max")
+        return dict(zip(keys, v))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            capi.lb_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

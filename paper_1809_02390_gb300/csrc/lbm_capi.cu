@@ -1,0 +1,386 @@
+// C ABI of the library: handles, parameter checking, launches.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <typename real>
+Coef<real> make_coef(const lb_params& p, const lb_derived& d) {
+  Coef<real> c;
+  const double w = 1.0 - d.k;  // varpi
+  const double k = d.k, h = d.h, b = d.b;
+  const double se = d.s_e, seps = d.s_eps, sq = d.s_q, sp = d.s_p;
+  c.eos = p.eos;
+  c.G2 = real(d.G2);
+  c.lam = real(d.lam);
+  c.RT = real(p.R_gas * d.T);
+  c.a = real(p.eos_a);
+  c.bq = real(p.eos == LB_EOS_VDW ? p.eos_b : p.eos_b / 4.0);
+  c.beta2 = real(d.beta2);
+  c.hk_seps = real(0.5 * k * seps);
+  c.hh_sq = real(0.5 * h * sq);
+  c.b_sq = real(b * sq);
+  c.hb_sq = real(0.5 * b * sq);
+  c.om_e = real(1.0 - 0.5 * se);
+  c.om_eps = real(1.0 - 0.5 * seps);
+  c.om_q = real(1.0 - 0.5 * sq);
+  c.om_p = real(1.0 - 0.5 * sp);
+  // Supplement Eq. 34, 37, 40.
+  c.R11 = real(-se / (4.0 * w) * (9.0 * (1.0 - k) - 2.0 * (3.0 * k + h)));
+  c.R17 = real(-3.0 * sp * (2.0 - se) / (4.0 * (2.0 - sp)) * (9.0 * (1.0 - k) + 2.0 * (3.0 * k + h)));
+  c.R18 = real(12.0 * sp * (2.0 - se) / (2.0 - sp) * (3.0 * k + h));
+  c.R71 = real(-se * (2.0 - sp) / (4.0 * w * (2.0 - se)) * (3.0 - 4.0 * b));
+  c.R77 = real(-3.0 * sp / 4.0 * (3.0 + 4.0 * b));
+  c.R81 = real(se * (2.0 - sp) / (w * (2.0 - se)) * b);
+  c.R88 = real(6.0 * sp * b);
+  c.T1a = real(3.0 * (2.0 - se) / 2.0 * (1.0 - k));
+  c.T1b = real(3.0 * (2.0 - se) / 2.0 * (2.0 * k + h));
+  c.X1 = real(9.0 * (2.0 - se) / 2.0 * (2.0 * k + h));
+  c.T7 = real((2.0 - sp) / 2.0);
+  c.T7b = real((2.0 - sp) * b);
+  c.X7 = real(-3.0 * (2.0 - sp) * b);
+  c.T8 = real(-(2.0 - sp) * b / 2.0);
+  c.X8 = real(3.0 * (2.0 - sp) * b / 2.0);
+  // Step (6): s_e Q1 + k (s_e/2 - 1) s_eps Q2 with Q1 = -Q2 = |F~|^2 / 2.
+  c.Q1 = real(0.5 * (se - k * (0.5 * se - 1.0) * seps));
+  c.Q2 = real(-0.5 * seps);
+  c.Q78 = real(sp / 12.0);
+  c.rho_ref = real(p.rho_ref);
+  return c;
+}
+
+template Coef<float> make_coef<float>(const lb_params&, const lb_derived&);
+template Coef<double> make_coef<double>(const lb_params&, const lb_derived&);
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lb_handle {
+  lb_params p;
+  lb_derived d;
+  void* f[2];
+  int cur;
+  void* scratch;
+  size_t scratch_bytes;
+  cudaStream_t stream;
+  int64_t steps;
+  int variant;  // LB_FUSED or LB_TWO_PASS
+  int nstrips, rows_per_warp, nwork, fused_blocks;
+  int reduce_blocks;
+  Coef<float> cf;
+  Coef<double> cd;
+  char err[512];
+};
+
+namespace {
+
+int fail(lb_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h)
+    std::snprintf(h->err, sizeof(h->err), "%s", buf);
+  else
+    set_thread_error(buf);
+  return code;
+}
+
+#define LB_CUDA(h, call)                                                                     \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail((h), LB_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t elem_bytes(int precision) { return precision == LB_FP64 ? 8 : precision == LB_FP32 ? 4 : 2; }
+size_t real_bytes(int precision) { return precision == LB_FP64 ? 8 : 4; }
+
+size_t rho_plane_bytes(const lb_params* p) {
+  return (size_t(p->nx) * p->ny * real_bytes(p->precision) + 255) / 256 * 256;
+}
+
+constexpr int kMaxReduceBlocks = 1024;
+
+size_t reduce_bytes() { return size_t(kMaxReduceBlocks) * kReduceSlots * sizeof(double) + 256; }
+
+template <typename real, typename store_t>
+void launch_step(lb_handle* h, const Coef<real>& c) {
+  const store_t* fin = static_cast<const store_t*>(h->f[h->cur]);
+  store_t* fout = static_cast<store_t*>(h->f[1 - h->cur]);
+  const int nx = h->p.nx, ny = h->p.ny;
+  if (h->variant == LB_FUSED) {
+    k_step_fused<real, store_t><<<h->fused_blocks, kFusedThreads, 0, h->stream>>>(
+        fin, fout, nx, ny, h->nstrips, h->rows_per_warp, h->nwork, c);
+  } else {
+    real* rho = static_cast<real*>(h->scratch);
+    const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
+    k_density<real, store_t><<<grd, blk, 0, h->stream>>>(fin, rho, nx, ny);
+    k_collide_rho<real, store_t><<<grd, blk, 0, h->stream>>>(fin, fout, rho, nx, ny, c);
+  }
+}
+
+template <typename real, typename store_t>
+int configure_fused(lb_handle* h) {
+  int dev = 0, sms = 0, per_sm = 0;
+  LB_CUDA(h, cudaGetDevice(&dev));
+  LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<real, store_t>, kFusedThreads, 0));
+  if (per_sm < 1) per_sm = 1;
+  const int nx = h->p.nx, ny = h->p.ny;
+  h->nstrips = (nx + 31) / 32;
+  // One wave: every warp slot of the GPU gets one (strip, row-chunk) work item.
+  const long slots = long(sms) * per_sm * (kFusedThreads / 32);
+  long chunks = slots / h->nstrips;
+  if (chunks < 1) chunks = 1;
+  int rows = int((ny + chunks - 1) / chunks);
+  if (rows < 8) rows = ny < 8 ? ny : 8;  // a few rows per warp amortise the two halo rows
+  h->rows_per_warp = rows;
+  const int nchunks = (ny + rows - 1) / rows;
+  h->nwork = h->nstrips * nchunks;
+  h->fused_blocks = (h->nwork * 32 + kFusedThreads - 1) / kFusedThreads;
+  h->reduce_blocks = sms * 2 < kMaxReduceBlocks ? sms * 2 : kMaxReduceBlocks;
+  return LB_OK;
+}
+
+int configure(lb_handle* h) {
+  switch (h->p.precision) {
+    case LB_FP64: return configure_fused<double, double>(h);
+    case LB_FP32: return configure_fused<float, float>(h);
+    default: return configure_fused<float, __half>(h);
+  }
+}
+
+template <typename real, typename store_t>
+void launch_moments(lb_handle* h, real* rho, real* ux, real* uy, real rho_ref, real G2) {
+  const store_t* f = static_cast<const store_t*>(h->f[h->cur]);
+  const int nx = h->p.nx, ny = h->p.ny;
+  const size_t N = size_t(nx) * ny;
+  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, rho_ref);
+  if (ux || uy) {
+    const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
+    k_velocity<real, store_t><<<grd, blk, 0, h->stream>>>(f, rho, ux, uy, nx, ny, G2);
+  }
+}
+
+template <typename real, typename store_t>
+int run_reduce(lb_handle* h, double out[8]) {
+  const int nx = h->p.nx, ny = h->p.ny;
+  const size_t N = size_t(nx) * ny;
+  real* rho = static_cast<real*>(h->scratch);
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(h->scratch) + rho_plane_bytes(&h->p));
+  double* dout = partial + size_t(kMaxReduceBlocks) * kReduceSlots;
+  const store_t* f = static_cast<const store_t*>(h->f[h->cur]);
+  const real rho_ref = real(h->p.rho_ref);
+  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, rho_ref);
+  const double rho_mid = 0.5 * (h->d.rho_g + h->d.rho_l);
+  k_reduce_partial<real, store_t><<<h->reduce_blocks, kReduceThreads, 0, h->stream>>>(
+      f, rho, nx, ny, real(h->d.G2), std::isfinite(rho_mid) ? rho_mid : 1e300, partial);
+  k_reduce_final<<<1, 32, 0, h->stream>>>(partial, h->reduce_blocks, dout);
+  double res[kReduceSlots];
+  real probe[2];
+  LB_CUDA(h, cudaGetLastError());
+  LB_CUDA(h, cudaMemcpyAsync(res, dout, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaMemcpyAsync(&probe[0], rho + size_t(ny / 2) * nx + nx / 2, sizeof(real), cudaMemcpyDeviceToHost,
+                             h->stream));
+  LB_CUDA(h, cudaMemcpyAsync(&probe[1], rho, sizeof(real), cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  // p_EOS / c^2 at the two probe nodes, FP64 on the host.
+  Coef<double> cd = h->cd;
+  auto pe = [&](double r) {
+    if (cd.eos == LB_EOS_VDW) return cd.lam * (r * cd.RT / (1.0 - cd.bq * r) - cd.a * r * r);
+    const double t = cd.bq * r, om = 1.0 - t;
+    return cd.lam * (r * cd.RT * (1.0 + t + t * t - t * t * t) / (om * om * om) - cd.a * r * r);
+  };
+  out[0] = res[0];
+  out[1] = res[1];
+  out[2] = res[2];
+  out[3] = pe(double(probe[0]));
+  out[4] = pe(double(probe[1]));
+  out[5] = res[3];
+  out[6] = res[4];
+  out[7] = res[5];
+  if (res[6] > 0) return fail(h, LB_ENONFINITE, "%.0f nodes have a non-finite density", res[6]);
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_abi_version(void) { return 1; }
+
+int lb_derive(const lb_params* p, lb_derived* out) {
+  if (!out) return fail(nullptr, LB_EINVAL, "null output");
+  char err[512] = {0};
+  const int rc = derive(p, out, err, sizeof(err));
+  if (rc != LB_OK) return fail(nullptr, rc, "%s", err);
+  return LB_OK;
+}
+
+size_t lb_state_bytes(const lb_params* p) {
+  if (!p || p->nx < 1 || p->ny < 1) return 0;
+  return 9 * size_t(p->nx) * p->ny * elem_bytes(p->precision);
+}
+
+size_t lb_scratch_bytes(const lb_params* p) {
+  if (!p || p->nx < 1 || p->ny < 1) return 0;
+  return rho_plane_bytes(p) + reduce_bytes();
+}
+
+int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scratch, size_t scratch_bytes,
+            const double* rho0, int rho0_on_device, void* stream) {
+  if (!out) return fail(nullptr, LB_EINVAL, "null handle pointer");
+  *out = nullptr;
+  lb_derived d;
+  char err[512] = {0};
+  int rc = derive(p, &d, err, sizeof(err));
+  if (rc != LB_OK) return fail(nullptr, rc, "%s", err);
+  if (!f_a || !f_b || f_a == f_b) return fail(nullptr, LB_EINVAL, "f_a and f_b must be two distinct device buffers");
+  if (!rho0) return fail(nullptr, LB_EINVAL, "null initial density");
+  const int variant = p->variant == LB_TWO_PASS ? LB_TWO_PASS : LB_FUSED;
+  if (scratch && scratch_bytes < lb_scratch_bytes(p))
+    return fail(nullptr, LB_ENOMEM, "scratch of %zu bytes is below the %zu needed", scratch_bytes,
+                lb_scratch_bytes(p));
+  if (variant == LB_TWO_PASS && !scratch)
+    return fail(nullptr, LB_ENOMEM, "the two-pass variant needs %zu bytes of scratch", lb_scratch_bytes(p));
+  const size_t N = size_t(p->nx) * p->ny;
+  if (!rho0_on_device) {
+    for (size_t n = 0; n < N; ++n)
+      if (!(rho0[n] > 0) || !std::isfinite(rho0[n]))
+        return fail(nullptr, LB_EINVAL, "initial density at node %zu is not positive and finite", n);
+    if (p->eos == LB_EOS_VDW)
+      for (size_t n = 0; n < N; ++n)
+        if (!(p->eos_b * rho0[n] < 1.0))
+          return fail(nullptr, LB_EINVAL, "initial density at node %zu exceeds 1/b of the vdW EOS", n);
+  }
+  lb_handle* h = new (std::nothrow) lb_handle();
+  if (!h) return fail(nullptr, LB_EINVAL, "out of host memory");
+  h->p = *p;
+  // The FP32 kernels add the shift back in float: store exactly that value.
+  if (p->precision != LB_FP64) h->p.rho_ref = double(float(p->rho_ref));
+  h->d = d;
+  h->f[0] = f_a;
+  h->f[1] = f_b;
+  h->cur = 0;
+  h->scratch = scratch;
+  h->scratch_bytes = scratch_bytes;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->steps = 0;
+  h->variant = variant;
+  h->cf = make_coef<float>(h->p, d);
+  h->cd = make_coef<double>(h->p, d);
+  rc = configure(h);
+  if (rc != LB_OK) {
+    set_thread_error(h->err);
+    delete h;
+    return rc;
+  }
+  const double* rho_dev = rho0;
+  auto bail = [&](cudaError_t e, const char* what) {
+    fail(nullptr, LB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    delete h;
+    return LB_ECUDA;
+  };
+  cudaError_t e;
+  if (!rho0_on_device) {
+    // Stage the host densities in the second population buffer (>= 8 bytes per node).
+    e = cudaMemcpyAsync(f_b, rho0, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return bail(e, "cudaMemcpyAsync(rho0)");
+    rho_dev = static_cast<const double*>(f_b);
+  }
+  const unsigned blocks = unsigned((N + 255) / 256);
+  switch (p->precision) {
+    case LB_FP64: k_init_rest<double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny, h->cd); break;
+    case LB_FP32: k_init_rest<float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, h->cd); break;
+    default: k_init_rest<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny, h->cd); break;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(e, "init kernel launch");
+  if (!rho0_on_device) {
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+  }
+  *out = h;
+  return LB_OK;
+}
+
+int lb_step(lb_handle* h, int64_t nsteps) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (nsteps < 0) return fail(h, LB_EINVAL, "nsteps must be >= 0");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    switch (h->p.precision) {
+      case LB_FP64: launch_step<double, double>(h, h->cd); break;
+      case LB_FP32: launch_step<float, float>(h, h->cf); break;
+      default: launch_step<float, __half>(h, h->cf); break;
+    }
+    LB_CUDA(h, cudaGetLastError());
+    h->cur = 1 - h->cur;
+    ++h->steps;
+  }
+  return LB_OK;
+}
+
+void* lb_state(lb_handle* h) { return h ? h->f[h->cur] : nullptr; }
+
+int64_t lb_steps_done(const lb_handle* h) { return h ? h->steps : -1; }
+
+int lb_moments(lb_handle* h, void* rho, void* ux, void* uy) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (!rho) return fail(h, LB_EINVAL, "rho output is required");
+  if (h->p.precision == LB_FP64)
+    launch_moments<double, double>(h, static_cast<double*>(rho), static_cast<double*>(ux), static_cast<double*>(uy),
+                                   h->cd.rho_ref, h->cd.G2);
+  else if (h->p.precision == LB_FP32)
+    launch_moments<float, float>(h, static_cast<float*>(rho), static_cast<float*>(ux), static_cast<float*>(uy),
+                                 h->cf.rho_ref, h->cf.G2);
+  else
+    launch_moments<float, __half>(h, static_cast<float*>(rho), static_cast<float*>(ux), static_cast<float*>(uy),
+                                  h->cf.rho_ref, h->cf.G2);
+  LB_CUDA(h, cudaGetLastError());
+  return LB_OK;
+}
+
+int lb_reduce(lb_handle* h, double out[8]) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (!out) return fail(h, LB_EINVAL, "null output");
+  if (!h->scratch) return fail(h, LB_ENOMEM, "lb_reduce needs the scratch buffer (lb_scratch_bytes)");
+  switch (h->p.precision) {
+    case LB_FP64: return run_reduce<double, double>(h, out);
+    case LB_FP32: return run_reduce<float, float>(h, out);
+    default: return run_reduce<float, __half>(h, out);
+  }
+}
+
+int lb_get_state(lb_handle* h, void* dst) {
+  if (!h || !dst) return fail(h, LB_EINVAL, "null argument");
+  LB_CUDA(h, cudaMemcpyAsync(dst, h->f[h->cur], lb_state_bytes(&h->p), cudaMemcpyDeviceToDevice, h->stream));
+  return LB_OK;
+}
+
+int lb_set_state(lb_handle* h, const void* src) {
+  if (!h || !src) return fail(h, LB_EINVAL, "null argument");
+  LB_CUDA(h, cudaMemcpyAsync(h->f[h->cur], src, lb_state_bytes(&h->p), cudaMemcpyDeviceToDevice, h->stream));
+  return LB_OK;
+}
+
+int lb_get_derived(const lb_handle* h, lb_derived* out) {
+  if (!h || !out) return LB_EINVAL;
+  *out = h->d;
+  return LB_OK;
+}
+
+const char* lb_last_error(const lb_handle* h) { return h ? h->err : thread_error(); }
+
+void lb_free(lb_handle* h) { delete h; }
+
+}  // extern "C"

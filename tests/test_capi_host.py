@@ -1,0 +1,105 @@
+"""CPU tests of the C ABI: the library loads, exports every declared entry
+point, derives the same lattice parameters as the oracle (host-only code),
+and rejects invalid input with clear errors before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import params as op
+from oracle import thermo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1809_02390_gb300 import build as b
+
+    b.build()
+    from paper_1809_02390_gb300 import capi as c
+
+    return c
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(lb_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = capi.lib()
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            names |= _declared(h)
+    assert len(names) >= 15
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    bound = {n for n, _, _ in capi.SIGNATURES}
+    assert names <= bound | {n for n in names if n.startswith("lb_batch") or n.startswith("lb_adjoint")}
+
+
+def test_abi_struct_sizes(capi):
+    assert ctypes.sizeof(capi.lb_params) == 6 * 4 + 16 * 8
+    assert ctypes.sizeof(capi.lb_derived) == 20 * 8
+    assert capi.lib().lb_abi_version() == 1
+
+
+@pytest.mark.parametrize("eos,a,b,Tr,K_int", [("vdw", 9 / 49, 2 / 21, 0.85, 1.0), ("vdw", 9 / 49, 2 / 21, 0.7, 1.7),
+                                              ("cs", 1.0, 4.0, 0.8, 2.2949), ("cs", 1.0, 4.0, 0.6, 1.0)])
+def test_derived_parameters_match_oracle(capi, eos, a, b, Tr, K_int):
+    p = capi.make_params(64, 64, eos=capi.LB_EOS_VDW if eos == "vdw" else capi.LB_EOS_CS, eos_a=a, eos_b=b,
+                         Tr=Tr, K_int=K_int, K_eos=2.0)
+    d = capi.lb_derive(p)
+    o = op.from_physical(eos=eos, a=a, b=b, Tr=Tr, K_int=K_int, K_eos=2.0)
+    for k_lib, k_or in [("rho_g", "rho_g"), ("rho_l", "rho_l"), ("lam", "lam"), ("G2", "G2"), ("s_e", "se"),
+                        ("s_q", "sq"), ("s_eps", "seps"), ("s_p", "sp"), ("T", "T"), ("Tc", "Tc")]:
+        assert d[k_lib] == pytest.approx(getattr(o, k_or), rel=1e-12), k_lib
+    it = thermo.interface(thermo.make_eos(eos, a, b, 1.0, Tr, K_eos=2.0), 1.0)
+    assert d["W1"] == pytest.approx(it["W"], rel=1e-9)
+    assert d["sigma1"] == pytest.approx(it["sigma"], rel=1e-9)
+    assert d["k"] == pytest.approx(5 / 6) and d["b"] == pytest.approx(5 / 3) and d["h"] == pytest.approx(5 / 3)
+    assert d["beta2"] == pytest.approx(-2.4)
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("nx", 2, "nx and ny"), ("varpi", 1.0, "varpi"), ("varpi", 1 / 3, "varpi"), ("s_p", 2.0, "s_p"),
+    ("s_p", 0.0, "s_p"), ("eos", 7, "eos"), ("precision", 5, "precision"), ("Tr", 1.2, "coexistence"),
+    ("eos_b", -1.0, "eos_a"), ("s_q", 2.5, "rates")])
+def test_invalid_parameters_are_rejected(capi, field, value, needle):
+    p = capi.make_params(64, 64)
+    setattr(p, field, value)
+    with pytest.raises(capi.LBError) as ei:
+        capi.lb_derive(p)
+    assert ei.value.code == capi.LB_EINVAL and needle in str(ei.value)
+
+
+def test_init_rejects_bad_input_before_any_gpu_work(capi):
+    import numpy as np
+
+    p = capi.make_params(8, 8)
+    rho = np.full(64, 2.0)
+    rho[5] = -1.0
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_char * 16)()
+    rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), ctypes.addressof(buf), ctypes.addressof(buf) + 8,
+                            None, 0, rho.ctypes.data, 0, None)
+    assert rc == capi.LB_EINVAL  # identical f buffers
+    rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), 1 << 40, 2 << 40, None, 0, rho.ctypes.data, 0, None)
+    assert rc == capi.LB_EINVAL and "node 5" in capi.lb_last_error(None)
+    p.variant = capi.LB_TWO_PASS
+    rho[5] = 2.0
+    rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), 1 << 40, 2 << 40, None, 0, rho.ctypes.data, 0, None)
+    assert rc == capi.LB_ENOMEM
+
+
+def test_sizes(capi):
+    p = capi.make_params(100, 30, precision=capi.LB_FP16S)
+    assert capi.lb_state_bytes(p) == 9 * 100 * 30 * 2
+    p.precision = capi.LB_FP64
+    assert capi.lb_state_bytes(p) == 9 * 100 * 30 * 8
+    assert capi.lb_scratch_bytes(p) >= 100 * 30 * 8

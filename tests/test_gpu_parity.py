@@ -1,0 +1,160 @@
+"""Parity of the CUDA time step (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 GPU path <= 1e-12 relative on f after 2,000 steps; FP32 path
+<= 2e-5 relative on rho; FP16 storage (FP32 arithmetic) <= 2e-3 relative on rho
+after 500 steps, derived from half precision's 2^-11 rounding of the stored
+deviations.  Relative error = max|diff| / max|reference|."""
+import numpy as np
+import pytest
+
+from gpu_util import W_REST, gpu_populations, lattice, oracle_params, rel_inf, set_state_fp64
+from paper_1809_02390_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_02390_gb300 import build
+
+    build.build()
+
+
+def droplet64():
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    return p, inputs.droplet(64, 64, 16, 5, p.rho_g, p.rho_l)
+
+
+@pytest.mark.parametrize("variant", ["fused", "two_pass"])
+def test_fp64_droplet_2000_steps(orc, variant):
+    """64x64 periodic vdW droplet, R = 16, tanh width 5, Tr = 0.85, tau = 1, 2,000 steps."""
+    p, rho0 = droplet64()
+    ref = orc.step(p, orc.init_feq(p, rho0), 2000)
+    lat = lattice(rho0, "fp64", variant, Tr=0.85, K_int=1.0)
+    lat.step(2000)
+    torch.cuda.synchronize()
+    assert rel_inf(gpu_populations(lat), ref) <= 1e-12
+
+
+def test_fp64_init_matches_oracle(orc):
+    p, rho0 = droplet64()
+    lat = lattice(rho0, "fp64")
+    assert rel_inf(gpu_populations(lat), orc.init_feq(p, rho0)) <= 1e-15
+
+
+@pytest.mark.parametrize("precision,tol,steps", [("fp32", 2e-5, 2000), ("fp16s", 2e-3, 500)])
+@pytest.mark.parametrize("variant", ["fused", "two_pass"])
+def test_reduced_precision_droplet(orc, precision, tol, steps, variant):
+    p, rho0 = droplet64()
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), steps))[0]
+    lat = lattice(rho0, precision, variant, Tr=0.85, K_int=1.0)
+    lat.step(steps)
+    rho = lat.moments(velocity=False).double().cpu().numpy()
+    assert rel_inf(rho, ref) <= tol
+
+
+RAGGED = [(37, 29), (70, 45), (33, 31), (32, 32), (3, 3), (5, 7), (4, 100), (100, 4), (65, 9)]
+
+
+@pytest.mark.parametrize("nx,ny", RAGGED)
+@pytest.mark.parametrize("variant", ["fused", "two_pass"])
+def test_fp64_ragged_with_flow(orc, nx, ny, variant):
+    """Arbitrary sizes (several strips, ragged tails, lattices narrower than a warp)
+    from a state with a random velocity field, so that the velocity-dependent
+    terms (S off-diagonals, R, T, X, the cubic F_m terms) are all exercised."""
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    rng = np.random.default_rng(nx * 1000 + ny)
+    rho = inputs.droplet(nx, ny, min(nx, ny) / 4, 3, p.rho_g, p.rho_l) * (1 + 0.01 * rng.uniform(-1, 1, (ny, nx)))
+    f0 = orc.init_eq(p, rho, 0.05 * rng.uniform(-1, 1, (ny, nx)), 0.05 * rng.uniform(-1, 1, (ny, nx)))
+    ref = orc.step(p, f0, 20)
+    lat = lattice(rho, "fp64", variant, Tr=0.85, K_int=1.0)
+    set_state_fp64(lat, f0)
+    lat.step(20)
+    torch.cuda.synchronize()
+    assert rel_inf(gpu_populations(lat), ref) <= 1e-13
+
+
+def test_fp64_carnahan_starling(orc):
+    """The paper's own EOS (Eq. 20, a = 1, b = 4, R = 1) at Tr = 0.8 with W = 10 (K_INT = 2.2949)."""
+    p = oracle_params(eos="cs", a=1.0, b=4.0, Tr=0.8, K_int=2.2949)
+    rho0 = inputs.slab(48, 16, 24, 10, p.rho_g, p.rho_l)
+    ref = orc.step(p, orc.init_feq(p, rho0), 300)
+    lat = lattice(rho0, "fp64", eos="cs", eos_a=1.0, eos_b=4.0, Tr=0.8, K_int=2.2949)
+    lat.step(300)
+    torch.cuda.synchronize()
+    assert rel_inf(gpu_populations(lat), ref) <= 1e-12
+
+
+def test_moments_and_reduce(orc):
+    p, rho0 = droplet64()
+    f = orc.step(p, orc.init_feq(p, rho0), 50)
+    rho_o, ux_o, uy_o = orc.macro(p, f)
+    lat = lattice(rho0, "fp64", Tr=0.85, K_int=1.0)
+    lat.step(50)
+    rho, ux, uy = (t.cpu().numpy() for t in lat.moments())
+    assert rel_inf(rho, rho_o) <= 1e-13
+    assert np.abs(ux - ux_o).max() <= 1e-13 and np.abs(uy - uy_o).max() <= 1e-13
+    r = lat.reduce()
+    assert r["mass"] == pytest.approx(rho_o.sum(), rel=1e-13)
+    assert r["mom_x"] == pytest.approx((rho_o * ux_o).sum(), abs=1e-11)
+    assert r["n_liquid"] == (rho_o > 0.5 * (p.rho_g + p.rho_l)).sum()
+    assert r["rho_min"] == pytest.approx(rho_o.min(), rel=1e-13)
+    assert r["rho_max"] == pytest.approx(rho_o.max(), rel=1e-13)
+    assert r["p_center"] == pytest.approx(orc.eos(p, rho_o[32, 32])[0], rel=1e-12)
+
+
+def test_deterministic():
+    p, rho0 = droplet64()
+    a = lattice(rho0, "fp32")
+    b = lattice(rho0, "fp32")
+    a.step(100)
+    b.step(100)
+    torch.cuda.synchronize()
+    assert torch.equal(a.state(), b.state())
+
+
+def _patch(f, x, y, r):
+    ny, nx = f.shape[1:]
+    ys = [(y + d) % ny for d in range(-r, r + 1)]
+    xs = [(x + d) % nx for d in range(-r, r + 1)]
+    return f[:, ys][:, :, xs]
+
+
+def test_full_size_spinodal_sampled(orc):
+    """4096 x 4096 FP32 spinodal decomposition in the benchmark's launch
+    configuration: two steps from the seeded initial state, checked at sampled
+    nodes, each computed by the oracle from its own initial state on the 9x9
+    neighbourhood that determines it (periodic wrap of the patch is never reached)."""
+    p = oracle_params(Tr=0.8, K_int=1.0)
+    n = 4096
+    rho0 = inputs.spinodal(n, n, 0.5 * (p.rho_g + p.rho_l), 0.01, seed=0)
+    lat = lattice(rho0, "fp32", Tr=0.8, K_int=1.0)
+    steps = 2
+    lat.step(steps)
+    torch.cuda.synchronize()
+    st = lat.state()
+    rng = np.random.default_rng(3)
+    pts = [(0, 0), (n - 1, n - 1), (31, 32), (32, 4095), (4064, 17)] + [tuple(v) for v in rng.integers(0, n, (27, 2))]
+    worst = 0.0
+    for x, y in pts:
+        patch_rho = _patch(rho0[None], x, y, 2 * steps + 2)[0]
+        ref = orc.step(p, orc.init_feq(p, patch_rho), steps)[:, 2 * steps + 2, 2 * steps + 2]
+        got = st[:, y, x].double().cpu().numpy() + lat.rho_ref * W_REST
+        worst = max(worst, float(np.abs(got - ref).max() / np.abs(ref).max()))
+    assert worst <= 2e-6
+
+
+def test_full_size_mass_conservation():
+    p = oracle_params(Tr=0.8, K_int=1.0)
+    n = 4096
+    rho0 = inputs.spinodal(n, n, 0.5 * (p.rho_g + p.rho_l), 0.01, seed=0)
+    lat = lattice(rho0, "fp32", Tr=0.8, K_int=1.0)
+    m0 = lat.reduce()["mass"]
+    lat.step(200)
+    r = lat.reduce()
+    assert r["mass"] == pytest.approx(m0, rel=2e-6)
+    assert rho0.sum() == pytest.approx(m0, rel=1e-6)
