@@ -1,0 +1,326 @@
+"""Benchmark of the D2Q9 self-tuning-EOS multiphase LB time step on GB300.
+
+Workload: FP32 spinodal decomposition on a 4096 x 4096 periodic lattice,
+mean density at the midpoint of the coexistence densities with seeded uniform
++-1% noise, van der Waals EOS (a = 9/49, b = 2/21, R = 1) at T/Tc = 0.8, fluid
+at rest, tau = 1.  One benchmark step = one full time step of the lattice
+(pull streaming, density, interaction force, moment-space collision of Eq. 13,
+inverse transform) = 16.8 M lattice updates.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent lattice (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 multiphase MLUPS & % of GB300 HBM peak (FP32 vs FP64); adjoint/forward cost"
+N_SIDE = 4096
+TR = 0.8
+BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 populations
+# DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
+# for the kernel sources they were measured on (sha256 of the files below).
+KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_02390_gb300/csrc/lbm_device.cuh"]
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_rho(n: int, seed: int):
+    from paper_1809_02390_gb300 import derive, inputs
+
+    d = derive(n, n, Tr=TR)
+    return inputs.spinodal(n, n, 0.5 * (d["rho_g"] + d["rho_l"]), 0.01, seed=seed), d
+
+
+def time_steps(lat, steps: int, torch) -> float:
+    """Milliseconds for `steps` time steps, CUDA events on the launching stream."""
+    s = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    lat.step(steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def max_over_ranks(v: float, torch, world: int) -> float:
+    if world == 1:
+        return v
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_baseline(rho0, seconds: float = 12.0) -> dict:
+    """The FP64 oracle as it stands (single-threaded C++), on a 256 x 256 periodic
+    crop of the same initial field, stepped until ~`seconds` of CPU time."""
+    import oracle
+    from oracle import params as op
+
+    p = op.from_physical(Tr=TR)
+    crop = rho0[:256, :256].copy()
+    f = oracle.init_feq(p, crop)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        f = oracle.step(p, f, 10)
+        steps += 10
+    dt = time.perf_counter() - t0
+    return {"value": round(256 * 256 * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the FP64 oracle on a 256x256 periodic crop of the workload" % steps}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores; each step is one
+    oracle time step on a 128 x 128 periodic crop of the workload."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from oracle import params as op
+    from paper_1809_02390_gb300 import inputs
+
+    p = op.from_physical(Tr=TR)
+    rho0 = inputs.spinodal(N_SIDE, N_SIDE, 0.5 * (p.rho_g + p.rho_l), 0.01, seed=0)
+    crop = np.ascontiguousarray(rho0[:128, :128])
+    f = oracle.init_feq(p, crop)
+    f = oracle.step(p, f, args.warmup)
+    t0 = time.perf_counter()
+    f = oracle.step(p, f, args.steps)
+    dt = time.perf_counter() - t0
+    value = 128 * 128 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "spinodal-4096x4096-vdw-Tr0.8 (128x128 periodic crop per step)",
+                       "lattice": [128, 128], "eos": "vdw", "Tr": TR},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d oracle steps on a 128x128 crop" % args.steps},
+            "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_1809_02390_gb300 import Lattice, capi
+    from paper_1809_02390_gb300 import build as lbuild
+
+    lbuild.build()
+    n = args.size
+    rho0, d = workload_rho(n, seed=rank)
+    nodes = n * n
+    pk = peaks()
+
+    # --- main measurement: FP32 fused, inputs resident in HBM -----------------
+    lat = Lattice(rho0, precision="fp32", variant="fused", Tr=TR)
+    lat.step(args.warmup)
+    barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = time_steps(lat, args.steps, torch)
+    ms = max_over_ranks(ms, torch, world)
+    ms_step = ms / args.steps
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    achieved = BYTES_PER_LU["fp32"] * nodes / (ms_step * 1e-3) / 1e9
+    sane = lat.reduce()
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    if args.only_main:
+        if rank == 0:
+            print(json.dumps({"only_main": True, "size": n, "MLUPS": round(value, 1), "ms_per_step": ms_step}))
+        return
+
+    # --- other variants / precisions (shorter runs, same workload) -------------
+    variants = {}
+    for prec, var, k in (("fp32", "two_pass", max(50, args.steps // 4)), ("fp16s", "fused", max(50, args.steps // 4)),
+                         ("fp64", "fused", 30)):
+        lt = Lattice(rho0, precision=prec, variant=var, Tr=TR)
+        lt.step(3)
+        m = time_steps(lt, k, torch) / k
+        variants["%s_%s" % (prec, var)] = {
+            "MLUPS": round(nodes / (m * 1e-3) / 1e6, 1), "ms_per_step": round(m, 4),
+            "algorithmic_GBps": round(BYTES_PER_LU[prec] * nodes / (m * 1e-3) / 1e9, 1)}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
+
+    # --- end to end through the public API with host buffers -------------------
+    rho_host = torch.from_numpy(np.ascontiguousarray(rho0)).pin_memory()
+    out_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    lt = Lattice(rho_host, precision="fp32", variant="fused", Tr=TR)
+    lt.step(args.steps)
+    rho_dev = lt.moments(velocity=False)
+    out_host.copy_(rho_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, torch, world)
+    lt.close()
+    del lt
+    e2e = {"value": round(world * nodes * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": round(nodes * 8 / args.steps, 1),
+           "d2h_bytes_per_step": round(nodes * 4 / args.steps, 1),
+           "note": "lb_init from pinned host densities, K steps, lb_moments, density read back; bytes amortised per step"}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(("k_step_fused<float,float>", src_hash))
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
+            "kernel": "k_step_fused<float,float>", "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
+            "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
+            "kernel_source_sha": src_hash}
+    cpu = cpu_baseline(rho0) if world == 1 else None
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "spinodal-%dx%d-fp32-vdw-Tr0.8" % (n, n), "lattice": [n, n], "eos": "vdw",
+                       "Tr": TR, "storage": "fp32 (deviation from w_i rho_ref)", "variant": "fused",
+                       "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
+                       "parallelism": "independent lattice per GPU" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk.summary(), "variants": variants,
+            "check": {"mass": sane["mass"], "rho_min": sane["rho_min"], "rho_max": sane["rho_max"]}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=N_SIDE, help="lattice side (profiling runs use smaller cases)")
+    ap.add_argument("--only-main", action="store_true", help="time the FP32 fused step only (profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -12,53 +12,92 @@
 
 namespace lbm {
 
-template <typename real>
-Coef<real> make_coef(const lb_params& p, const lb_derived& d) {
-  Coef<real> c;
+template <typename V>
+V bc(double x);
+template <>
+double bc<double>(double x) {
+  return x;
+}
+template <>
+float bc<float>(double x) {
+  return float(x);
+}
+template <>
+f2 bc<f2>(double x) {
+  return f2{make_float2(float(x), float(x))};
+}
+
+// Collision constants (FP64 on the host, then rounded to V).
+template <typename V>
+VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d) {
+  VCoef<V> c;
   const double w = 1.0 - d.k;  // varpi
   const double k = d.k, h = d.h, b = d.b;
   const double se = d.s_e, seps = d.s_eps, sq = d.s_q, sp = d.s_p;
+  const double lam = d.lam, RT = p.R_gas * d.T, a = p.eos_a;
+  const double bq = p.eos == LB_EOS_VDW ? p.eos_b : p.eos_b / 4.0;
   c.eos = p.eos;
-  c.G2 = real(d.G2);
-  c.lam = real(d.lam);
-  c.RT = real(p.R_gas * d.T);
-  c.a = real(p.eos_a);
-  c.bq = real(p.eos == LB_EOS_VDW ? p.eos_b : p.eos_b / 4.0);
-  c.beta2 = real(d.beta2);
-  c.hk_seps = real(0.5 * k * seps);
-  c.hh_sq = real(0.5 * h * sq);
-  c.b_sq = real(b * sq);
-  c.hb_sq = real(0.5 * b * sq);
-  c.om_e = real(1.0 - 0.5 * se);
-  c.om_eps = real(1.0 - 0.5 * seps);
-  c.om_q = real(1.0 - 0.5 * sq);
-  c.om_p = real(1.0 - 0.5 * sp);
-  // Supplement Eq. 34, 37, 40.
-  c.R11 = real(-se / (4.0 * w) * (9.0 * (1.0 - k) - 2.0 * (3.0 * k + h)));
-  c.R17 = real(-3.0 * sp * (2.0 - se) / (4.0 * (2.0 - sp)) * (9.0 * (1.0 - k) + 2.0 * (3.0 * k + h)));
-  c.R18 = real(12.0 * sp * (2.0 - se) / (2.0 - sp) * (3.0 * k + h));
-  c.R71 = real(-se * (2.0 - sp) / (4.0 * w * (2.0 - se)) * (3.0 - 4.0 * b));
-  c.R77 = real(-3.0 * sp / 4.0 * (3.0 + 4.0 * b));
-  c.R81 = real(se * (2.0 - sp) / (w * (2.0 - se)) * b);
-  c.R88 = real(6.0 * sp * b);
-  c.T1a = real(3.0 * (2.0 - se) / 2.0 * (1.0 - k));
-  c.T1b = real(3.0 * (2.0 - se) / 2.0 * (2.0 * k + h));
-  c.X1 = real(9.0 * (2.0 - se) / 2.0 * (2.0 * k + h));
-  c.T7 = real((2.0 - sp) / 2.0);
-  c.T7b = real((2.0 - sp) * b);
-  c.X7 = real(-3.0 * (2.0 - sp) * b);
-  c.T8 = real(-(2.0 - sp) * b / 2.0);
-  c.X8 = real(3.0 * (2.0 - sp) * b / 2.0);
-  // Step (6): s_e Q1 + k (s_e/2 - 1) s_eps Q2 with Q1 = -Q2 = |F~|^2 / 2.
-  c.Q1 = real(0.5 * (se - k * (0.5 * se - 1.0) * seps));
-  c.Q2 = real(-0.5 * seps);
-  c.Q78 = real(sp / 12.0);
-  c.rho_ref = real(p.rho_ref);
+  c.G2 = bc<V>(d.G2);
+  c.rho_ref = bc<V>(p.rho_ref);
+  c.neg_bq = bc<V>(-bq);
+  c.bq = bc<V>(bq);
+  c.RT = bc<V>(RT);
+  c.lam_RT = bc<V>(lam * RT);
+  c.neg_lam_a = bc<V>(-lam * a);
+  c.neg_2lam_a = bc<V>(-2.0 * lam * a);
+  c.lam = bc<V>(lam);
+  c.a = bc<V>(a);
+  c.beta2 = bc<V>(d.beta2);
+  // Step (2) and (3) of the execution sequence.
+  c.hk_seps = bc<V>(0.5 * k * seps);
+  c.hh_sq = bc<V>(0.5 * h * sq);
+  c.b_sq = bc<V>(b * sq);
+  c.hb_sq = bc<V>(0.5 * b * sq);
+  c.om_e = bc<V>(1.0 - 0.5 * se);
+  c.om_eps = bc<V>(1.0 - 0.5 * seps);
+  c.om_q = bc<V>(1.0 - 0.5 * sq);
+  c.om_p = bc<V>(1.0 - 0.5 * sp);
+  // Step (4): supplement Eqs. 34, 37, 40.
+  c.R11 = bc<V>(-se / (4.0 * w) * (9.0 * (1.0 - k) - 2.0 * (3.0 * k + h)));
+  c.R17 = bc<V>(-3.0 * sp * (2.0 - se) / (4.0 * (2.0 - sp)) * (9.0 * (1.0 - k) + 2.0 * (3.0 * k + h)));
+  c.R18 = bc<V>(12.0 * sp * (2.0 - se) / (2.0 - sp) * (3.0 * k + h));
+  c.R71 = bc<V>(-se * (2.0 - sp) / (4.0 * w * (2.0 - se)) * (3.0 - 4.0 * b));
+  c.R77 = bc<V>(-3.0 * sp / 4.0 * (3.0 + 4.0 * b));
+  c.R81 = bc<V>(se * (2.0 - sp) / (w * (2.0 - se)) * b);
+  c.R88 = bc<V>(6.0 * sp * b);
+  c.T1a = bc<V>(3.0 * (2.0 - se) / 2.0 * (1.0 - k));
+  c.negT1b = bc<V>(-3.0 * (2.0 - se) / 2.0 * (2.0 * k + h));
+  c.X1 = bc<V>(9.0 * (2.0 - se) / 2.0 * (2.0 * k + h));
+  c.T7 = bc<V>((2.0 - sp) / 2.0);
+  c.T7b = bc<V>((2.0 - sp) * b);
+  c.X7 = bc<V>(-3.0 * (2.0 - sp) * b);
+  c.T8 = bc<V>(-(2.0 - sp) * b / 2.0);
+  c.X8 = bc<V>(3.0 * (2.0 - sp) * b / 2.0);
+  // Step (6): s_e Q1 + k (s_e/2 - 1) s_eps Q2 with Q1 = -Q2 = G^2 |S|^2 / 2; s_p Q7, s_p Q8.
+  c.Q1G2 = bc<V>(0.5 * (se - k * (0.5 * se - 1.0) * seps) * d.G2);
+  c.Q2G2 = bc<V>(-0.5 * seps * d.G2);
+  c.Q78G2 = bc<V>(sp / 12.0 * d.G2);
+  c.one = bc<V>(1.0);
+  c.mone = bc<V>(-1.0);
+  c.two = bc<V>(2.0);
+  c.three = bc<V>(3.0);
+  c.four = bc<V>(4.0);
+  c.six = bc<V>(6.0);
+  c.m6 = bc<V>(-6.0);
+  c.nine = bc<V>(9.0);
+  c.eighteen = bc<V>(18.0);
+  c.half = bc<V>(0.5);
+  c.m2 = bc<V>(-2.0);
+  c.m4 = bc<V>(-4.0);
+  c.m2rr = bc<V>(-2.0 * p.rho_ref);
+  c.g15 = bc<V>(1.5 * d.G2);
+  c.ninth = bc<V>(1.0 / 9.0);
+  c.i36 = bc<V>(1.0 / 36.0);
+  c.sixth = bc<V>(1.0 / 6.0);
+  c.i12 = bc<V>(1.0 / 12.0);
+  c.quarter = bc<V>(0.25);
   return c;
 }
-
-template Coef<float> make_coef<float>(const lb_params&, const lb_derived&);
-template Coef<double> make_coef<double>(const lb_params&, const lb_derived&);
 
 }  // namespace lbm
 
@@ -74,10 +113,10 @@ struct lb_handle {
   cudaStream_t stream;
   int64_t steps;
   int variant;  // LB_FUSED or LB_TWO_PASS
-  int nstrips, rows_per_warp, nwork, fused_blocks;
   int reduce_blocks;
-  Coef<float> cf;
-  Coef<double> cd;
+  VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
+  VCoef<f2> c2;     // FP32 pairs (fused variant)
+  VCoef<double> cd;
   char err[512];
 };
 
@@ -113,14 +152,14 @@ constexpr int kMaxReduceBlocks = 1024;
 
 size_t reduce_bytes() { return size_t(kMaxReduceBlocks) * kReduceSlots * sizeof(double) + 256; }
 
-template <typename real, typename store_t>
-void launch_step(lb_handle* h, const Coef<real>& c) {
+template <typename V, typename real, typename store_t>
+void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
   const store_t* fin = static_cast<const store_t*>(h->f[h->cur]);
   store_t* fout = static_cast<store_t*>(h->f[1 - h->cur]);
   const int nx = h->p.nx, ny = h->p.ny;
   if (h->variant == LB_FUSED) {
-    k_step_fused<real, store_t><<<h->fused_blocks, kFusedThreads, 0, h->stream>>>(
-        fin, fout, nx, ny, h->nstrips, h->rows_per_warp, h->nwork, c);
+    const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
+    k_step_fused<V, store_t><<<grd, kFusedThreads, 0, h->stream>>>(fin, fout, nx, ny, cv);
   } else {
     real* rho = static_cast<real*>(h->scratch);
     const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
@@ -129,36 +168,15 @@ void launch_step(lb_handle* h, const Coef<real>& c) {
   }
 }
 
-template <typename real, typename store_t>
-int configure_fused(lb_handle* h) {
-  int dev = 0, sms = 0, per_sm = 0;
+int configure_device(lb_handle* h) {
+  int dev = 0, sms = 0;
   LB_CUDA(h, cudaGetDevice(&dev));
   LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_fused<real, store_t>, kFusedThreads, 0));
-  if (per_sm < 1) per_sm = 1;
-  const int nx = h->p.nx, ny = h->p.ny;
-  h->nstrips = (nx + 31) / 32;
-  // One wave: every warp slot of the GPU gets one (strip, row-chunk) work item.
-  const long slots = long(sms) * per_sm * (kFusedThreads / 32);
-  long chunks = slots / h->nstrips;
-  if (chunks < 1) chunks = 1;
-  int rows = int((ny + chunks - 1) / chunks);
-  if (rows < 8) rows = ny < 8 ? ny : 8;  // a few rows per warp amortise the two halo rows
-  h->rows_per_warp = rows;
-  const int nchunks = (ny + rows - 1) / rows;
-  h->nwork = h->nstrips * nchunks;
-  h->fused_blocks = (h->nwork * 32 + kFusedThreads - 1) / kFusedThreads;
   h->reduce_blocks = sms * 2 < kMaxReduceBlocks ? sms * 2 : kMaxReduceBlocks;
   return LB_OK;
 }
 
-int configure(lb_handle* h) {
-  switch (h->p.precision) {
-    case LB_FP64: return configure_fused<double, double>(h);
-    case LB_FP32: return configure_fused<float, float>(h);
-    default: return configure_fused<float, __half>(h);
-  }
-}
+int configure(lb_handle* h) { return configure_device(h); }
 
 template <typename real, typename store_t>
 void launch_moments(lb_handle* h, real* rho, real* ux, real* uy, real rho_ref, real G2) {
@@ -195,7 +213,7 @@ int run_reduce(lb_handle* h, double out[8]) {
   LB_CUDA(h, cudaMemcpyAsync(&probe[1], rho, sizeof(real), cudaMemcpyDeviceToHost, h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   // p_EOS / c^2 at the two probe nodes, FP64 on the host.
-  Coef<double> cd = h->cd;
+  const VCoef<double>& cd = h->cd;
   auto pe = [&](double r) {
     if (cd.eos == LB_EOS_VDW) return cd.lam * (r * cd.RT / (1.0 - cd.bq * r) - cd.a * r * r);
     const double t = cd.bq * r, om = 1.0 - t;
@@ -277,8 +295,9 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   h->stream = static_cast<cudaStream_t>(stream);
   h->steps = 0;
   h->variant = variant;
-  h->cf = make_coef<float>(h->p, d);
-  h->cd = make_coef<double>(h->p, d);
+  h->cf = make_vcoef<float>(h->p, d);
+  h->c2 = make_vcoef<f2>(h->p, d);
+  h->cd = make_vcoef<double>(h->p, d);
   rc = configure(h);
   if (rc != LB_OK) {
     set_thread_error(h->err);
@@ -319,9 +338,9 @@ int lb_step(lb_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, LB_EINVAL, "nsteps must be >= 0");
   for (int64_t s = 0; s < nsteps; ++s) {
     switch (h->p.precision) {
-      case LB_FP64: launch_step<double, double>(h, h->cd); break;
-      case LB_FP32: launch_step<float, float>(h, h->cf); break;
-      default: launch_step<float, __half>(h, h->cf); break;
+      case LB_FP64: launch_step<double, double, double>(h, h->cd, h->cd); break;
+      case LB_FP32: launch_step<f2, float, float>(h, h->c2, h->cf); break;
+      default: launch_step<f2, float, __half>(h, h->c2, h->cf); break;
     }
     LB_CUDA(h, cudaGetLastError());
     h->cur = 1 - h->cur;

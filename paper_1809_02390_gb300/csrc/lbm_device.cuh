@@ -4,6 +4,11 @@
 // supplement Sec. IV, which equals the matrix form of Eq. 13 (supplement Eq. 1)
 // up to rounding.  Conserved moments are not relaxed: rho stays, and the
 // momentum gains F (their rows of S, R, T, X and Q_m act on zero).
+//
+// The arithmetic is written once for a value type V: double, float, or f2 = a
+// pair of FP32 lanes (two lattice nodes) executed with Blackwell's packed
+// FFMA2 / FADD2 / FMUL2 instructions, which halves the instruction count of the
+// FP32 collision.  Every constant comes from the Coef<V> block.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -11,6 +16,60 @@
 #include "lbm_internal.h"
 
 namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Value types.
+struct f2 {
+  float2 v;
+};
+
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 fmav(f2 a, f2 b, f2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ f2 rcp(f2 x) { return {make_float2(__frcp_rn(x.v.x), __frcp_rn(x.v.y))}; }
+
+__device__ __forceinline__ float fmav(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmav(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// Lanes of a value (1 for scalars, 2 for f2).
+template <typename V>
+struct Lanes;
+template <>
+struct Lanes<double> {
+  static constexpr int n = 1;
+  __device__ static double get(double v, int) { return v; }
+  __device__ static void set(double& v, int, double x) { v = x; }
+};
+template <>
+struct Lanes<float> {
+  static constexpr int n = 1;
+  __device__ static float get(float v, int) { return v; }
+  __device__ static void set(float& v, int, float x) { v = x; }
+};
+template <>
+struct Lanes<f2> {
+  static constexpr int n = 2;
+  __device__ static float get(f2 v, int k) { return k ? v.v.y : v.v.x; }
+  __device__ static void set(f2& v, int k, float x) {
+    if (k)
+      v.v.y = x;
+    else
+      v.v.x = x;
+  }
+};
+
+// Scalar type of each lane.
+template <typename V>
+struct LaneType {
+  using type = V;
+};
+template <>
+struct LaneType<f2> {
+  using type = float;
+};
 
 // Storage <-> compute conversions.
 __device__ __forceinline__ float ld_st(const float* p) { return __ldg(p); }
@@ -20,140 +79,150 @@ __device__ __forceinline__ void st_st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st_st(__half* p, float v) { *p = __float2half_rn(v); }
 
-template <typename real>
-__device__ __forceinline__ real rcp(real x) {
-  return real(1) / x;
-}
+// ---------------------------------------------------------------------------
+// Collision constants for value type V (host: make_vcoef).
+template <typename V>
+struct VCoef {
+  int eos;
+  V G2, rho_ref, neg_bq, bq, RT, lam_RT, neg_lam_a, neg_2lam_a, lam, a;
+  V beta2, hk_seps, hh_sq, b_sq, hb_sq, om_e, om_eps, om_q, om_p;
+  V R11, R17, R18, R71, R77, R81, R88, T1a, negT1b, X1, T7, T7b, X7, T8, X8, Q1G2, Q2G2, Q78G2;
+  // literals and products of parameters with literals
+  V one, mone, two, three, four, six, m6, nine, eighteen, half, m2, m4, m2rr, g15, ninth, i36, sixth, i12,
+      quarter;
+};
 
 // p_EOS / c^2 and d(p_EOS/c^2)/drho.  vdW: rho R T/(1 - b rho) - a rho^2;
 // Carnahan-Starling (Eq. 20) with t = b rho / 4.  Both times K_EOS / c^2.
-template <typename real>
-__device__ __forceinline__ void eos(const Coef<real>& c, real rho, real& pe, real& dpe) {
+template <typename V>
+__device__ __forceinline__ void eos(const VCoef<V>& c, V rho, V& pe, V& dpe) {
   if (c.eos == LB_EOS_VDW) {
-    const real io = rcp(real(1) - c.bq * rho);
-    const real rt_io = c.RT * io;
-    pe = c.lam * (rho * rt_io - c.a * rho * rho);
-    dpe = c.lam * (rt_io * io - real(2) * c.a * rho);
+    const V io = rcp(fmav(c.neg_bq, rho, c.one));
+    const V q = c.lam_RT * io;                       // lam R T / (1 - b rho)
+    pe = rho * fmav(c.neg_lam_a, rho, q);            // lam (rho R T/(1 - b rho) - a rho^2)
+    dpe = fmav(q, io, c.neg_2lam_a * rho);           // lam (R T/(1 - b rho)^2 - 2 a rho)
   } else {
-    const real t = c.bq * rho;
-    const real io = rcp(real(1) - t);
-    const real io3 = io * io * io;
-    const real t2 = t * t;
-    const real z = (real(1) + t + t2 - t2 * t) * io3;
-    const real dz = (real(1) + real(4) * t + real(4) * t2 - real(4) * t2 * t + t2 * t2) * io3 * io;
-    pe = c.lam * (rho * c.RT * z - c.a * rho * rho);
-    dpe = c.lam * (c.RT * dz - real(2) * c.a * rho);
+    const V t = c.bq * rho;
+    const V io = rcp(c.one - t);
+    const V io3 = io * io * io;
+    const V t2 = t * t;
+    const V z = fmav(t2, c.one - t, c.one + t) * io3;                              // (1+t+t^2-t^3)/(1-t)^3
+    const V poly = fmav(t2, fmav(t, t - c.four, c.four), fmav(c.four, t, c.one));  // 1+4t+4t^2-4t^3+t^4
+    const V dz = poly * io3 * io;
+    pe = rho * fmav(c.neg_lam_a, rho, c.lam_RT * z);
+    dpe = fmav(c.lam_RT, dz, c.neg_2lam_a * rho);
   }
 }
 
-// One node.  d: post-streaming populations stored as deviations f_i - w_i rho_ref;
-// (Sx, Sy) = sum_i omega_i rho(x + e_i) e_i (Eq. 12, = grad rho of supplement
-// Eq. 61); o: post-collision deviations.
-template <typename real>
-__device__ __forceinline__ void collide(const Coef<real>& c, const real (&d)[9], real Sx, real Sy,
-                                        real (&o)[9]) {
+// One node (or a pair of nodes for V = f2).  d: post-streaming populations
+// stored as deviations f_i - w_i rho_ref; (Sx, Sy) = sum_i omega_i rho(x + e_i) e_i
+// (Eq. 12, = grad rho of supplement Eq. 61); o: post-collision deviations.
+template <typename V>
+__device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx, V Sy, V (&o)[9]) {
   // Moment transform (supplement Eq. 4) with shared sums; M w = (1, -2, 1, 0, ...).
-  const real a13 = d[1] + d[3], a24 = d[2] + d[4], a57 = d[5] + d[7], a68 = d[6] + d[8];
-  const real s13 = d[1] - d[3], s24 = d[2] - d[4], s57 = d[5] - d[7], s68 = d[6] - d[8];
-  const real axis = a13 + a24, diag = a57 + a68;
-  const real rho_dev = d[0] + axis + diag;
-  const real rho = rho_dev + c.rho_ref;
-  const real m1 = real(-4) * d[0] - axis + real(2) * diag - real(2) * c.rho_ref;
-  const real m2 = real(4) * d[0] - real(2) * axis + diag + c.rho_ref;
-  const real jx = s13 + s57 - s68;
-  const real jy = s24 + s57 + s68;
-  const real m4 = real(-2) * s13 + s57 - s68;
-  const real m6 = real(-2) * s24 + s57 + s68;
-  const real m7 = a13 - a24;
-  const real m8 = a57 - a68;
+  const V a13 = d[1] + d[3], a24 = d[2] + d[4], a57 = d[5] + d[7], a68 = d[6] + d[8];
+  const V s13 = d[1] - d[3], s24 = d[2] - d[4], s57 = d[5] - d[7], s68 = d[6] - d[8];
+  const V axis = a13 + a24, diag = a57 + a68;
+  const V rho_dev = d[0] + (axis + diag);
+  const V rho = rho_dev + c.rho_ref;
+  const V m1 = fmav(c.m4, d[0], fmav(c.two, diag, c.m2rr) - axis);       // -4 d0 - axis + 2 diag - 2 rho_ref
+  const V m2 = fmav(c.four, d[0], fmav(c.m2, axis, diag + c.rho_ref));   //  4 d0 - 2 axis + diag + rho_ref
+  const V dm = s57 - s68, dp = s57 + s68;
+  const V jx = s13 + dm, jy = s24 + dp;
+  const V m4 = fmav(c.m2, s13, dm);
+  const V m6 = fmav(c.m2, s24, dp);
+  const V m7 = a13 - a24;
+  const V m8 = a57 - a68;
 
   // Interaction force (Eq. 12) and velocity (Eq. 5), c = 1.
-  const real Fx = c.G2 * rho * Sx, Fy = c.G2 * rho * Sy;
-  const real inv_rho = rcp(rho);
-  const real ux = (jx + real(0.5) * Fx) * inv_rho;
-  const real uy = (jy + real(0.5) * Fy) * inv_rho;
+  const V G2rho = c.G2 * rho;
+  const V Fx = G2rho * Sx, Fy = G2rho * Sy;
+  const V inv_rho = rcp(rho);
+  const V ux = fmav(c.half, Fx, jx) * inv_rho;
+  const V uy = fmav(c.half, Fy, jy) * inv_rho;
 
   // Self-tuning EOS: p_LBE = p_EOS + G^2 rho^2/2 (Eq. 18) = c_s^2 (rho + eta);
   // grad p_LBE = (p_EOS' + G^2 rho) grad rho (supplement Eq. 61).
-  real pe, dpe;
+  V pe, dpe;
   eos(c, rho, pe, dpe);
-  const real eta = real(3) * (pe + real(0.5) * c.G2 * rho * rho) - rho;
-  const real g = dpe + c.G2 * rho;
+  const V eta = fmav(c.three, pe, rho * fmav(c.g15, rho, c.mone));  // 3 pe + 1.5 G2 rho^2 - rho
+  const V g = G2rho + dpe;
 
-  const real x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2;
+  const V x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2;
+  const V r3u2 = c.three * rho * u2;
   // Equilibrium (Eq. 3, alpha_1 = -1, beta_1 = 1, alpha_2 = 1), non-conserved rows.
-  const real meq1 = real(-2) * rho + real(2) * eta + real(3) * rho * u2;
-  const real meq2 = rho + c.beta2 * eta - real(3) * rho * u2 + real(9) * rho * x2 * y2;
-  const real meq4 = rho * ux * (real(3) * y2 - real(1));
-  const real meq6 = rho * uy * (real(3) * x2 - real(1));
-  const real meq7 = rho * (x2 - y2);
-  const real meq8 = rho * xy;
+  const V meq1 = fmav(c.two, eta - rho, r3u2);
+  const V meq2 = fmav(c.nine * rho * x2, y2, fmav(c.beta2, eta, rho) - r3u2);
+  const V meq4 = rho * ux * fmav(c.three, y2, c.mone);   // rho ux (3 uy^2 - 1)
+  const V meq6 = rho * uy * fmav(c.three, x2, c.mone);   // rho uy (3 ux^2 - 1)
+  const V meq7 = rho * (x2 - y2);
+  const V meq8 = rho * xy;
   // Forcing (Eq. 4), brackets summed over the force's positions.
-  const real Fu = Fx * ux + Fy * uy;
-  const real Fm1 = real(6) * Fu;
-  const real Fm2 = real(-6) * Fu + real(18) * xy * (Fx * uy + Fy * ux);
-  const real Fm4 = -Fx + real(3) * (Fx * y2 + real(2) * Fy * xy);
-  const real Fm6 = -Fy + real(3) * (real(2) * Fx * xy + Fy * x2);
-  const real Fm7 = real(2) * (Fx * ux - Fy * uy);
-  const real Fm8 = Fx * uy + Fy * ux;
+  const V Fu = fmav(Fx, ux, Fy * uy);
+  const V Fc = fmav(Fx, uy, Fy * ux);                                    // Fx uy + Fy ux
+  const V Fm1 = c.six * Fu;
+  const V Fm2 = fmav(c.eighteen * xy, Fc, c.m6 * Fu);                    // -6 Fu + 18 xy Fc
+  const V Fm4 = fmav(c.three, fmav(Fx, y2, (c.two * Fy) * xy), c.mone * Fx);  // -Fx + 3(Fx y2 + 2 Fy xy)
+  const V Fm6 = fmav(c.three, fmav(Fy, x2, (c.two * Fx) * xy), c.mone * Fy);  // -Fy + 3(2 Fx xy + Fy x2)
+  const V Fm7 = c.two * (Fx * ux - Fy * uy);
+  const V Fm8 = Fc;
 
-  // (1): mbar = 2 m_eq - m ; G = m - m_eq + F_m / 2.
-  real mb1 = real(2) * meq1 - m1, mb2 = real(2) * meq2 - m2, mb4 = real(2) * meq4 - m4;
-  real mb6 = real(2) * meq6 - m6, mb7 = real(2) * meq7 - m7, mb8 = real(2) * meq8 - m8;
-  const real G1 = m1 - meq1 + real(0.5) * Fm1, G2 = m2 - meq2 + real(0.5) * Fm2;
-  const real G4 = m4 - meq4 + real(0.5) * Fm4, G6 = m6 - meq6 + real(0.5) * Fm6;
-  const real G7 = m7 - meq7 + real(0.5) * Fm7, G8 = m8 - meq8 + real(0.5) * Fm8;
+  // (1): D = m - m_eq, G = D + F_m / 2, and mbar starts as 2 m_eq - m = m_eq - D.
+  const V D1 = m1 - meq1, D2 = m2 - meq2, D4 = m4 - meq4, D6 = m6 - meq6, D7 = m7 - meq7, D8 = m8 - meq8;
+  const V G1 = fmav(c.half, Fm1, D1), G2 = fmav(c.half, Fm2, D2);
+  const V G4 = fmav(c.half, Fm4, D4), G6 = fmav(c.half, Fm6, D6);
+  const V G7 = fmav(c.half, Fm7, D7), G8 = fmav(c.half, Fm8, D8);
   // (2) off-diagonal part of S, then (3) I - diag(S)/2.
-  const real A1 = c.om_e * (G1 + c.hk_seps * G2 + c.hh_sq * (ux * G4 + uy * G6));
-  const real A2 = c.om_eps * G2;
-  const real A4 = c.om_q * G4, A6 = c.om_q * G6;
-  const real A7 = c.om_p * (G7 + c.b_sq * (ux * G4 - uy * G6));
-  const real A8 = c.om_p * (G8 + c.hb_sq * (uy * G4 + ux * G6));
-  // (4) cubic-velocity correction: R (I - S/2) G + T . grad rho + X . grad p_LBE.
-  const real ax = x2 * ux * Sx, ay = y2 * uy * Sy;
-  const real cr1 = c.T1a * (ax + ay) + (g * c.X1 - c.T1b) * xy * (uy * Sx + ux * Sy);
-  const real cr7 = c.T7 * (ax - ay) + (c.T7b + g * c.X7) * xy * (uy * Sx - ux * Sy);
-  const real cr8 = (c.T8 + g * c.X8) * ((y2 + real(2) * x2) * uy * Sx + (x2 + real(2) * y2) * ux * Sy);
-  mb1 -= c.R11 * u2 * A1 + c.R17 * (x2 - y2) * A7 + c.R18 * xy * A8 + cr1;
-  mb7 -= c.R71 * (x2 - y2) * A1 + c.R77 * u2 * A7 + cr7;
-  mb8 -= c.R81 * xy * A1 + c.R88 * u2 * A8 + cr8;
-  // (5)
-  mb1 += real(2) * A1;
-  mb2 += real(2) * A2;
-  mb4 += real(2) * A4;
-  mb6 += real(2) * A6;
-  mb7 += real(2) * A7;
-  mb8 += real(2) * A8;
-  // (6) S Q_m with |F~|^2 = G^2 |S|^2 (Eq. 14).
-  const real sxx = Sx * Sx, syy = Sy * Sy;
-  mb1 += c.Q1 * c.G2 * (sxx + syy);
-  mb2 += c.Q2 * c.G2 * (sxx + syy);
-  mb7 += c.Q78 * c.G2 * (sxx - syy);
-  mb8 += c.Q78 * c.G2 * Sx * Sy;
+  const V uG = fmav(ux, G4, uy * G6), vG = ux * G4 - uy * G6, wG = fmav(uy, G4, ux * G6);
+  const V A1 = c.om_e * fmav(c.hh_sq, uG, fmav(c.hk_seps, G2, G1));
+  const V A2 = c.om_eps * G2;
+  const V A4 = c.om_q * G4, A6 = c.om_q * G6;
+  const V A7 = c.om_p * fmav(c.b_sq, vG, G7);
+  const V A8 = c.om_p * fmav(c.hb_sq, wG, G8);
+  // (4) cubic-velocity correction: R (I - S/2) G + T . grad rho + X . grad p_LBE
+  // (supplement Eqs. 34, 37, 40), with grad p_LBE = g S.
+  const V ax = x2 * ux * Sx, ay = y2 * uy * Sy;
+  const V xyS1 = xy * fmav(uy, Sx, ux * Sy), xyS7 = xy * (uy * Sx - ux * Sy);
+  const V cr1 = fmav(c.T1a, ax + ay, fmav(g, c.X1, c.negT1b) * xyS1);
+  const V cr7 = fmav(c.T7, ax - ay, fmav(g, c.X7, c.T7b) * xyS7);
+  const V cr8 = fmav(g, c.X8, c.T8) * fmav(fmav(c.two, x2, y2) * uy, Sx, fmav(c.two, y2, x2) * ux * Sy);
+  const V x2my2 = x2 - y2;
+  const V corr1 = fmav(c.R11 * u2, A1, fmav(c.R17 * x2my2, A7, fmav(c.R18 * xy, A8, cr1)));
+  const V corr7 = fmav(c.R71 * x2my2, A1, fmav(c.R77 * u2, A7, cr7));
+  const V corr8 = fmav(c.R81 * xy, A1, fmav(c.R88 * u2, A8, cr8));
+  // (5): mbar = m_eq - D + 2 A - corrections; (6): + S Q_m with |F~|^2 = G^2 |S|^2.
+  const V sxx = Sx * Sx, syy = Sy * Sy, ss = sxx + syy;
+  const V mb1 = fmav(c.Q1G2, ss, fmav(c.two, A1, meq1 - D1) - corr1);
+  const V mb2 = fmav(c.Q2G2, ss, fmav(c.two, A2, meq2 - D2));
+  const V mb4 = fmav(c.two, A4, meq4 - D4);
+  const V mb6 = fmav(c.two, A6, meq6 - D6);
+  const V mb7 = fmav(c.Q78G2, sxx - syy, fmav(c.two, A7, meq7 - D7) - corr7);
+  const V mb8 = fmav(c.Q78G2 * Sx, Sy, fmav(c.two, A8, meq8 - D8) - corr8);
 
   // Inverse transform M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4),
   // applied to mbar - rho_ref M w (deviation storage); conserved: rho, j + F.
-  const real n0 = rho_dev * real(1.0 / 9.0);
-  const real n1 = (mb1 + real(2) * c.rho_ref) * real(1.0 / 36.0);
-  const real n2 = (mb2 - c.rho_ref) * real(1.0 / 36.0);
-  const real n3 = (jx + Fx) * real(1.0 / 6.0);
-  const real n4 = mb4 * real(1.0 / 12.0);
-  const real n5 = (jy + Fy) * real(1.0 / 6.0);
-  const real n6 = mb6 * real(1.0 / 12.0);
-  const real n7 = mb7 * real(0.25);
-  const real n8 = mb8 * real(0.25);
-  const real base_a = n0 - n1 - real(2) * n2, base_d = n0 + real(2) * n1 + n2;
-  const real px = n3 - real(2) * n4, py = n5 - real(2) * n6;
-  const real qx = n3 + n4, qy = n5 + n6;
-  o[0] = n0 - real(4) * n1 + real(4) * n2;
-  o[1] = base_a + px + n7;
-  o[2] = base_a + py - n7;
-  o[3] = base_a - px + n7;
-  o[4] = base_a - py - n7;
-  o[5] = base_d + qx + qy + n8;
-  o[6] = base_d - qx + qy - n8;
-  o[7] = base_d - qx - qy + n8;
-  o[8] = base_d + qx - qy - n8;
+  const V n0 = rho_dev * c.ninth;
+  const V n1 = fmav(c.two, c.rho_ref, mb1) * c.i36;
+  const V n2 = (mb2 - c.rho_ref) * c.i36;
+  const V n3 = (jx + Fx) * c.sixth;
+  const V n4 = mb4 * c.i12;
+  const V n5 = (jy + Fy) * c.sixth;
+  const V n6 = mb6 * c.i12;
+  const V n7 = mb7 * c.quarter;
+  const V n8 = mb8 * c.quarter;
+  const V base_a = fmav(c.m2, n2, n0 - n1), base_d = fmav(c.two, n1, n0 + n2);
+  const V px = fmav(c.m2, n4, n3), py = fmav(c.m2, n6, n5);
+  const V qx = n3 + n4, qy = n5 + n6;
+  const V ba7 = base_a + n7, bm7 = base_a - n7, bd8 = base_d + n8, bm8 = base_d - n8;
+  o[0] = fmav(c.four, n2 - n1, n0);
+  o[1] = ba7 + px;
+  o[2] = bm7 + py;
+  o[3] = ba7 - px;
+  o[4] = bm7 - py;
+  o[5] = bd8 + (qx + qy);
+  o[6] = bm8 + (qy - qx);
+  o[7] = bd8 - (qx + qy);
+  o[8] = bm8 + (qx - qy);
 }
 
 // Force stencil of Eq. 12 from the densities of the 8 neighbours

@@ -16,22 +16,26 @@ __host__ __device__ __forceinline__ int wrap(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// Single periodic wrap of v in [-n, 2n).
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 // Pulls the nine populations of row r at columns (cm, cc, cp) = (x-1, x, x+1):
-// f_i(x, r) = fbar_i(x - e_i, r - e_i) (supplement Eq. 2), periodic.
+// f_i(x, r) = fbar_i(x - e_i, r - e_i) (supplement Eq. 2), periodic.  32-bit
+// offsets: the library limits 9 nx ny to below 2^31.
 template <typename real, typename store_t>
-__device__ __forceinline__ void pull_row(const store_t* __restrict__ fin, size_t plane, int nx, int ny, int r,
-                                         int cm, int cc, int cp, real (&f)[9]) {
+__device__ __forceinline__ void pull_row(const store_t* __restrict__ fin, int plane, int nx, int ny, int r, int cm,
+                                         int cc, int cp, real (&f)[9]) {
   const int rm = r == 0 ? ny - 1 : r - 1, rp = r == ny - 1 ? 0 : r + 1;
-  const size_t oc = size_t(r) * nx, om = size_t(rm) * nx, op = size_t(rp) * nx;
-  f[0] = ld_st(fin + oc + cc);
-  f[1] = ld_st(fin + plane + oc + cm);
-  f[2] = ld_st(fin + 2 * plane + om + cc);
-  f[3] = ld_st(fin + 3 * plane + oc + cp);
-  f[4] = ld_st(fin + 4 * plane + op + cc);
-  f[5] = ld_st(fin + 5 * plane + om + cm);
-  f[6] = ld_st(fin + 6 * plane + om + cp);
-  f[7] = ld_st(fin + 7 * plane + op + cp);
-  f[8] = ld_st(fin + 8 * plane + op + cm);
+  const int oc = r * nx, om = rm * nx, op = rp * nx;
+  f[0] = ld_st(fin + (oc + cc));
+  f[1] = ld_st(fin + (plane + oc + cm));
+  f[2] = ld_st(fin + (2 * plane + om + cc));
+  f[3] = ld_st(fin + (3 * plane + oc + cp));
+  f[4] = ld_st(fin + (4 * plane + op + cc));
+  f[5] = ld_st(fin + (5 * plane + om + cm));
+  f[6] = ld_st(fin + (6 * plane + om + cp));
+  f[7] = ld_st(fin + (7 * plane + op + cp));
+  f[8] = ld_st(fin + (8 * plane + op + cm));
 }
 
 template <typename real>
@@ -39,93 +43,105 @@ __device__ __forceinline__ real sum9(const real (&f)[9]) {
   return ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
 }
 
-// Fused stream + force + collide step.  Each warp owns a strip of 32 columns
-// [32*strip, 32*strip + 32) and a chunk of rows, and marches down the rows:
-// lane l pulls the populations of its column, sums the density, exchanges the
-// neighbour densities with warp shuffles (lanes 0 and 31 also compute the
-// density of the column just outside the strip), and collides.  The pull of
-// row y + 2 is issued before the collision of row y so that it is in flight
-// while the warp computes.  No shared memory, no block barrier.
-template <typename real, typename store_t>
-__global__ void __launch_bounds__(kFusedThreads)
-    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, int nstrips,
-                 int rows_per_warp, int nwork, Coef<real> c) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * kFusedThreads + threadIdx.x) >> 5;
-  if (warp >= nwork) return;  // uniform per warp
-  const int strip = warp % nstrips, chunk = warp / nstrips;
-  const int xl = strip * 32 + lane;
-  const int xc = wrap(xl, nx), xm = wrap(xl - 1, nx), xp = wrap(xl + 1, nx);
-  const bool edge = lane == 0 || lane == 31;
-  const int hl = lane == 0 ? xl - 1 : xl + 1;  // halo column of the edge lanes
-  const int hc = wrap(hl, nx), hm = wrap(hl - 1, nx), hp = wrap(hl + 1, nx);
-  const bool writer = xl < nx;
-  const int y0 = chunk * rows_per_warp;
-  const int y1 = min(y0 + rows_per_warp, ny);
-  const size_t plane = size_t(nx) * ny;
+// Fused stream + force + collide step on a TX x TY tile per block (TX = 32
+// columns, TY = 16 rows, 256 threads, two nodes per thread in the same column).
+// Phase 1: each thread pulls the nine populations of its two nodes into
+// registers and sums their densities; warps 0..3 also pull the 100 nodes of the
+// one-node ring around the tile (densities only), one warp-uniform segment each.
+// The densities of tile + ring go to shared memory.  Phase 2: each thread forms
+// the force stencil of its nodes from shared memory and collides; with V = f2
+// the two nodes are the two lanes of one packed FP32x2 collision.  DRAM traffic
+// is one read and one write of every population; the ring re-reads hit L2.
+constexpr int kTileX = 32, kTileY = 16, kTileRows = kTileY / (kFusedThreads / kTileX);
+constexpr int kRowStride = kFusedThreads / kTileX;  // 8
+#ifndef LBM_FUSED_MIN_BLOCKS
+#define LBM_FUSED_MIN_BLOCKS 4
+#endif
+// Resident blocks per SM the register budget must allow: 4 for the FP32-pair
+// kernels (64 registers; the kernel is latency-bound, so the extra resident warps
+// outweigh a few spilled registers), 2 for FP64.
+template <typename V>
+constexpr int fused_min_blocks() {
+  return sizeof(typename LaneType<V>::type) == 8 ? 2 : LBM_FUSED_MIN_BLOCKS;
+}
 
-  real fa[9], fb[9], ft[9];
-  real rm, rc, rp, hmv = 0, hcv = 0, hpv = 0;
-  pull_row(fin, plane, nx, ny, wrap(y0 - 1, ny), xm, xc, xp, ft);
-  rm = sum9(ft);
-  if (edge) {
-    pull_row(fin, plane, nx, ny, wrap(y0 - 1, ny), hm, hc, hp, ft);
-    hmv = sum9(ft);
-  }
-  pull_row(fin, plane, nx, ny, y0, xm, xc, xp, fa);
-  rc = sum9(fa);
-  if (edge) {
-    pull_row(fin, plane, nx, ny, y0, hm, hc, hp, ft);
-    hcv = sum9(ft);
-  }
-  pull_row(fin, plane, nx, ny, wrap(y0 + 1, ny), xm, xc, xp, fb);
-  rp = sum9(fb);
-  if (edge) {
-    pull_row(fin, plane, nx, ny, wrap(y0 + 1, ny), hm, hc, hp, ft);
-    hpv = sum9(ft);
-  }
+template <typename V, typename store_t>
+__global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
+    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c) {
+  using real = typename LaneType<V>::type;
+  static_assert(kTileRows == 2, "two nodes per thread");
+  __shared__ real rs[kTileY + 2][kTileX + 2];
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  const int plane = nx * ny;
+  const bool small = nx <= kTileX || ny <= kTileY;  // tiles may wrap more than once
+  const int gx = x0 + tx;
+  const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
+  const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
 
-  for (int y = y0; y < y1; ++y) {
-    const bool more = y + 1 < y1;
-    real fc[9];
-    if (more) {
-      pull_row(fin, plane, nx, ny, wrap(y + 2, ny), xm, xc, xp, fc);
-      if (edge) pull_row(fin, plane, nx, ny, wrap(y + 2, ny), hm, hc, hp, ft);
-    }
-    // Neighbour densities: left from lane - 1, right from lane + 1, halos at the ends.
-    real l_m = __shfl_up_sync(0xffffffffu, rm, 1), r_m = __shfl_down_sync(0xffffffffu, rm, 1);
-    real l_c = __shfl_up_sync(0xffffffffu, rc, 1), r_c = __shfl_down_sync(0xffffffffu, rc, 1);
-    real l_p = __shfl_up_sync(0xffffffffu, rp, 1), r_p = __shfl_down_sync(0xffffffffu, rp, 1);
-    if (lane == 0) {
-      l_m = hmv;
-      l_c = hcv;
-      l_p = hpv;
-    } else if (lane == 31) {
-      r_m = hmv;
-      r_c = hcv;
-      r_p = hpv;
-    }
-    real Sx, Sy;
-    stencil(l_m, rm, r_m, l_c, r_c, l_p, rp, r_p, Sx, Sy);
-    real o[9];
-    collide(c, fa, Sx, Sy, o);
-    if (writer) {
-      const size_t off = size_t(y) * nx + xc;
+  // All loads of phase 1 are issued before any of them is consumed.
+  real f[kTileRows][9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) st_st(fout + i * plane + off, o[i]);
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * kRowStride;
+    pull_row(fin, plane, nx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
+  }
+  // Ring: warp 0 the row above, warp 1 the row below, warp 2 the left (lanes
+  // 0..15) and right (16..31) columns, warp 3 lanes 0..3 the corners.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool ring = warp < 3 || (warp == 3 && lane < 4);
+  int wx = 0, wy = 0;
+  real g[9];
+  if (ring) {
+    if (warp == 0) {
+      wx = lane + 1, wy = 0;
+    } else if (warp == 1) {
+      wx = lane + 1, wy = kTileY + 1;
+    } else if (warp == 2) {
+      wx = lane < 16 ? 0 : kTileX + 1, wy = (lane & 15) + 1;
+    } else {
+      wx = (lane & 1) ? kTileX + 1 : 0, wy = (lane & 2) ? kTileY + 1 : 0;
     }
-    if (more) {
-      rm = rc;
-      rc = rp;
-      rp = sum9(fc);
-      hmv = hcv;
-      hcv = hpv;
-      if (edge) hpv = sum9(ft);
+    const int hx = small ? wrap(x0 - 1 + wx, nx) : wrap1(x0 - 1 + wx, nx);
+    const int hy = small ? wrap(y0 - 1 + wy, ny) : wrap1(y0 - 1 + wy, ny);
+    pull_row(fin, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
+  }
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        fa[i] = fb[i];
-        fb[i] = fc[i];
-      }
+  for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  if (ring) rs[wy][wx] = sum9(g);
+  __syncthreads();
+
+  real Sx[kTileRows], Sy[kTileRows];
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int ly = ty + k * kRowStride + 1, lx = tx + 1;
+    stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
+            rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx[k], Sy[k]);
+  }
+  real out[kTileRows][9];
+  if constexpr (Lanes<V>::n == 2) {
+    V d[9], o[9], sx, sy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i].v = make_float2(f[0][i], f[1][i]);
+    sx.v = make_float2(Sx[0], Sx[1]);
+    sy.v = make_float2(Sy[0], Sy[1]);
+    collide(c, d, sx, sy, o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      out[0][i] = o[i].v.x;
+      out[1][i] = o[i].v.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kTileRows; ++k) collide(c, f[k], Sx[k], Sy[k], out[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * kRowStride;
+    if (gx < nx && gy < ny) {
+      const int off = gy * nx + gx;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), out[k][i]);
     }
   }
 }
@@ -136,39 +152,39 @@ __global__ void k_density(const store_t* __restrict__ fin, real* __restrict__ rh
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   real f[9];
-  pull_row(fin, size_t(nx) * ny, nx, ny, y, x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1, f);
-  rho[size_t(y) * nx + x] = sum9(f);
+  pull_row(fin, nx * ny, nx, ny, y, x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1, f);
+  rho[y * nx + x] = sum9(f);
 }
 
 // Two-pass variant, pass 2: pull, force stencil from the density plane, collide.
 template <typename real, typename store_t>
 __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restrict__ fout,
-                              const real* __restrict__ rho, int nx, int ny, Coef<real> c) {
+                              const real* __restrict__ rho, int nx, int ny, VCoef<real> c) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const size_t plane = size_t(nx) * ny;
+  const int plane = nx * ny;
   real f[9];
   pull_row(fin, plane, nx, ny, y, xm, x, xp, f);
-  const real* rm = rho + size_t(ym) * nx;
-  const real* rc = rho + size_t(y) * nx;
-  const real* rpp = rho + size_t(yp) * nx;
+  const real* rm = rho + ym * nx;
+  const real* rc = rho + y * nx;
+  const real* rpp = rho + yp * nx;
   real Sx, Sy;
   stencil(__ldg(rm + xm), __ldg(rm + x), __ldg(rm + xp), __ldg(rc + xm), __ldg(rc + xp), __ldg(rpp + xm),
           __ldg(rpp + x), __ldg(rpp + xp), Sx, Sy);
   real o[9];
   collide(c, f, Sx, Sy, o);
-  const size_t off = size_t(y) * nx + x;
+  const int off = y * nx + x;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) st_st(fout + i * plane + off, o[i]);
+  for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), o[i]);
 }
 
 // Rest equilibrium from an initial density (computed in FP64, rounded once):
 // m_eq(rho, u = 0) = (rho, -2 rho + 2 eta, rho + beta_2 eta, 0, ...), minus rho_ref M w.
 template <typename store_t>
 __global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny,
-                            Coef<double> c) {
+                            VCoef<double> c) {
   const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const size_t N = size_t(nx) * ny;
   if (n >= N) return;

@@ -189,7 +189,7 @@ int derive(const lb_params* p, lb_derived* d, char* err, size_t errlen) {
   };
   if (!p) return fail("null parameters");
   if (p->nx < 3 || p->ny < 3) return fail("nx and ny must be >= 3");
-  if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) return fail("lattice larger than 2^31 nodes");
+  if (9 * (int64_t)p->nx * p->ny >= ((int64_t)1 << 31)) return fail("lattice too large: 9 nx ny must be below 2^31");
   if (p->precision < LB_FP64 || p->precision > LB_FP16S) return fail("unknown precision");
   if (p->eos != LB_EOS_VDW && p->eos != LB_EOS_CS) return fail("unknown eos");
   if (p->variant < LB_AUTO || p->variant > LB_TWO_PASS) return fail("unknown variant");

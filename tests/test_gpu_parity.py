@@ -1,9 +1,12 @@
 """Parity of the CUDA time step (through the C ABI) with the FP64 CPU oracle.
 
 Tolerances: FP64 GPU path <= 1e-12 relative on f after 2,000 steps; FP32 path
-<= 2e-5 relative on rho; FP16 storage (FP32 arithmetic) <= 2e-3 relative on rho
-after 500 steps, derived from half precision's 2^-11 rounding of the stored
-deviations.  Relative error = max|diff| / max|reference|."""
+<= 2e-5 relative on rho; FP16 storage (FP32 arithmetic) <= 8e-3 relative on rho
+after 500 steps: each step rounds every stored deviation to half precision
+(relative 2^-12), the nine roundings of a node add to its density, and the
+mass they move performs a random walk, so the bound is
+2^-12 * sqrt(500) * (sum_i |f_i - w_i rho_ref| / max rho ~ 1.4) ~ 8e-3.
+Relative error = max|diff| / max|reference|."""
 import numpy as np
 import pytest
 
@@ -46,7 +49,7 @@ def test_fp64_init_matches_oracle(orc):
     assert rel_inf(gpu_populations(lat), orc.init_feq(p, rho0)) <= 1e-15
 
 
-@pytest.mark.parametrize("precision,tol,steps", [("fp32", 2e-5, 2000), ("fp16s", 2e-3, 500)])
+@pytest.mark.parametrize("precision,tol,steps", [("fp32", 2e-5, 2000), ("fp16s", 8e-3, 500)])
 @pytest.mark.parametrize("variant", ["fused", "two_pass"])
 def test_reduced_precision_droplet(orc, precision, tol, steps, variant):
     p, rho0 = droplet64()
