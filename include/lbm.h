@@ -149,6 +149,26 @@ int lb_moments(lb_handle* h, void* rho, void* ux, void* uy);
  * not finite (the values are still written). */
 int lb_reduce(lb_handle* h, double out[8]);
 
+/* lb_reduce for callers that cannot allocate device memory (the paper has no
+ * counterpart).  Such callers exist: a host program whose allocator owns the whole
+ * GPU and grants no further buffers, a plugin inside such a program, or code that
+ * runs while a stream is captured into a CUDA graph, where an allocation would
+ * break the capture.  Same results as lb_reduce (same kernels, same order), but the
+ * scratch is a file-scope static device array inside the library, of
+ * LB_REDUCE_STATIC_MAX_NODES * 8 + 65600 bytes (about 8.1 MB), which every GPU
+ * that loads the library holds until the process exits.  Nothing is allocated:
+ * no cudaMalloc / cudaFree, no allocating library routine.  The handle may have
+ * been created with scratch = NULL.
+ * Limits: lattices above LB_REDUCE_STATIC_MAX_NODES nodes are rejected with
+ * LB_ENOMEM (use lb_reduce).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  All calls share the one array and each
+ * call writes every element it reads, so nothing carries over between calls, but
+ * calls whose GPU work overlaps (several streams or threads at once) race on it
+ * and must be serialised by the caller.  Synchronous like lb_reduce. */
+#define LB_REDUCE_STATIC_MAX_NODES 1048576
+int lb_reduce_static(lb_handle* h, double out[8]);
+
 /* Copies the current state to / from a caller device buffer of lb_state_bytes(). */
 int lb_get_state(lb_handle* h, void* dst);
 int lb_set_state(lb_handle* h, const void* src);

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("lb_steps_done", ctypes.c_int64, [_V]),
     ("lb_moments", ctypes.c_int, [_V, _V, _V, _V]),
     ("lb_reduce", ctypes.c_int, [_V, _D]),
+    ("lb_reduce_static", ctypes.c_int, [_V, _D]),
     ("lb_get_state", ctypes.c_int, [_V, _V]),
     ("lb_set_state", ctypes.c_int, [_V, _V]),
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
@@ -145,6 +146,15 @@ def lb_reduce(h: int) -> list[float]:
     if rc not in (LB_OK, LB_ENONFINITE):
         check(rc, h)
     return vals if rc == LB_OK else check(rc, h)
+
+
+def lb_reduce_static(h: int) -> list[float]:
+    """lb_reduce with the library's static device scratch (no allocation anywhere)."""
+    out = (ctypes.c_double * 8)()
+    rc = lib().lb_reduce_static(h, out)
+    if rc not in (LB_OK, LB_ENONFINITE):
+        check(rc, h)
+    return list(out) if rc == LB_OK else check(rc, h)
 
 
 def lb_get_state(h: int, dst: int) -> None:

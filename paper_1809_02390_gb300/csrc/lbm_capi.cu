@@ -8,7 +8,7 @@
 #include <cstring>
 #include <new>
 
-#include "lbm_kernels.cuh"
+#include "lbm_handle.cuh"
 
 namespace lbm {
 
@@ -102,23 +102,6 @@ VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d) {
 }  // namespace lbm
 
 using namespace lbm;
-
-struct lb_handle {
-  lb_params p;
-  lb_derived d;
-  void* f[2];
-  int cur;
-  void* scratch;
-  size_t scratch_bytes;
-  cudaStream_t stream;
-  int64_t steps;
-  int variant;  // LB_FUSED or LB_TWO_PASS
-  int reduce_blocks;
-  VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
-  VCoef<f2> c2;     // FP32 pairs (fused variant)
-  VCoef<double> cd;
-  char err[512];
-};
 
 namespace {
 

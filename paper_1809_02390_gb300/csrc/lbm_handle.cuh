@@ -1,0 +1,24 @@
+// Handle of one lattice (shared by the library's CUDA translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+struct lb_handle {
+  lb_params p;
+  lb_derived d;
+  void* f[2];
+  int cur;
+  void* scratch;
+  size_t scratch_bytes;
+  cudaStream_t stream;
+  int64_t steps;
+  int variant;  // LB_FUSED or LB_TWO_PASS
+  int reduce_blocks;
+  lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
+  lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
+  lbm::VCoef<double> cd;
+  char err[512];
+};
+

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kReduceThreads)
 }
 
 // Folds the block partials in a fixed order (deterministic) into out[kReduceSlots].
-__global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+static __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
   const int k = threadIdx.x;
   if (k >= kReduceSlots) return;
   double v = partial[k];
