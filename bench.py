@@ -35,7 +35,10 @@ BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 popula
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
 # for the kernel sources they were measured on (sha256 of the files below).
 KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_02390_gb300/csrc/lbm_device.cuh"]
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 2048^2 capture (profiles/k_step_fused_fp32_2048_full.md) scaled x4 to 4096^2.
+    ("k_step_fused<float,float>", "a72ef00d530669bb"): 1075540000,
+}
 
 
 def kernel_source_hash() -> str:
