@@ -169,6 +169,27 @@ int lb_reduce(lb_handle* h, double out[8]);
 #define LB_REDUCE_STATIC_MAX_NODES 1048576
 int lb_reduce_static(lb_handle* h, double out[8]);
 
+/* Bytes of device scratch lb_adjoint_step needs: 11 planes of the compute type
+ * (the population cotangents mu and the force-stencil cotangent) plus FP64
+ * per-block partial sums of the parameter gradient. */
+size_t lb_adjoint_scratch_bytes(const lb_params* p);
+
+/* Adjoint (transposed Jacobian) of one time step.  The forward step maps the
+ * post-collision state s to s' = Phi(s; theta): pull streaming (supplement
+ * Eq. 2), rho, the force stencil of Eq. 12, the collision of Eq. 13 (execution
+ * sequence of supplement Sec. IV).  Given lam_in = dL/ds' this computes
+ * lam_out = (dPhi/ds)^T lam_in: the collision's vector-Jacobian product at every
+ * node (hand-written reverse of the sequence, including the EOS, the force, S(u),
+ * R(u), T(u), X(u) and Q_m), the transposed force stencil and the transposed pull.
+ * dtheta (device, 3 doubles, or NULL) accumulates dL/dT, dL/dG2, dL/dlam, with
+ * T the temperature, G2 = G^2/c^2 and lam = K_EOS/c^2 as in lb_derived.
+ * f_state: the state s the step started from (storage type of the handle);
+ * lam_in, lam_out: [9][ny][nx] device arrays in the compute type (double for
+ * LB_FP64, float for LB_FP32), distinct.  Uses the handle's parameters and stream,
+ * not its current state.  LB_ENOTSUP for LB_FP16S, LB_ENOMEM for a short scratch. */
+int lb_adjoint_step(lb_handle* h, const void* f_state, const void* lam_in, void* lam_out, double* dtheta,
+                    void* scratch, size_t scratch_bytes);
+
 /* Copies the current state to / from a caller device buffer of lb_state_bytes(). */
 int lb_get_state(lb_handle* h, void* dst);
 int lb_set_state(lb_handle* h, const void* src);

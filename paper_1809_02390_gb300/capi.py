@@ -61,6 +61,8 @@ SIGNATURES = [
     ("lb_moments", ctypes.c_int, [_V, _V, _V, _V]),
     ("lb_reduce", ctypes.c_int, [_V, _D]),
     ("lb_reduce_static", ctypes.c_int, [_V, _D]),
+    ("lb_adjoint_scratch_bytes", ctypes.c_size_t, [_P]),
+    ("lb_adjoint_step", ctypes.c_int, [_V, _V, _V, _V, _V, _V, ctypes.c_size_t]),
     ("lb_get_state", ctypes.c_int, [_V, _V]),
     ("lb_set_state", ctypes.c_int, [_V, _V]),
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
@@ -155,6 +157,15 @@ def lb_reduce_static(h: int) -> list[float]:
     if rc not in (LB_OK, LB_ENONFINITE):
         check(rc, h)
     return list(out) if rc == LB_OK else check(rc, h)
+
+
+def lb_adjoint_scratch_bytes(p: lb_params) -> int:
+    return lib().lb_adjoint_scratch_bytes(ctypes.byref(p))
+
+
+def lb_adjoint_step(h: int, f_state: int, lam_in: int, lam_out: int, dtheta: int | None, scratch: int,
+                    scratch_bytes: int) -> None:
+    check(lib().lb_adjoint_step(h, f_state, lam_in, lam_out, dtheta, scratch, scratch_bytes), h)
 
 
 def lb_get_state(h: int, dst: int) -> None:

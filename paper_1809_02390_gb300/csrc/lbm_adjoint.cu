@@ -1,0 +1,232 @@
+// Adjoint of one time step (lb_adjoint_step).
+//
+// Forward step: f = pull(s) (supplement Eq. 2), rho = sum_i f_i, S(x) = sum_j
+// omega_j rho(x + e_j) e_j (Eq. 12), s'(x) = C(f(x), S(x); theta) (Eq. 13).
+// Given lam' = dL/ds', the adjoint is
+//   (mu, Sb, thetab)(x) = VJP of C at (f(x), S(x)) with lam'(x)      [k_adj_local]
+//   rhob(y) = sum_j omega_j e_j . Sb(y - e_j)        (transposed stencil)
+//   lam_i(z) = mu_i(z + e_i) + rhob(z + e_i)         (transposed pull) [k_adj_transpose]
+// and dL/dtheta += sum_x thetab(x), reduced per block in FP64, folded in a
+// fixed order (deterministic).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "lbm_adjoint.cuh"
+#include "lbm_handle.cuh"
+
+namespace {
+
+using namespace lbm;
+
+constexpr int kAdjThreads = 256;
+
+template <typename real, typename store_t>
+__global__ void __launch_bounds__(kAdjThreads)
+    k_adj_local(const store_t* __restrict__ s, const real* __restrict__ lam_in, real* __restrict__ mu,
+                real* __restrict__ sbar, double* __restrict__ partial, int nx, int ny, VCoef<real> c) {
+  __shared__ real rs[kTileY + 2][kTileX + 2];
+  __shared__ double red[kAdjThreads / 32][3];
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  const int plane = nx * ny;
+  const int gx = x0 + tx;
+  const int xc = wrap(gx, nx);
+  const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
+  real f[kTileRows][9];
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * kRowStride;
+    pull_row(s, plane, nx, ny, wrap(gy, ny), xm, xc, xp, f[k]);
+    rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  }
+  for (int t = threadIdx.x; t < 2 * (kTileX + 2) + 2 * kTileY; t += kAdjThreads) {
+    int wx, wy;
+    if (t < kTileX + 2) {
+      wx = t, wy = 0;
+    } else if (t < 2 * (kTileX + 2)) {
+      wx = t - (kTileX + 2), wy = kTileY + 1;
+    } else if (t < 2 * (kTileX + 2) + kTileY) {
+      wx = 0, wy = t - 2 * (kTileX + 2) + 1;
+    } else {
+      wx = kTileX + 1, wy = t - 2 * (kTileX + 2) - kTileY + 1;
+    }
+    const int hx = wrap(x0 - 1 + wx, nx), hy = wrap(y0 - 1 + wy, ny);
+    real g[9];
+    pull_row(s, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
+    rs[wy][wx] = sum9(g);
+  }
+  __syncthreads();
+  double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int ly = ty + k * kRowStride + 1, lx = tx + 1;
+    const int gy = y0 + ly - 1;
+    if (gx >= nx || gy >= ny) continue;
+    real Sx, Sy;
+    stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
+            rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx, Sy);
+    const int off = gy * nx + gx;
+    real ob[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ob[i] = lam_in[i * plane + off];
+    AdjOut<real> r;
+    collide_vjp(c, f[k], Sx, Sy, ob, r);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i * plane + off] = r.d[i];
+    sbar[off] = r.Sx;
+    sbar[plane + off] = r.Sy;
+    acc[0] += double(r.RT);
+    acc[1] += double(r.G2);
+    acc[2] += double(r.lam);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) red[w][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int j = 0; j < kAdjThreads / 32; ++j) v += red[j][threadIdx.x];
+    partial[(size_t(blockIdx.y) * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = v;
+  }
+}
+
+// rhob(y) = sum_j omega_j e_j . Sb(y - e_j), read from the two Sb planes.
+template <typename real>
+__device__ __forceinline__ real stencil_t(const real* __restrict__ sbar, int plane, int nx, int ny, int x, int y) {
+  const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const real* bx = sbar;
+  const real* by = sbar + plane;
+  const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0);
+  const real ax = bx[y * nx + xm] - bx[y * nx + xp];
+  const real ay = by[ym * nx + x] - by[yp * nx + x];
+  const real d5 = bx[ym * nx + xm] + by[ym * nx + xm];   // e = (+1, +1) from (x-1, y-1)
+  const real d6 = by[ym * nx + xp] - bx[ym * nx + xp];   // e = (-1, +1) from (x+1, y-1)
+  const real d7 = -bx[yp * nx + xp] - by[yp * nx + xp];  // e = (-1, -1) from (x+1, y+1)
+  const real d8 = bx[yp * nx + xm] - by[yp * nx + xm];   // e = (+1, -1) from (x-1, y+1)
+  return third * (ax + ay) + twelfth * ((d5 + d6) + (d7 + d8));
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kAdjThreads)
+    k_adj_transpose(const real* __restrict__ mu, const real* __restrict__ sbar, real* __restrict__ lam_out, int nx,
+                    int ny) {
+  __shared__ real rb[kTileY + 2][kTileX + 2];
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  const int plane = nx * ny;
+  for (int t = threadIdx.x; t < (kTileY + 2) * (kTileX + 2); t += kAdjThreads) {
+    const int wy = t / (kTileX + 2), wx = t - wy * (kTileX + 2);
+    rb[wy][wx] = stencil_t(sbar, plane, nx, ny, wrap(x0 - 1 + wx, nx), wrap(y0 - 1 + wy, ny));
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int gx = x0 + tx;
+  if (gx >= nx) return;
+  const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * kRowStride;
+    if (gy >= ny) continue;
+    const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
+    const int ly = ty + k * kRowStride + 1, lx = tx + 1;
+    // lam_i(z) = mu_i(z + e_i) + rhob(z + e_i).
+    const int oc = gy * nx, om = ym * nx, op = yp * nx;
+    const int off = oc + gx;
+    lam_out[off] = mu[off] + rb[ly][lx];
+    lam_out[plane + off] = mu[plane + oc + xp] + rb[ly][lx + 1];
+    lam_out[2 * plane + off] = mu[2 * plane + op + gx] + rb[ly + 1][lx];
+    lam_out[3 * plane + off] = mu[3 * plane + oc + xm] + rb[ly][lx - 1];
+    lam_out[4 * plane + off] = mu[4 * plane + om + gx] + rb[ly - 1][lx];
+    lam_out[5 * plane + off] = mu[5 * plane + op + xp] + rb[ly + 1][lx + 1];
+    lam_out[6 * plane + off] = mu[6 * plane + op + xm] + rb[ly + 1][lx - 1];
+    lam_out[7 * plane + off] = mu[7 * plane + om + xm] + rb[ly - 1][lx - 1];
+    lam_out[8 * plane + off] = mu[8 * plane + om + xp] + rb[ly - 1][lx + 1];
+  }
+}
+
+// dtheta[k] += sum over blocks of partial[b][k], in a fixed order.
+__global__ void k_adj_theta(const double* __restrict__ partial, int nblocks, double RT_over_T,
+                            double* __restrict__ dtheta) {
+  __shared__ double sh[256];
+  for (int k = 0; k < 3; ++k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) v += partial[size_t(b) * 3 + k];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) dtheta[k] += k == 0 ? sh[0] * RT_over_T : sh[0];
+    __syncthreads();
+  }
+}
+
+size_t adj_scratch_bytes(const lb_params* p, size_t real_bytes) {
+  const size_t N = size_t(p->nx) * p->ny;
+  const size_t blocks = size_t((p->nx + kTileX - 1) / kTileX) * ((p->ny + kTileY - 1) / kTileY);
+  return ((11 * N * real_bytes + 255) / 256) * 256 + blocks * 3 * sizeof(double);
+}
+
+template <typename real, typename store_t>
+int adjoint(lb_handle* h, const void* f_state, const void* lam_in, void* lam_out, double* dtheta, void* scratch) {
+  const int nx = h->p.nx, ny = h->p.ny;
+  const size_t N = size_t(nx) * ny;
+  real* mu = static_cast<real*>(scratch);
+  real* sbar = mu + 9 * N;
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + ((11 * N * sizeof(real) + 255) / 256) * 256);
+  const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
+  const VCoef<real>* c;
+  if constexpr (sizeof(real) == 8)
+    c = &h->cd;
+  else
+    c = &h->cf;
+  k_adj_local<real, store_t><<<grd, kAdjThreads, 0, h->stream>>>(
+      static_cast<const store_t*>(f_state), static_cast<const real*>(lam_in), mu, sbar, partial, nx, ny, *c);
+  k_adj_transpose<real><<<grd, kAdjThreads, 0, h->stream>>>(mu, sbar, static_cast<real*>(lam_out), nx, ny);
+  if (dtheta) k_adj_theta<<<1, 256, 0, h->stream>>>(partial, int(grd.x * grd.y), h->p.R_gas, dtheta);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::snprintf(h->err, sizeof(h->err), "adjoint kernels: %s", cudaGetErrorString(e));
+    return LB_ECUDA;
+  }
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lb_adjoint_scratch_bytes(const lb_params* p) {
+  if (!p || p->nx < 1 || p->ny < 1) return 0;
+  return adj_scratch_bytes(p, p->precision == LB_FP64 ? 8 : 4);
+}
+
+int lb_adjoint_step(lb_handle* h, const void* f_state, const void* lam_in, void* lam_out, double* dtheta,
+                    void* scratch, size_t scratch_bytes) {
+  if (!h) return LB_EINVAL;
+  if (!f_state || !lam_in || !lam_out || lam_in == lam_out) {
+    std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step: null or aliased buffers");
+    return LB_EINVAL;
+  }
+  const size_t need = lb_adjoint_scratch_bytes(&h->p);
+  if (!scratch || scratch_bytes < need) {
+    std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step needs %zu bytes of scratch, got %zu", need,
+                  scratch ? scratch_bytes : 0);
+    return LB_ENOMEM;
+  }
+  switch (h->p.precision) {
+    case LB_FP64: return adjoint<double, double>(h, f_state, lam_in, lam_out, dtheta, scratch);
+    case LB_FP32: return adjoint<float, float>(h, f_state, lam_in, lam_out, dtheta, scratch);
+    default:
+      std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step supports FP64 and FP32 storage");
+      return LB_ENOTSUP;
+  }
+}
+
+}  // extern "C"
