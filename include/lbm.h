@@ -190,6 +190,49 @@ size_t lb_adjoint_scratch_bytes(const lb_params* p);
 int lb_adjoint_step(lb_handle* h, const void* f_state, const void* lam_in, void* lam_out, double* dtheta,
                     void* scratch, size_t scratch_bytes);
 
+/* Adjoint of k consecutive steps in one call (a checkpoint segment): states[j]
+ * (host array of k device pointers) is the state s^{n+j} each forward step
+ * started from; lam holds dL/ds^{n+k} on entry and dL/ds^n on return (in place,
+ * compute type).  Same mathematics as k calls of lb_adjoint_step, but the
+ * transposed pull and stencil of step j+1 are fused into the local
+ * vector-Jacobian product of step j, so each step is one kernel reading the
+ * state, the cotangent populations and the stencil cotangent (124 B per node in
+ * FP32).  dtheta as in lb_adjoint_step.  Scratch: lb_adjoint_steps_scratch_bytes. */
+size_t lb_adjoint_steps_scratch_bytes(const lb_params* p);
+int lb_adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, double* dtheta, void* scratch,
+                     size_t scratch_bytes);
+
+/* ---------------------------------------------------------------------------
+ * Batched solver: n independent periodic lattices (each with its own size and
+ * lb_params: Tr, K_int, rho_ref, ...) advanced together by one persistent kernel
+ * launch per time step over a flat list of tiles of all lattices; runs of 64
+ * steps are captured into CUDA graphs and replayed.  FP32 storage only.
+ * Memory (all the caller's): two population pools of lb_batch_pool_bytes (lattice
+ * i at element offset lb_batch_offset(i), layout f[9][ny][nx] as above) and a
+ * metadata buffer of lb_batch_meta_bytes (descriptors, coefficients).
+ * rho0: the initial densities of all lattices concatenated ([y][x] each), host
+ * (staged through pool_b, synchronous) or device.  A stream of NULL (the legacy
+ * default stream) cannot be captured: lb_batch_run then launches step by step. */
+typedef struct lb_batch lb_batch;
+size_t lb_batch_pool_bytes(const lb_params* ps, int n);
+size_t lb_batch_meta_bytes(const lb_params* ps, int n);
+int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
+                  size_t meta_bytes, const double* rho0, int rho0_on_device, void* stream);
+/* Advances every lattice by nsteps. */
+int lb_batch_run(lb_batch* b, int64_t nsteps);
+/* Autotuner: times each (tile height 16 or 32, resident blocks per SM) pair for
+ * trial_steps steps on the batch itself (advancing it) and keeps the fastest;
+ * writes its time per step. */
+int lb_batch_tune(lb_batch* b, int trial_steps, double* best_ms_per_step);
+int lb_batch_config(const lb_batch* b, int* tile_y, int* blocks_per_sm, int* grid);
+/* Device pointer of the pool holding the current state; element offset of lattice i. */
+void* lb_batch_state(lb_batch* b);
+int64_t lb_batch_steps_done(const lb_batch* b);
+int64_t lb_batch_offset(const lb_batch* b, int i);
+int lb_batch_derived(const lb_batch* b, int i, lb_derived* out);
+const char* lb_batch_last_error(const lb_batch* b);
+void lb_batch_free(lb_batch* b);
+
 /* Copies the current state to / from a caller device buffer of lb_state_bytes(). */
 int lb_get_state(lb_handle* h, void* dst);
 int lb_set_state(lb_handle* h, const void* src);

@@ -126,3 +126,71 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Independent FP32 lattices advanced together (lb_batch_*).
+
+    rho0s: list of initial densities [ny, nx] (numpy); kws: list of dicts of
+    lb_params fields per lattice (Tr, K_int, ...).  Runs on its own CUDA stream
+    (graphs cannot be captured on the legacy default stream)."""
+
+    def __init__(self, rho0s, kws, stream=None):
+        torch = _torch()
+        n = len(rho0s)
+        self.n = n
+        self.shapes = [np.asarray(r).shape for r in rho0s]
+        self.rho_refs = [float(np.float32(kw.pop("rho_ref", float(np.mean(r))))) for r, kw in zip(rho0s, kws)]
+        ps = (capi.lb_params * n)(*[params(s[1], s[0], precision="fp32", rho_ref=rr, **kw)
+                                    for s, rr, kw in zip(self.shapes, self.rho_refs, kws)])
+        self._ps = ps
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        pb, mb = capi.lb_batch_pool_bytes(ps), capi.lb_batch_meta_bytes(ps)
+        self.pool_a = torch.empty(pb // 4, dtype=torch.float32, device=dev)
+        self.pool_b = torch.empty(pb // 4, dtype=torch.float32, device=dev)
+        self.meta = torch.empty(mb, dtype=torch.uint8, device=dev)
+        rho = np.concatenate([np.ascontiguousarray(r, dtype=np.float64).ravel() for r in rho0s])
+        self._rho_host = torch.from_numpy(rho).pin_memory()
+        torch.cuda.current_stream().synchronize()
+        self.b = capi.lb_batch_init(ps, self.pool_a.data_ptr(), self.pool_b.data_ptr(), self.meta.data_ptr(), mb,
+                                    self._rho_host.data_ptr(), False, self.stream.cuda_stream)
+
+    def run(self, nsteps: int) -> None:
+        capi.lb_batch_run(self.b, nsteps)
+
+    def tune(self, trial_steps: int = 10) -> float:
+        return capi.lb_batch_tune(self.b, trial_steps)
+
+    def config(self) -> dict:
+        return capi.lb_batch_config(self.b)
+
+    @property
+    def steps_done(self) -> int:
+        return capi.lb_batch_steps_done(self.b)
+
+    def state(self, i: int):
+        """Current state of lattice i: [9, ny, nx] view of the current pool (deviations)."""
+        self.stream.synchronize()
+        pool = self.pool_a if capi.lb_batch_state(self.b) == self.pool_a.data_ptr() else self.pool_b
+        off = capi.lb_batch_offset(self.b, i)
+        ny, nx = self.shapes[i]
+        return pool[off:off + 9 * nx * ny].view(9, ny, nx)
+
+    def density(self, i: int):
+        return self.state(i).double().sum(0) + self.rho_refs[i]
+
+    def derived(self, i: int) -> dict:
+        return capi.lb_batch_derived(self.b, i)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            self.stream.synchronize()
+            capi.lb_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -86,24 +86,22 @@ def _make_function():
             real = torch.float64 if spec.precision == "fp64" else torch.float32
             dev = grad_out.device
             lam = grad_out.to(real).contiguous().clone()
-            lam_next = torch.empty_like(lam)
-            nscr = capi.lb_adjoint_scratch_bytes(lat.p)
+            nscr = capi.lb_adjoint_steps_scratch_bytes(lat.p)
             scratch = torch.empty(nscr, dtype=torch.uint8, device=dev)
             dtheta = torch.zeros(3, dtype=torch.float64, device=dev)
             nseg = len(ctx.checkpoints)
             for seg in range(nseg - 1, -1, -1):
                 start = seg * ctx.every
                 k = min(ctx.every, ctx.nsteps - start)
-                # Recompute the states s^start .. s^(start+k-1) of this segment.
+                # Recompute the states s^start .. s^(start+k-1) of this segment, then
+                # run the segment's adjoint steps backwards in one call.
                 states = [ctx.checkpoints[seg]]
                 capi.lb_set_state(lat.h, ctx.checkpoints[seg].data_ptr())
                 for _ in range(k - 1):
                     lat.step(1)
                     states.append(lat.state().clone())
-                for s in reversed(states):
-                    capi.lb_adjoint_step(lat.h, s.data_ptr(), lam.data_ptr(), lam_next.data_ptr(),
-                                         dtheta.data_ptr(), scratch.data_ptr(), nscr)
-                    lam, lam_next = lam_next, lam
+                capi.lb_adjoint_steps(lat.h, [t.data_ptr() for t in states], lam.data_ptr(), dtheta.data_ptr(),
+                                      scratch.data_ptr(), nscr)
             dT, dG2, dlam = (float(v) for v in dtheta.cpu())
             Tr, G2, K = (float(v) for v in theta.detach().cpu())
             lam_val = spec.lam_ref * (spec.K_ref / K) ** 2

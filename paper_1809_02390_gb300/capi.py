@@ -63,6 +63,22 @@ SIGNATURES = [
     ("lb_reduce_static", ctypes.c_int, [_V, _D]),
     ("lb_adjoint_scratch_bytes", ctypes.c_size_t, [_P]),
     ("lb_adjoint_step", ctypes.c_int, [_V, _V, _V, _V, _V, _V, ctypes.c_size_t]),
+    ("lb_adjoint_steps_scratch_bytes", ctypes.c_size_t, [_P]),
+    ("lb_adjoint_steps", ctypes.c_int, [_V, ctypes.POINTER(_V), ctypes.c_int, _V, _V, _V, ctypes.c_size_t]),
+    ("lb_batch_pool_bytes", ctypes.c_size_t, [_P, ctypes.c_int]),
+    ("lb_batch_meta_bytes", ctypes.c_size_t, [_P, ctypes.c_int]),
+    ("lb_batch_init", ctypes.c_int, [ctypes.POINTER(_V), _P, ctypes.c_int, _V, _V, _V, ctypes.c_size_t, _V,
+                                     ctypes.c_int, _V]),
+    ("lb_batch_run", ctypes.c_int, [_V, ctypes.c_int64]),
+    ("lb_batch_tune", ctypes.c_int, [_V, ctypes.c_int, _D]),
+    ("lb_batch_config", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
+    ("lb_batch_state", _V, [_V]),
+    ("lb_batch_steps_done", ctypes.c_int64, [_V]),
+    ("lb_batch_offset", ctypes.c_int64, [_V, ctypes.c_int]),
+    ("lb_batch_derived", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(lb_derived)]),
+    ("lb_batch_last_error", ctypes.c_char_p, [_V]),
+    ("lb_batch_free", None, [_V]),
     ("lb_get_state", ctypes.c_int, [_V, _V]),
     ("lb_set_state", ctypes.c_int, [_V, _V]),
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
@@ -168,6 +184,16 @@ def lb_adjoint_step(h: int, f_state: int, lam_in: int, lam_out: int, dtheta: int
     check(lib().lb_adjoint_step(h, f_state, lam_in, lam_out, dtheta, scratch, scratch_bytes), h)
 
 
+def lb_adjoint_steps_scratch_bytes(p: lb_params) -> int:
+    return lib().lb_adjoint_steps_scratch_bytes(ctypes.byref(p))
+
+
+def lb_adjoint_steps(h: int, states: list[int], lam: int, dtheta: int | None, scratch: int,
+                     scratch_bytes: int) -> None:
+    arr = (ctypes.c_void_p * len(states))(*states)
+    check(lib().lb_adjoint_steps(h, arr, len(states), lam, dtheta, scratch, scratch_bytes), h)
+
+
 def lb_get_state(h: int, dst: int) -> None:
     check(lib().lb_get_state(h, dst), h)
 
@@ -180,6 +206,67 @@ def lb_get_derived(h: int) -> dict:
     d = lb_derived()
     check(lib().lb_get_derived(h, ctypes.byref(d)), h)
     return d.as_dict()
+
+
+def check_batch(rc: int, b=None) -> int:
+    if rc != LB_OK:
+        msg = lib().lb_batch_last_error(b)
+        raise LBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lb_batch_pool_bytes(ps) -> int:
+    return lib().lb_batch_pool_bytes(ps, len(ps))
+
+
+def lb_batch_meta_bytes(ps) -> int:
+    return lib().lb_batch_meta_bytes(ps, len(ps))
+
+
+def lb_batch_init(ps, pool_a: int, pool_b: int, meta: int, meta_bytes: int, rho0: int, rho0_on_device: bool,
+                  stream: int) -> int:
+    b = ctypes.c_void_p()
+    check_batch(lib().lb_batch_init(ctypes.byref(b), ps, len(ps), pool_a, pool_b, meta, meta_bytes, rho0,
+                                    int(bool(rho0_on_device)), stream or None))
+    return b.value
+
+
+def lb_batch_run(b: int, nsteps: int) -> None:
+    check_batch(lib().lb_batch_run(b, int(nsteps)), b)
+
+
+def lb_batch_tune(b: int, trial_steps: int) -> float:
+    ms = ctypes.c_double()
+    check_batch(lib().lb_batch_tune(b, int(trial_steps), ctypes.byref(ms)), b)
+    return ms.value
+
+
+def lb_batch_config(b: int) -> dict:
+    ty, bps, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check_batch(lib().lb_batch_config(b, ctypes.byref(ty), ctypes.byref(bps), ctypes.byref(grid)), b)
+    return {"tile_y": ty.value, "blocks_per_sm": bps.value, "grid": grid.value}
+
+
+def lb_batch_state(b: int) -> int:
+    return lib().lb_batch_state(b)
+
+
+def lb_batch_steps_done(b: int) -> int:
+    return lib().lb_batch_steps_done(b)
+
+
+def lb_batch_offset(b: int, i: int) -> int:
+    return lib().lb_batch_offset(b, i)
+
+
+def lb_batch_derived(b: int, i: int) -> dict:
+    d = lb_derived()
+    check_batch(lib().lb_batch_derived(b, i, ctypes.byref(d)), b)
+    return d.as_dict()
+
+
+def lb_batch_free(b: int) -> None:
+    lib().lb_batch_free(b)
 
 
 def lb_last_error(h: int | None = None) -> str:

@@ -58,7 +58,9 @@ __global__ void __launch_bounds__(kAdjThreads)
     rs[wy][wx] = sum9(g);
   }
   __syncthreads();
-  double acc[3] = {0.0, 0.0, 0.0};
+  // Parameter cotangents summed in the compute type within a warp (FP64 arithmetic
+  // is slow on this GPU); warp partials are folded in FP64.
+  real acc[3] = {real(0), real(0), real(0)};
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
     const int ly = ty + k * kRowStride + 1, lx = tx + 1;
@@ -77,15 +79,17 @@ __global__ void __launch_bounds__(kAdjThreads)
     for (int i = 0; i < 9; ++i) mu[i * plane + off] = r.d[i];
     sbar[off] = r.Sx;
     sbar[plane + off] = r.Sy;
-    acc[0] += double(r.RT);
-    acc[1] += double(r.G2);
-    acc[2] += double(r.lam);
+    acc[0] += r.RT;
+    acc[1] += r.G2;
+    acc[2] += r.lam;
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double v = warp_sum(acc[k]);
-    if (lane == 0) red[w][k] = v;
+    real v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][k] = double(v);
   }
   __syncthreads();
   if (threadIdx.x < 3) {
@@ -167,10 +171,192 @@ __global__ void k_adj_theta(const double* __restrict__ partial, int nblocks, dou
   }
 }
 
+// Fused adjoint step on the (mu, Sb) representation of the cotangent: the
+// cotangent of the state after step n+1 is lam(z) = mu'_i(z + e_i) + rhob'(z + e_i)
+// with rhob' the transposed stencil of Sb'.  One kernel per step reads the state
+// s^n (with its density ring), mu' (pulled backwards) and Sb' (with a two-node
+// ring, staged in shared memory), forms lam at each node, and writes the local
+// VJP (mu, Sb) of step n: 124 B per node in FP32 against 196 B for
+// k_adj_local + k_adj_transpose.
+// 3 resident blocks per SM for FP32 (<= 85 registers), 2 for FP64.
+template <typename real>
+constexpr int adj_min_blocks() {
+  return sizeof(real) == 8 ? 1 : 3;
+}
+
+template <typename real, typename store_t>
+__global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
+    k_adj_fused(const store_t* __restrict__ s, const real* __restrict__ mu_in, const real* __restrict__ sb_in,
+                real* __restrict__ mu, real* __restrict__ sbar, double* __restrict__ partial, int accumulate,
+                int nx, int ny, VCoef<real> c) {
+  __shared__ real rs[kTileY + 2][kTileX + 2];   // density of s^n on tile + ring
+  __shared__ real rb[kTileY + 2][kTileX + 2];   // rhob' on tile + ring
+  __shared__ real sbx[kTileY + 4][kTileX + 4];  // Sb' on tile + two-node ring
+  __shared__ real sby[kTileY + 4][kTileX + 4];
+  __shared__ double red[kAdjThreads / 32][3];
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  const int plane = nx * ny;
+  const int gx = x0 + tx;
+  const int xc = wrap(gx, nx);
+  const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
+  real f[kTileRows][9];
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * kRowStride;
+    pull_row(s, plane, nx, ny, wrap(gy, ny), xm, xc, xp, f[k]);
+  }
+  for (int t = threadIdx.x; t < (kTileY + 4) * (kTileX + 4); t += kAdjThreads) {
+    const int wy = t / (kTileX + 4), wx = t - wy * (kTileX + 4);
+    const int o = wrap(y0 - 2 + wy, ny) * nx + wrap(x0 - 2 + wx, nx);
+    sbx[wy][wx] = sb_in[o];
+    sby[wy][wx] = sb_in[plane + o];
+  }
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  for (int t = threadIdx.x; t < 2 * (kTileX + 2) + 2 * kTileY; t += kAdjThreads) {
+    int wx, wy;
+    if (t < kTileX + 2) {
+      wx = t, wy = 0;
+    } else if (t < 2 * (kTileX + 2)) {
+      wx = t - (kTileX + 2), wy = kTileY + 1;
+    } else if (t < 2 * (kTileX + 2) + kTileY) {
+      wx = 0, wy = t - 2 * (kTileX + 2) + 1;
+    } else {
+      wx = kTileX + 1, wy = t - 2 * (kTileX + 2) - kTileY + 1;
+    }
+    const int hx = wrap(x0 - 1 + wx, nx), hy = wrap(y0 - 1 + wy, ny);
+    real g[9];
+    pull_row(s, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
+    rs[wy][wx] = sum9(g);
+  }
+  __syncthreads();
+  // rhob'(y) = sum_j omega_j e_j . Sb'(y - e_j) on tile + ring (smem index of y is (wy + 1, wx + 1)).
+  const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0);
+  for (int t = threadIdx.x; t < (kTileY + 2) * (kTileX + 2); t += kAdjThreads) {
+    const int wy = t / (kTileX + 2), wx = t - wy * (kTileX + 2);
+    const int cy = wy + 1, cx = wx + 1;
+    const real ax = sbx[cy][cx - 1] - sbx[cy][cx + 1];
+    const real ay = sby[cy - 1][cx] - sby[cy + 1][cx];
+    const real d5 = sbx[cy - 1][cx - 1] + sby[cy - 1][cx - 1];
+    const real d6 = sby[cy - 1][cx + 1] - sbx[cy - 1][cx + 1];
+    const real d7 = -sbx[cy + 1][cx + 1] - sby[cy + 1][cx + 1];
+    const real d8 = sbx[cy + 1][cx - 1] - sby[cy + 1][cx - 1];
+    rb[wy][wx] = third * (ax + ay) + twelfth * ((d5 + d6) + (d7 + d8));
+  }
+  __syncthreads();
+  // Parameter cotangents summed in the compute type within a warp (FP64 arithmetic
+  // is slow on this GPU); warp partials are folded in FP64.
+  real acc[3] = {real(0), real(0), real(0)};
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int ly = ty + k * kRowStride + 1, lx = tx + 1;
+    const int gy = y0 + ly - 1;
+    if (gx >= nx || gy >= ny) continue;
+    real Sx, Sy;
+    stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
+            rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx, Sy);
+    const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
+    const int oc = gy * nx, om = ym * nx, op = yp * nx, off = oc + gx;
+    // lam_i(x) = mu'_i(x + e_i) + rhob'(x + e_i).
+    real ob[9];
+    ob[0] = mu_in[off] + rb[ly][lx];
+    ob[1] = mu_in[plane + oc + xp] + rb[ly][lx + 1];
+    ob[2] = mu_in[2 * plane + op + gx] + rb[ly + 1][lx];
+    ob[3] = mu_in[3 * plane + oc + xm] + rb[ly][lx - 1];
+    ob[4] = mu_in[4 * plane + om + gx] + rb[ly - 1][lx];
+    ob[5] = mu_in[5 * plane + op + xp] + rb[ly + 1][lx + 1];
+    ob[6] = mu_in[6 * plane + op + xm] + rb[ly + 1][lx - 1];
+    ob[7] = mu_in[7 * plane + om + xm] + rb[ly - 1][lx - 1];
+    ob[8] = mu_in[8 * plane + om + xp] + rb[ly - 1][lx + 1];
+    AdjOut<real> r;
+    collide_vjp(c, f[k], Sx, Sy, ob, r);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i * plane + off] = r.d[i];
+    sbar[off] = r.Sx;
+    sbar[plane + off] = r.Sy;
+    acc[0] += r.RT;
+    acc[1] += r.G2;
+    acc[2] += r.lam;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    real v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][k] = double(v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int j = 0; j < kAdjThreads / 32; ++j) v += red[j][threadIdx.x];
+    // Each block owns its slot; successive steps on one stream accumulate in order.
+    double* slot = partial + (size_t(blockIdx.y) * gridDim.x + blockIdx.x) * 3 + threadIdx.x;
+    *slot = accumulate ? *slot + v : v;
+  }
+}
+
+// Cotangent lam of a state -> (mu, Sb) representation: mu_i(y) = lam_i(y - e_i), Sb = 0.
+template <typename real>
+__global__ void k_adj_push(const real* __restrict__ lam, real* __restrict__ mu, real* __restrict__ sbar, int nx,
+                           int ny) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const int plane = nx * ny;
+  real v[9];
+  pull_row(lam, plane, nx, ny, y, x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1, v);
+  const int off = y * nx + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) mu[i * plane + off] = v[i];
+  sbar[off] = real(0);
+  sbar[plane + off] = real(0);
+}
+
 size_t adj_scratch_bytes(const lb_params* p, size_t real_bytes) {
   const size_t N = size_t(p->nx) * p->ny;
   const size_t blocks = size_t((p->nx + kTileX - 1) / kTileX) * ((p->ny + kTileY - 1) / kTileY);
   return ((11 * N * real_bytes + 255) / 256) * 256 + blocks * 3 * sizeof(double);
+}
+
+// Two (mu, Sb) sets (ping-pong) + per-block partials.
+size_t adj_steps_scratch_bytes(const lb_params* p, size_t real_bytes) {
+  const size_t N = size_t(p->nx) * p->ny;
+  const size_t blocks = size_t((p->nx + kTileX - 1) / kTileX) * ((p->ny + kTileY - 1) / kTileY);
+  return 2 * ((11 * N * real_bytes + 255) / 256) * 256 + blocks * 3 * sizeof(double);
+}
+
+template <typename real, typename store_t>
+int adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, double* dtheta, void* scratch) {
+  const int nx = h->p.nx, ny = h->p.ny;
+  const size_t N = size_t(nx) * ny;
+  const size_t set = ((11 * N * sizeof(real) + 255) / 256) * 256;
+  real* mu[2] = {static_cast<real*>(scratch), reinterpret_cast<real*>(static_cast<char*>(scratch) + set)};
+  real* sb[2] = {mu[0] + 9 * N, mu[1] + 9 * N};
+  double* partial = reinterpret_cast<double*>(static_cast<char*>(scratch) + 2 * set);
+  const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
+  const VCoef<real>* c;
+  if constexpr (sizeof(real) == 8)
+    c = &h->cd;
+  else
+    c = &h->cf;
+  const dim3 blk(32, 8), pgrd((nx + 31) / 32, (ny + 7) / 8);
+  k_adj_push<real><<<pgrd, blk, 0, h->stream>>>(static_cast<const real*>(lam), mu[0], sb[0], nx, ny);
+  int cur = 0;
+  for (int j = k - 1; j >= 0; --j) {
+    k_adj_fused<real, store_t><<<grd, kAdjThreads, 0, h->stream>>>(static_cast<const store_t*>(states[j]), mu[cur],
+                                                                   sb[cur], mu[1 - cur], sb[1 - cur], partial,
+                                                                   j < k - 1, nx, ny, *c);
+    cur = 1 - cur;
+  }
+  if (dtheta) k_adj_theta<<<1, 256, 0, h->stream>>>(partial, int(grd.x * grd.y), h->p.R_gas, dtheta);
+  k_adj_transpose<real><<<grd, kAdjThreads, 0, h->stream>>>(mu[cur], sb[cur], static_cast<real*>(lam), nx, ny);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::snprintf(h->err, sizeof(h->err), "adjoint kernels: %s", cudaGetErrorString(e));
+    return LB_ECUDA;
+  }
+  return LB_OK;
 }
 
 template <typename real, typename store_t>
@@ -225,6 +411,38 @@ int lb_adjoint_step(lb_handle* h, const void* f_state, const void* lam_in, void*
     case LB_FP32: return adjoint<float, float>(h, f_state, lam_in, lam_out, dtheta, scratch);
     default:
       std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step supports FP64 and FP32 storage");
+      return LB_ENOTSUP;
+  }
+}
+
+size_t lb_adjoint_steps_scratch_bytes(const lb_params* p) {
+  if (!p || p->nx < 1 || p->ny < 1) return 0;
+  return adj_steps_scratch_bytes(p, p->precision == LB_FP64 ? 8 : 4);
+}
+
+int lb_adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, double* dtheta, void* scratch,
+                     size_t scratch_bytes) {
+  if (!h) return LB_EINVAL;
+  if (!states || k < 1 || !lam) {
+    std::snprintf(h->err, sizeof(h->err), "lb_adjoint_steps: need k >= 1 states and a cotangent buffer");
+    return LB_EINVAL;
+  }
+  for (int j = 0; j < k; ++j)
+    if (!states[j]) {
+      std::snprintf(h->err, sizeof(h->err), "lb_adjoint_steps: state %d is null", j);
+      return LB_EINVAL;
+    }
+  const size_t need = lb_adjoint_steps_scratch_bytes(&h->p);
+  if (!scratch || scratch_bytes < need) {
+    std::snprintf(h->err, sizeof(h->err), "lb_adjoint_steps needs %zu bytes of scratch, got %zu", need,
+                  scratch ? scratch_bytes : 0);
+    return LB_ENOMEM;
+  }
+  switch (h->p.precision) {
+    case LB_FP64: return adjoint_steps<double, double>(h, states, k, lam, dtheta, scratch);
+    case LB_FP32: return adjoint_steps<float, float>(h, states, k, lam, dtheta, scratch);
+    default:
+      std::snprintf(h->err, sizeof(h->err), "lb_adjoint_steps supports FP64 and FP32 storage");
       return LB_ENOTSUP;
   }
 }

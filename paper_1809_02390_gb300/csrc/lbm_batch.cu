@@ -1,0 +1,373 @@
+// Batched solver: many independent periodic lattices, each with its own size and
+// parameters, advanced together.  One persistent kernel launch per time step
+// walks a flat list of 32 x TY tiles spanning all lattices (each block takes
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ...), stages the coefficients of the
+// tile's lattice in shared memory and runs the same tile code as the
+// single-lattice fused step.  Runs of steps are captured once into CUDA graphs
+// and replayed.  The autotuner times every (tile height, resident blocks per SM)
+// pair on the batch itself and keeps the fastest.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_handle.cuh"
+
+namespace lbm {
+template <typename V>
+VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d);
+}  // namespace lbm
+
+namespace {
+
+using namespace lbm;
+
+struct BatchLattice {
+  int nx, ny;
+  long long offset;  // element offset of the lattice's plane 0 in a pool
+  int tile_start;    // index of its first tile in the flat tile list
+  int tiles_x;       // tiles per row of tiles
+};
+
+constexpr int kShapes = 2;
+constexpr int kShapeTY[kShapes] = {16, 32};
+constexpr int kGraphSteps = 64;  // steps per captured graph (even: the pools end where they started)
+
+// Register budget of 64 per thread (4 blocks of 256 or 2 of 512 threads per SM),
+// as for the single-lattice kernel.
+template <typename store_t, int TY>
+__global__ void __launch_bounds__(TileShape<TY>::threads, 1024 / TileShape<TY>::threads)
+    k_step_batch(const store_t* __restrict__ pool_in, store_t* __restrict__ pool_out,
+                 const BatchLattice* __restrict__ desc, const VCoef<f2>* __restrict__ coef, int n,
+                 int total_tiles) {
+  __shared__ float rs[TY + 2][kTileX + 2];
+  __shared__ VCoef<f2> cs;
+  int last = -1;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    // Lattice of tile t: last descriptor with tile_start <= t (same for the whole block).
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (desc[mid].tile_start <= t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BatchLattice L = desc[lo];
+    if (lo != last) {
+      const int* src = reinterpret_cast<const int*>(coef + lo);
+      int* dst = reinterpret_cast<int*>(&cs);
+      for (int w = threadIdx.x; w < int(sizeof(VCoef<f2>) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      last = lo;
+    }
+    const int local = t - L.tile_start;
+    const int tyi = local / L.tiles_x, txi = local - tyi * L.tiles_x;
+    step_tile<f2, store_t, TY>(pool_in + L.offset, pool_out + L.offset, L.nx, L.ny, cs, txi * kTileX, tyi * TY, rs);
+    __syncthreads();  // shared densities and coefficients are reused by the next tile
+  }
+}
+
+template <int TY>
+const void* batch_kernel() {
+  return reinterpret_cast<const void*>(k_step_batch<float, TY>);
+}
+
+}  // namespace
+
+struct lb_batch {
+  int n;
+  std::vector<lb_params> p;
+  std::vector<lb_derived> d;
+  std::vector<BatchLattice> desc[kShapes];
+  int total_tiles[kShapes];
+  void* pool[2];
+  int cur;
+  BatchLattice* d_desc[kShapes];
+  VCoef<f2>* d_coef;
+  cudaStream_t stream;
+  int sms;
+  int shape;          // index into kShapeTY
+  int blocks_per_sm;  // persistent grid = blocks_per_sm * sms
+  int64_t steps;
+  cudaGraphExec_t graph[2];  // starting from pool 0 / pool 1
+  int graph_cfg[2];          // configuration the graph was captured with
+  char err[512];
+};
+
+namespace {
+
+int berr(lb_batch* b, int code, const char* fmt, const char* detail = "") {
+  if (b) std::snprintf(b->err, sizeof(b->err), fmt, detail);
+  else {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), fmt, detail);
+    set_thread_error(buf);
+  }
+  return code;
+}
+
+size_t lattice_elems(const lb_params& p) { return ((9 * size_t(p.nx) * p.ny + 63) / 64) * 64; }
+
+int max_blocks(lb_batch* b, int shape, int* out) {
+  const void* k = shape == 0 ? batch_kernel<16>() : batch_kernel<32>();
+  const int threads = shape == 0 ? TileShape<16>::threads : TileShape<32>::threads;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, threads, 0);
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (*out < 1) *out = 1;
+  return LB_OK;
+}
+
+void launch_one(lb_batch* b, int from) {
+  const float* in = static_cast<const float*>(b->pool[from]);
+  float* out = static_cast<float*>(b->pool[1 - from]);
+  const int grid = b->blocks_per_sm * b->sms;
+  if (b->shape == 0)
+    k_step_batch<float, 16><<<grid, TileShape<16>::threads, 0, b->stream>>>(in, out, b->d_desc[0], b->d_coef, b->n,
+                                                                           b->total_tiles[0]);
+  else
+    k_step_batch<float, 32><<<grid, TileShape<32>::threads, 0, b->stream>>>(in, out, b->d_desc[1], b->d_coef, b->n,
+                                                                           b->total_tiles[1]);
+}
+
+int config_id(const lb_batch* b) { return b->shape * 64 + b->blocks_per_sm; }
+
+int ensure_graph(lb_batch* b, int from) {
+  if (b->graph[from] && b->graph_cfg[from] == config_id(b)) return LB_OK;
+  if (b->graph[from]) {
+    cudaGraphExecDestroy(b->graph[from]);
+    b->graph[from] = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  int side = from;
+  for (int s = 0; s < kGraphSteps; ++s) {
+    launch_one(b, side);
+    side = 1 - side;
+  }
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph[from], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  b->graph_cfg[from] = config_id(b);
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lb_batch_pool_bytes(const lb_params* ps, int n) {
+  if (!ps || n < 1) return 0;
+  size_t e = 0;
+  for (int i = 0; i < n; ++i) e += lattice_elems(ps[i]);
+  return e * sizeof(float);
+}
+
+size_t lb_batch_meta_bytes(const lb_params* ps, int n) {
+  if (!ps || n < 1) return 0;
+  return size_t(n) * (kShapes * sizeof(BatchLattice) + sizeof(VCoef<f2>)) + 1024;
+}
+
+int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
+                  size_t meta_bytes, const double* rho0, int rho0_on_device, void* stream) {
+  if (!out) return berr(nullptr, LB_EINVAL, "null output%s");
+  *out = nullptr;
+  if (!ps || n < 1 || !pool_a || !pool_b || pool_a == pool_b || !meta || !rho0)
+    return berr(nullptr, LB_EINVAL, "lb_batch_init: invalid arguments%s");
+  if (meta_bytes < lb_batch_meta_bytes(ps, n)) return berr(nullptr, LB_ENOMEM, "lb_batch_init: meta buffer too small%s");
+  lb_batch* b = new (std::nothrow) lb_batch();
+  if (!b) return berr(nullptr, LB_EINVAL, "out of host memory%s");
+  b->n = n;
+  b->p.assign(ps, ps + n);
+  b->d.resize(n);
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->pool[0] = pool_a;
+  b->pool[1] = pool_b;
+  b->cur = 0;
+  b->graph[0] = b->graph[1] = nullptr;
+  b->graph_cfg[0] = b->graph_cfg[1] = -1;
+  auto bail = [&](int code, const char* msg) {
+    set_thread_error(msg);
+    delete b;
+    return code;
+  };
+  std::vector<VCoef<f2>> h_coef(n);
+  std::vector<VCoef<double>> h_coefd(n);
+  size_t off = 0, total_nodes = 0;
+  for (int i = 0; i < n; ++i) {
+    char err[512] = {0};
+    if (ps[i].precision != LB_FP32) return bail(LB_ENOTSUP, "lb_batch_init: the batched solver stores FP32");
+    if (derive(&ps[i], &b->d[i], err, sizeof(err)) != LB_OK) {
+      char m[600];
+      std::snprintf(m, sizeof(m), "lattice %d: %s", i, err);
+      return bail(LB_EINVAL, m);
+    }
+    b->p[i].rho_ref = double(float(ps[i].rho_ref));
+    h_coef[i] = make_vcoef<f2>(b->p[i], b->d[i]);
+    h_coefd[i] = make_vcoef<double>(b->p[i], b->d[i]);
+    for (int s = 0; s < kShapes; ++s) {
+      BatchLattice L;
+      L.nx = ps[i].nx;
+      L.ny = ps[i].ny;
+      L.offset = (long long)off;
+      L.tiles_x = (ps[i].nx + kTileX - 1) / kTileX;
+      L.tile_start = 0;
+      b->desc[s].push_back(L);
+    }
+    off += lattice_elems(ps[i]);
+    total_nodes += size_t(ps[i].nx) * ps[i].ny;
+  }
+  for (int s = 0; s < kShapes; ++s) {
+    int start = 0;
+    for (int i = 0; i < n; ++i) {
+      b->desc[s][i].tile_start = start;
+      start += b->desc[s][i].tiles_x * ((ps[i].ny + kShapeTY[s] - 1) / kShapeTY[s]);
+    }
+    b->total_tiles[s] = start;
+  }
+  // Metadata in the caller's buffer: descriptors per tile shape, then coefficients.
+  char* m = static_cast<char*>(meta);
+  b->d_desc[0] = reinterpret_cast<BatchLattice*>(m);
+  b->d_desc[1] = b->d_desc[0] + n;
+  b->d_coef = reinterpret_cast<VCoef<f2>*>(((reinterpret_cast<uintptr_t>(b->d_desc[1] + n) + 255) / 256) * 256);
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < kShapes && e == cudaSuccess; ++s)
+    e = cudaMemcpyAsync(b->d_desc[s], b->desc[s].data(), n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_coef, h_coef.data(), n * sizeof(VCoef<f2>), cudaMemcpyHostToDevice, b->stream);
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  // Initial state: rest equilibrium of each lattice's density (host path staged in pool_b).
+  const double* rd = rho0;
+  if (e == cudaSuccess && !rho0_on_device) {
+    e = cudaMemcpyAsync(pool_b, rho0, total_nodes * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    rd = static_cast<const double*>(pool_b);
+  }
+  size_t node_off = 0;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const size_t N = size_t(ps[i].nx) * ps[i].ny;
+    k_init_rest<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
+        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny, h_coefd[i]);
+    e = cudaGetLastError();
+    node_off += N;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    char msg[512];
+    std::snprintf(msg, sizeof(msg), "lb_batch_init: %s", cudaGetErrorString(e));
+    return bail(LB_ECUDA, msg);
+  }
+  b->shape = 0;
+  int mb = 1;
+  if (max_blocks(b, 0, &mb) != LB_OK) return bail(LB_ECUDA, b->err);
+  b->blocks_per_sm = mb;
+  b->steps = 0;
+  *out = b;
+  return LB_OK;
+}
+
+int lb_batch_run(lb_batch* b, int64_t nsteps) {
+  if (!b) return LB_EINVAL;
+  if (nsteps < 0) return berr(b, LB_EINVAL, "nsteps must be >= 0%s");
+  // The legacy default stream cannot be captured: plain launches there.
+  while (b->stream != nullptr && nsteps >= kGraphSteps) {
+    const int rc = ensure_graph(b, b->cur);
+    if (rc != LB_OK) return rc;
+    const cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);
+    if (e != cudaSuccess) return berr(b, LB_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    nsteps -= kGraphSteps;
+    b->steps += kGraphSteps;
+  }
+  for (; nsteps > 0; --nsteps) {
+    launch_one(b, b->cur);
+    b->cur = 1 - b->cur;
+    ++b->steps;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "batch step: %s", cudaGetErrorString(e));
+  return LB_OK;
+}
+
+int lb_batch_tune(lb_batch* b, int trial_steps, double* best_ms_per_step) {
+  if (!b || trial_steps < 1) return LB_EINVAL;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return berr(b, LB_ECUDA, "cudaEventCreate%s");
+  float best = 1e30f;
+  int best_shape = b->shape, best_bps = b->blocks_per_sm;
+  int64_t tuned_steps = 0;
+  for (int s = 0; s < kShapes; ++s) {
+    int mb = 1;
+    if (max_blocks(b, s, &mb) != LB_OK) return LB_ECUDA;
+    for (int bps = 1; bps <= mb; ++bps) {
+      b->shape = s;
+      b->blocks_per_sm = bps;
+      launch_one(b, b->cur);  // warm-up (two launches keep the pool parity)
+      launch_one(b, 1 - b->cur);
+      cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < 2 * ((trial_steps + 1) / 2); ++k) launch_one(b, (b->cur + k) & 1);
+      tuned_steps += 2 + 2 * ((trial_steps + 1) / 2);
+      cudaEventRecord(e1, b->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return berr(b, LB_ECUDA, "autotune: %s", cudaGetErrorString(e));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= float(2 * ((trial_steps + 1) / 2));
+      if (ms < best) {
+        best = ms;
+        best_shape = s;
+        best_bps = bps;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->shape = best_shape;
+  b->blocks_per_sm = best_bps;
+  if (best_ms_per_step) *best_ms_per_step = best;
+  // The trial launches advance every lattice by an even number of steps (the
+  // pools end where they started); the state stays a valid trajectory.
+  b->steps += tuned_steps;
+  return LB_OK;
+}
+
+int lb_batch_config(const lb_batch* b, int* tile_y, int* blocks_per_sm, int* grid) {
+  if (!b) return LB_EINVAL;
+  if (tile_y) *tile_y = kShapeTY[b->shape];
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  if (grid) *grid = b->blocks_per_sm * b->sms;
+  return LB_OK;
+}
+
+void* lb_batch_state(lb_batch* b) { return b ? b->pool[b->cur] : nullptr; }
+
+int64_t lb_batch_steps_done(const lb_batch* b) { return b ? b->steps : -1; }
+
+int64_t lb_batch_offset(const lb_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return -1;
+  return b->desc[0][i].offset;
+}
+
+int lb_batch_derived(const lb_batch* b, int i, lb_derived* out) {
+  if (!b || i < 0 || i >= b->n || !out) return LB_EINVAL;
+  *out = b->d[i];
+  return LB_OK;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err : thread_error(); }
+
+void lb_batch_free(lb_batch* b) {
+  if (!b) return;
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+  delete b;
+}
+
+}  // extern "C"

@@ -99,6 +99,10 @@ VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d) {
   return c;
 }
 
+template VCoef<float> make_vcoef<float>(const lb_params&, const lb_derived&);
+template VCoef<f2> make_vcoef<f2>(const lb_params&, const lb_derived&);
+template VCoef<double> make_vcoef<double>(const lb_params&, const lb_derived&);
+
 }  // namespace lbm
 
 using namespace lbm;

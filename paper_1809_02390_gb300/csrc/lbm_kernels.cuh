@@ -43,17 +43,17 @@ __device__ __forceinline__ real sum9(const real (&f)[9]) {
   return ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
 }
 
-// Fused stream + force + collide step on a TX x TY tile per block (TX = 32
-// columns, TY = 16 rows, 256 threads, two nodes per thread in the same column).
+// Fused stream + force + collide step on a TX x TY tile (TX = 32 columns, TY
+// rows, 16 TY threads, two nodes per thread in the same column, TY/2 rows apart).
 // Phase 1: each thread pulls the nine populations of its two nodes into
-// registers and sums their densities; warps 0..3 also pull the 100 nodes of the
-// one-node ring around the tile (densities only), one warp-uniform segment each.
+// registers; the 2 (TX + 2) + 2 TY nodes of the one-node ring around the tile
+// are pulled too (densities only).  All loads are issued before any is used.
 // The densities of tile + ring go to shared memory.  Phase 2: each thread forms
 // the force stencil of its nodes from shared memory and collides; with V = f2
 // the two nodes are the two lanes of one packed FP32x2 collision.  DRAM traffic
 // is one read and one write of every population; the ring re-reads hit L2.
-constexpr int kTileX = 32, kTileY = 16, kTileRows = kTileY / (kFusedThreads / kTileX);
-constexpr int kRowStride = kFusedThreads / kTileX;  // 8
+constexpr int kTileX = 32, kTileY = 16, kTileRows = 2;
+constexpr int kRowStride = kTileY / kTileRows;  // 8
 #ifndef LBM_FUSED_MIN_BLOCKS
 #define LBM_FUSED_MIN_BLOCKS 4
 #endif
@@ -65,56 +65,61 @@ constexpr int fused_min_blocks() {
   return sizeof(typename LaneType<V>::type) == 8 ? 2 : LBM_FUSED_MIN_BLOCKS;
 }
 
-template <typename V, typename store_t>
-__global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
-    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c) {
+template <int TY>
+struct TileShape {
+  static constexpr int threads = kTileX * TY / kTileRows;
+  static constexpr int stride = TY / kTileRows;
+  static constexpr int ring = 2 * (kTileX + 2) + 2 * TY;
+};
+
+// rs: shared array of (TY + 2) x (TX + 2) densities.  (x0, y0): tile origin.
+template <typename V, typename store_t, int TY>
+__device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
+                                          int ny, const VCoef<V>& c, int x0, int y0,
+                                          typename LaneType<V>::type (*rs)[kTileX + 2]) {
   using real = typename LaneType<V>::type;
-  static_assert(kTileRows == 2, "two nodes per thread");
-  __shared__ real rs[kTileY + 2][kTileX + 2];
+  using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   const int plane = nx * ny;
-  const bool small = nx <= kTileX || ny <= kTileY;  // tiles may wrap more than once
+  const bool small = nx <= kTileX || ny <= TY;  // tiles may wrap more than once
   const int gx = x0 + tx;
   const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
   const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
 
-  // All loads of phase 1 are issued before any of them is consumed.
   real f[kTileRows][9];
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * kRowStride;
+    const int gy = y0 + ty + k * Shape::stride;
     pull_row(fin, plane, nx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
   }
-  // Ring: warp 0 the row above, warp 1 the row below, warp 2 the left (lanes
-  // 0..15) and right (16..31) columns, warp 3 lanes 0..3 the corners.
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool ring = warp < 3 || (warp == 3 && lane < 4);
+  // Ring: the row above, the row below, then the left and right columns.
+  const int t = threadIdx.x;
+  const bool ring = t < Shape::ring;
   int wx = 0, wy = 0;
   real g[9];
   if (ring) {
-    if (warp == 0) {
-      wx = lane + 1, wy = 0;
-    } else if (warp == 1) {
-      wx = lane + 1, wy = kTileY + 1;
-    } else if (warp == 2) {
-      wx = lane < 16 ? 0 : kTileX + 1, wy = (lane & 15) + 1;
+    if (t < kTileX + 2) {
+      wx = t, wy = 0;
+    } else if (t < 2 * (kTileX + 2)) {
+      wx = t - (kTileX + 2), wy = TY + 1;
+    } else if (t < 2 * (kTileX + 2) + TY) {
+      wx = 0, wy = t - 2 * (kTileX + 2) + 1;
     } else {
-      wx = (lane & 1) ? kTileX + 1 : 0, wy = (lane & 2) ? kTileY + 1 : 0;
+      wx = kTileX + 1, wy = t - 2 * (kTileX + 2) - TY + 1;
     }
     const int hx = small ? wrap(x0 - 1 + wx, nx) : wrap1(x0 - 1 + wx, nx);
     const int hy = small ? wrap(y0 - 1 + wy, ny) : wrap1(y0 - 1 + wy, ny);
     pull_row(fin, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
   }
 #pragma unroll
-  for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
   if (ring) rs[wy][wx] = sum9(g);
   __syncthreads();
 
   real Sx[kTileRows], Sy[kTileRows];
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
-    const int ly = ty + k * kRowStride + 1, lx = tx + 1;
+    const int ly = ty + k * Shape::stride + 1, lx = tx + 1;
     stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
             rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx[k], Sy[k]);
   }
@@ -137,13 +142,20 @@ __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
   }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * kRowStride;
+    const int gy = y0 + ty + k * Shape::stride;
     if (gx < nx && gy < ny) {
       const int off = gy * nx + gx;
 #pragma unroll
       for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), out[k][i]);
     }
   }
+}
+
+template <typename V, typename store_t>
+__global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
+    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c) {
+  __shared__ typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
+  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, c, blockIdx.x * kTileX, blockIdx.y * kTileY, rs);
 }
 
 // Two-pass variant, pass 1: density plane rho_dev(x) = sum_i fbar_i(x - e_i).

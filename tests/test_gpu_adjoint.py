@@ -149,3 +149,38 @@ def test_rollout_gradient_vs_oracle_complex_step(orc):
     dl = orc.step_cs(p, fabs, None, (0, 0, h), steps)[1].sum(0) / h
     ref = np.array([(resid * dT).sum() * spec.Tc, (resid * dG).sum(), (resid * dl).sum() * (-2 * spec.lam_ref)])
     assert np.allclose(g, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_fused_segment_equals_single_steps(orc, precision, tol):
+    """lb_adjoint_steps (fused, one kernel per step) against k calls of lb_adjoint_step."""
+    from paper_1809_02390_gb300 import capi
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    nx, ny, k = 45, 38, 5
+    f0 = _flow_state(orc, p, nx, ny, 3)
+    lat = lattice(np.full((ny, nx), 2.0), precision, Tr=0.85, G2=p.G2, lam=p.lam, rho_ref=0.0)
+    real = torch.float64 if precision == "fp64" else torch.float32
+    states = [torch.from_numpy(f0).to("cuda", lat.dtype)]
+    capi.lb_set_state(lat.h, states[0].data_ptr())
+    for _ in range(k - 1):
+        lat.step(1)
+        states.append(lat.state().clone())
+    lam0 = torch.from_numpy(np.random.default_rng(2).standard_normal(f0.shape)).to("cuda", real)
+    # k single steps
+    ns = capi.lb_adjoint_scratch_bytes(lat.p)
+    scr = torch.empty(ns, dtype=torch.uint8, device="cuda")
+    a, b = lam0.clone(), torch.empty_like(lam0)
+    th1 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for st in reversed(states):
+        capi.lb_adjoint_step(lat.h, st.data_ptr(), a.data_ptr(), b.data_ptr(), th1.data_ptr(), scr.data_ptr(), ns)
+        a, b = b, a
+    # one fused call
+    ns2 = capi.lb_adjoint_steps_scratch_bytes(lat.p)
+    scr2 = torch.empty(ns2, dtype=torch.uint8, device="cuda")
+    c = lam0.clone()
+    th2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    capi.lb_adjoint_steps(lat.h, [t.data_ptr() for t in states], c.data_ptr(), th2.data_ptr(), scr2.data_ptr(), ns2)
+    torch.cuda.synchronize()
+    assert float((a - c).abs().max()) <= tol * float(a.abs().max())
+    assert float((th1 - th2).abs().max()) <= tol * float(th1.abs().max())

@@ -1,0 +1,93 @@
+"""The batched solver (one persistent launch per step over the tiles of many
+lattices, CUDA-graph replay, autotuned launch shape) gives every lattice exactly
+the trajectory the single-lattice step gives it."""
+import numpy as np
+import pytest
+
+from gpu_util import oracle_params, rel_inf
+from paper_1809_02390_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_02390_gb300 import build
+
+    build.build()
+
+
+CASES = [((64, 64), 0.85, 1.0, "droplet"), ((100, 70), 0.7, 1.6, "slab"), ((33, 45), 0.9, 1.0, "droplet"),
+         ((130, 96), 0.8, 1.3, "slab"), ((40, 40), 0.75, 1.2, "droplet"), ((17, 23), 0.85, 1.0, "slab")]
+
+
+def _inputs():
+    from paper_1809_02390_gb300 import derive
+
+    rhos, kws = [], []
+    for (nx, ny), tr, kint, shape in CASES:
+        d = derive(nx, ny, Tr=tr, K_int=kint)
+        if shape == "droplet":
+            r = inputs.droplet(nx, ny, min(nx, ny) / 4, 4, d["rho_g"], d["rho_l"])
+        else:
+            r = inputs.slab(nx, ny, nx / 2, 4, d["rho_g"], d["rho_l"])
+        rhos.append(r)
+        kws.append(dict(Tr=tr, K_int=kint))
+    return rhos, kws
+
+
+def _singles(rhos, kws, steps):
+    from paper_1809_02390_gb300 import Lattice
+
+    out = []
+    for r, kw in zip(rhos, kws):
+        lat = Lattice(r, precision="fp32", **kw)
+        lat.step(steps)
+        out.append(lat.state().clone())
+        lat.close()
+    return out
+
+
+@pytest.mark.parametrize("steps", [37, 64 * 2 + 5])
+def test_batch_equals_single_lattices(steps):
+    from paper_1809_02390_gb300 import Batch
+
+    rhos, kws = _inputs()
+    b = Batch(rhos, [dict(k) for k in kws])
+    b.run(steps)
+    ref = _singles(rhos, kws, steps)
+    for i in range(len(rhos)):
+        assert torch.equal(b.state(i), ref[i]), i
+    b.close()
+
+
+def test_autotune_keeps_the_trajectory():
+    from paper_1809_02390_gb300 import Batch
+
+    rhos, kws = _inputs()
+    b = Batch(rhos, [dict(k) for k in kws])
+    ms = b.tune(4)
+    cfg = b.config()
+    assert ms > 0 and cfg["tile_y"] in (16, 32) and cfg["blocks_per_sm"] >= 1
+    b.run(70)
+    ref = _singles(rhos, kws, b.steps_done)
+    for i in range(len(rhos)):
+        assert torch.equal(b.state(i), ref[i]), i
+    b.close()
+
+
+def test_batch_lattice_matches_oracle(orc):
+    from paper_1809_02390_gb300 import Batch
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    r = inputs.droplet(48, 40, 10, 4, p.rho_g, p.rho_l)
+    other = inputs.slab(70, 30, 35, 4, p.rho_g, p.rho_l)
+    b = Batch([other, r], [dict(Tr=0.8), dict(Tr=0.85, K_int=1.0)])
+    b.run(100)
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, r), 100))[0]
+    assert rel_inf(b.density(1).cpu().numpy(), ref) <= 2e-5
+    b.close()
