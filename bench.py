@@ -37,7 +37,7 @@ BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 popula
 KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_02390_gb300/csrc/lbm_device.cuh"]
 NCU_TRAFFIC = {
     # 2048^2 capture (profiles/k_step_fused_fp32_2048_full.md) scaled x4 to 4096^2.
-    ("k_step_fused<float,float>", "a72ef00d530669bb"): 1075540000,
+    ("k_step_fused<float,float>", "06e84bc8d90550ff"): 1079328768,
 }
 
 
@@ -175,6 +175,131 @@ def cpu_baseline(rho0, seconds: float = 12.0) -> dict:
             "sample": "%d steps of the FP64 oracle on a 256x256 periodic crop of the workload" % steps}
 
 
+def measure_adjoint(n: int, torch) -> dict:
+    """Adjoint (lb_adjoint_steps, a 45-step checkpoint segment) against the forward step, FP32."""
+    from paper_1809_02390_gb300 import Lattice, capi
+
+    rho0, _ = workload_rho(n, seed=0)
+    lat = Lattice(rho0, precision="fp32", Tr=TR)
+    lat.step(5)
+    st = lat.state().clone()
+    lam = torch.randn((9, n, n), dtype=torch.float32, device="cuda")
+    dth = torch.zeros(3, dtype=torch.float64, device="cuda")
+    nscr = capi.lb_adjoint_steps_scratch_bytes(lat.p)
+    scr = torch.empty(nscr, dtype=torch.uint8, device="cuda")
+    k = 45
+    states = [st.data_ptr()] * k
+    capi.lb_adjoint_steps(lat.h, states, lam.data_ptr(), dth.data_ptr(), scr.data_ptr(), nscr)
+    s = lat.stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record(s)
+    lat.step(k)
+    e[1].record(s)
+    capi.lb_adjoint_steps(lat.h, states, lam.data_ptr(), dth.data_ptr(), scr.data_ptr(), nscr)
+    e[2].record(s)
+    torch.cuda.synchronize()
+    fw, ad = e[0].elapsed_time(e[1]) / k, e[1].elapsed_time(e[2]) / k
+    lat.close()
+    return {"lattice": [n, n], "dtype": "f32", "steps": k, "forward_ms_per_step": round(fw, 5),
+            "adjoint_ms_per_step": round(ad, 5), "adjoint_over_forward": round(ad / fw, 3),
+            "adjoint_bytes_per_node": 124, "adjoint_GBps_algorithmic": round(124 * n * n / (ad * 1e-3) / 1e9, 1)}
+
+
+def batch_workload(n_lattices: int = 256, seed: int = 0):
+    """256 lattices: side log-uniform in [64, 1024], Tr uniform in [0.65, 0.95],
+    interface width W uniform in [3, 8] (K_int = W / W1(Tr)), droplet (R = L/4)
+    or slab (thickness L/2) by a seeded coin."""
+    from paper_1809_02390_gb300 import derive, inputs
+
+    rhos, kws, meta = [], [], []
+    for sp in inputs.batch_specs(n_lattices, seed=seed):
+        nx, ny = sp["nx"], sp["ny"]
+        d = derive(nx, ny, Tr=sp["Tr"])
+        rg, rl = d["rho_g"], d["rho_l"]
+        if sp["shape"] == "droplet":
+            r = inputs.droplet(nx, ny, nx / 4, sp["W"], rg, rl)
+        else:
+            r = inputs.slab(nx, ny, nx / 2, sp["W"], rg, rl)
+        rhos.append(r)
+        kws.append(dict(Tr=sp["Tr"], K_int=sp["W"] / d["W1"]))
+        meta.append(dict(sp, rho_g=rg, rho_l=rl))
+    return rhos, kws, meta
+
+
+def measure_batch(torch, single_mlups: float, steps: int) -> dict:
+    from paper_1809_02390_gb300 import Batch
+
+    rhos, kws, meta = batch_workload()
+    nodes = sum(r.size for r in rhos)
+    b = Batch(rhos, kws)
+    b.tune(4)
+    cfg = b.config()
+    s = b.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.run(64)
+    s.synchronize()
+    e0.record(s)
+    b.run(steps)
+    e1.record(s)
+    s.synchronize()
+    ms = e0.elapsed_time(e1)
+    mlups = nodes * steps / (ms * 1e-3) / 1e6
+    # Coexistence curve: bulk densities (centre = liquid, corner / edge column = gas) against Maxwell.
+    import numpy as np
+
+    eg, el, curve, unstable = [], [], [], []
+    for i, m in enumerate(meta):
+        rho = b.density(i).cpu().numpy()
+        ny, nx = rho.shape
+        liq, gas = float(rho[ny // 2, nx // 2]), float(rho[0, 0])
+        if not np.isfinite(rho).all():
+            unstable.append({"side": m["nx"], "Tr": round(m["Tr"], 4), "W": round(m["W"], 3), "shape": m["shape"]})
+            continue
+        eg.append(abs(gas / m["rho_g"] - 1))
+        el.append(abs(liq / m["rho_l"] - 1))
+        curve.append([round(m["Tr"], 4), round(gas, 5), round(liq, 5), round(m["rho_g"], 5), round(m["rho_l"], 5)])
+    b.close()
+
+    return {"lattices": len(rhos), "nodes": nodes, "steps": steps, "ms": round(ms, 2), "MLUPS": round(mlups, 1),
+            "ratio_vs_single_lattice": round(mlups / single_mlups, 4), "tuned": cfg,
+            "launch": "one multi-lattice kernel per step (blocks_per_sm 0: one block per tile, else persistent), "
+                      "graph replay of 64 steps",
+            "unstable_lattices": unstable,
+            "coexistence_vs_maxwell": {"lattices": len(eg),"gas_rel_err_median": round(float(np.median(eg)), 5),
+                                       "gas_rel_err_max": round(float(np.max(eg)), 5),
+                                       "liquid_rel_err_median": round(float(np.median(el)), 5),
+                                       "liquid_rel_err_max": round(float(np.max(el)), 5),
+                                       "columns": ["Tr", "rho_gas", "rho_liquid", "maxwell_gas", "maxwell_liquid"],
+                                       "first_8": curve[:8]}}
+
+
+def measure_calibration(torch, iterations: int = 50) -> dict:
+    """256 x 256 FP32, perturbed ellipse (axis ratio 1.5, area of an R = 40 disk),
+    2,000 steps, checkpoints every 45; target made at (Tr, G2, K_int) = (0.8, G2_ref, 1)."""
+    from paper_1809_02390_gb300 import inputs
+    from paper_1809_02390_gb300.adjoint import RolloutSpec, calibrate, density, initial_state, rollout
+
+    n, steps = 256, 2000
+    spec = RolloutSpec(n, n, precision="fp32", Tr_ref=TR, K_int_ref=1.0)
+    ref = torch.tensor([TR, spec.G2_ref, 1.0], dtype=torch.float64)
+    a = 40 * 1.5 ** 0.5
+    rho0 = inputs.ellipse(n, n, a, 40 * 40 / a, 5.0, spec.rho_g, spec.rho_l, noise=0.01, seed=0)
+    f0 = initial_state(spec, rho0, ref)
+    with torch.no_grad():
+        target = density(rollout(ref, f0, spec, steps, 45), spec).detach()
+    start = ref * torch.tensor([0.97, 1.05, 1.08], dtype=torch.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta, losses = calibrate(spec, f0, target, start, steps, iterations=iterations, lr=0.01, checkpoint_every=45)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rel = lambda t: [round(float(v), 5) for v in ((t - ref) / ref)]
+    return {"lattice": [n, n], "steps_per_rollout": steps, "checkpoint_every": 45, "iterations": iterations,
+            "seconds": round(dt, 2), "loss_first": losses[0], "loss_last": losses[-1],
+            "rel_error_start": rel(start), "rel_error_fit": rel(theta), "params": ["Tr", "G2", "K_int"]}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores; each step is one
     oracle time step on a 128 x 128 periodic crop of the workload."""
@@ -281,6 +406,14 @@ def run_ours(args):
            "d2h_bytes_per_step": round(nodes * 4 / args.steps, 1),
            "note": "lb_init from pinned host densities, K steps, lb_moments, density read back; bytes amortised per step"}
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras["adjoint"] = measure_adjoint(n, torch)
+        torch.cuda.empty_cache()
+        extras["batch"] = measure_batch(torch, value, args.batch_steps)
+        torch.cuda.empty_cache()
+        extras["calibration"] = measure_calibration(torch)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -301,7 +434,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
                        "parallelism": "independent lattice per GPU" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clk.summary(), "variants": variants,
+            "clocks": clk.summary(), "variants": variants, **extras,
             "check": {"mass": sane["mass"], "rho_min": sane["rho_min"], "rho_max": sane["rho_max"]}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -316,6 +449,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=N_SIDE, help="lattice side (profiling runs use smaller cases)")
     ap.add_argument("--only-main", action="store_true", help="time the FP32 fused step only (profiling)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batch and calibration runs")
+    ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the 256-lattice batch run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -220,9 +220,11 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
                   size_t meta_bytes, const double* rho0, int rho0_on_device, void* stream);
 /* Advances every lattice by nsteps. */
 int lb_batch_run(lb_batch* b, int64_t nsteps);
-/* Autotuner: times each (tile height 16 or 32, resident blocks per SM) pair for
- * trial_steps steps on the batch itself (advancing it) and keeps the fastest;
- * writes its time per step. */
+/* Autotuner: times each launch shape (tile height 16 or 32, register budget, and
+ * either one block per tile or a persistent grid of 1..max resident blocks per SM)
+ * for trial_steps steps on the batch itself (advancing it) and keeps the fastest;
+ * writes its time per step.  lb_batch_config reports blocks_per_sm = 0 for the
+ * one-block-per-tile grid. */
 int lb_batch_tune(lb_batch* b, int trial_steps, double* best_ms_per_step);
 int lb_batch_config(const lb_batch* b, int* tile_y, int* blocks_per_sm, int* grid);
 /* Device pointer of the pool holding the current state; element offset of lattice i. */

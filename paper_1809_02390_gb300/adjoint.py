@@ -137,3 +137,25 @@ def initial_state(spec: RolloutSpec, rho0, theta):
 def density(state, spec: RolloutSpec):
     """rho = sum_i f_i of a state tensor (the weights of the storage shift sum to 1)."""
     return state.sum(0) + spec.rho_ref
+
+
+def calibrate(spec: RolloutSpec, f0, target, theta0, nsteps: int, iterations: int = 50, lr: float = 0.02,
+              checkpoint_every: int | None = None):
+    """Fits theta = (Tr, G2, K_int) so that the density after ``nsteps`` steps from
+    ``f0`` matches ``target`` (loss = sum (rho - target)^2), with Adam on the
+    relative deviations theta = theta0 (1 + delta).  Returns (theta, losses)."""
+    import torch
+
+    base = theta0.detach().clone().double()
+    delta = torch.zeros(3, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([delta], lr=lr)
+    losses = []
+    for _ in range(iterations):
+        opt.zero_grad()
+        theta = base * (1.0 + delta)
+        out = rollout(theta, f0, spec, nsteps, checkpoint_every)
+        loss = ((density(out, spec) - target) ** 2).sum()
+        loss.backward()
+        losses.append(float(loss.detach()))
+        opt.step()
+    return (base * (1.0 + delta)).detach(), losses

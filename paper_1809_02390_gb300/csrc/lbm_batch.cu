@@ -32,48 +32,93 @@ struct BatchLattice {
   int tiles_x;       // tiles per row of tiles
 };
 
-constexpr int kShapes = 2;
-constexpr int kShapeTY[kShapes] = {16, 32};
+// Launch shapes the autotuner chooses among: tile height and the register budget
+// the kernel is compiled for (resident blocks per SM it must allow).
+constexpr int kShapes = 3;
+constexpr int kShapeTY[kShapes] = {16, 16, 32};
+constexpr int kShapeMinBlocks[kShapes] = {4, 3, 2};
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: the pools end where they started)
 
 // Register budget of 64 per thread (4 blocks of 256 or 2 of 512 threads per SM),
 // as for the single-lattice kernel.
-template <typename store_t, int TY>
-__global__ void __launch_bounds__(TileShape<TY>::threads, 1024 / TileShape<TY>::threads)
+// One record per tile: its lattice, origin and the lattice's size and pool offset.
+struct TileRec {
+  int lat, x0, y0, nx, ny, pad;
+  long long offset;
+};
+
+// The coefficients shared by all lattices (varpi, rates, EOS constants) come from
+// the kernel parameters; the ten that depend on each lattice's Tr, K_int, G2 and
+// storage shift are staged in shared memory when the block moves to a new lattice,
+// one 32-bit word per thread, stored after the tile's pulls are issued.  In the
+// persistent mode the next tile's record and coefficient word are fetched while
+// the current tile is processed.
+constexpr int kCoefWords = int(sizeof(LatCoef<f2>) / sizeof(int));
+
+struct StoreCoef {
+  LatCoef<f2>* cs;
+  int word;
+  bool store;
+  __device__ void operator()() const {
+    if (store && threadIdx.x < kCoefWords) reinterpret_cast<int*>(cs)[threadIdx.x] = word;
+  }
+};
+
+template <typename store_t, int TY, int MINB, bool PERSIST>
+__global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
     k_step_batch(const store_t* __restrict__ pool_in, store_t* __restrict__ pool_out,
-                 const BatchLattice* __restrict__ desc, const VCoef<f2>* __restrict__ coef, int n,
-                 int total_tiles) {
+                 const TileRec* __restrict__ tiles, const LatCoef<f2>* __restrict__ coef, int total_tiles,
+                 VCoef<f2> common) {
+  static_assert(kCoefWords <= TileShape<TY>::threads, "one coefficient word per thread");
   __shared__ float rs[TY + 2][kTileX + 2];
-  __shared__ VCoef<f2> cs;
+  __shared__ LatCoef<f2> cs;
+  int t = blockIdx.x;
+  if (t >= total_tiles) return;
+  TileRec ti = tiles[t];
+  int word = threadIdx.x < kCoefWords ? reinterpret_cast<const int*>(coef + ti.lat)[threadIdx.x] : 0;
+  if constexpr (!PERSIST) {  // one block per tile
+    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, common, cs, ti.x0, ti.y0,
+                               rs, StoreCoef{&cs, word, true});
+    return;
+  }
   int last = -1;
-  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    // Lattice of tile t: last descriptor with tile_start <= t (same for the whole block).
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (desc[mid].tile_start <= t)
-        lo = mid;
-      else
-        hi = mid - 1;
+  for (;;) {
+    const int tn = t + gridDim.x;
+    TileRec tin = ti;
+    int wordn = word;
+    if (tn < total_tiles) {
+      tin = tiles[tn];
+      if (threadIdx.x < kCoefWords) wordn = reinterpret_cast<const int*>(coef + tin.lat)[threadIdx.x];
     }
-    const BatchLattice L = desc[lo];
-    if (lo != last) {
-      const int* src = reinterpret_cast<const int*>(coef + lo);
-      int* dst = reinterpret_cast<int*>(&cs);
-      for (int w = threadIdx.x; w < int(sizeof(VCoef<f2>) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-      __syncthreads();
-      last = lo;
-    }
-    const int local = t - L.tile_start;
-    const int tyi = local / L.tiles_x, txi = local - tyi * L.tiles_x;
-    step_tile<f2, store_t, TY>(pool_in + L.offset, pool_out + L.offset, L.nx, L.ny, cs, txi * kTileX, tyi * TY, rs);
+    const StoreCoef hook{&cs, word, ti.lat != last};
+    last = ti.lat;
+    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, common, cs, ti.x0, ti.y0,
+                               rs, hook);
+    if (tn >= total_tiles) break;
     __syncthreads();  // shared densities and coefficients are reused by the next tile
+    t = tn;
+    ti = tin;
+    word = wordn;
   }
 }
 
-template <int TY>
-const void* batch_kernel() {
-  return reinterpret_cast<const void*>(k_step_batch<float, TY>);
+template <int TY, int MINB>
+void launch_shape(const float* in, float* out, const TileRec* tiles, const LatCoef<f2>* coef, int total, int bps,
+                  int sms, const VCoef<f2>& common, cudaStream_t st) {
+  if (bps > 0)
+    k_step_batch<float, TY, MINB, true><<<bps * sms, TileShape<TY>::threads, 0, st>>>(in, out, tiles, coef, total,
+                                                                                        common);
+  else
+    k_step_batch<float, TY, MINB, false><<<total, TileShape<TY>::threads, 0, st>>>(in, out, tiles, coef, total,
+                                                                                     common);
+}
+
+const void* batch_kernel(int shape) {
+  switch (shape) {
+    case 0: return reinterpret_cast<const void*>(k_step_batch<float, 16, 4, true>);
+    case 1: return reinterpret_cast<const void*>(k_step_batch<float, 16, 3, true>);
+    default: return reinterpret_cast<const void*>(k_step_batch<float, 32, 2, true>);
+  }
 }
 
 }  // namespace
@@ -87,7 +132,9 @@ struct lb_batch {
   void* pool[2];
   int cur;
   BatchLattice* d_desc[kShapes];
-  VCoef<f2>* d_coef;
+  TileRec* d_tiles[kShapes];
+  LatCoef<f2>* d_coef;
+  VCoef<f2> common;
   cudaStream_t stream;
   int sms;
   int shape;          // index into kShapeTY
@@ -113,8 +160,8 @@ int berr(lb_batch* b, int code, const char* fmt, const char* detail = "") {
 size_t lattice_elems(const lb_params& p) { return ((9 * size_t(p.nx) * p.ny + 63) / 64) * 64; }
 
 int max_blocks(lb_batch* b, int shape, int* out) {
-  const void* k = shape == 0 ? batch_kernel<16>() : batch_kernel<32>();
-  const int threads = shape == 0 ? TileShape<16>::threads : TileShape<32>::threads;
+  const void* k = batch_kernel(shape);
+  const int threads = kShapeTY[shape] == 16 ? TileShape<16>::threads : TileShape<32>::threads;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, threads, 0);
   if (e != cudaSuccess) return berr(b, LB_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
   if (*out < 1) *out = 1;
@@ -124,13 +171,17 @@ int max_blocks(lb_batch* b, int shape, int* out) {
 void launch_one(lb_batch* b, int from) {
   const float* in = static_cast<const float*>(b->pool[from]);
   float* out = static_cast<float*>(b->pool[1 - from]);
-  const int grid = b->blocks_per_sm * b->sms;
-  if (b->shape == 0)
-    k_step_batch<float, 16><<<grid, TileShape<16>::threads, 0, b->stream>>>(in, out, b->d_desc[0], b->d_coef, b->n,
-                                                                           b->total_tiles[0]);
+  // blocks_per_sm = 0: one block per tile (the hardware schedules the tiles);
+  // otherwise a persistent grid whose blocks walk the tile list.
+  const int s = b->shape;
+  const TileRec* tiles = b->d_tiles[s];
+  const int total = b->total_tiles[s];
+  if (s == 0)
+    launch_shape<16, 4>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
+  else if (s == 1)
+    launch_shape<16, 3>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
   else
-    k_step_batch<float, 32><<<grid, TileShape<32>::threads, 0, b->stream>>>(in, out, b->d_desc[1], b->d_coef, b->n,
-                                                                           b->total_tiles[1]);
+    launch_shape<32, 2>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
 }
 
 int config_id(const lb_batch* b) { return b->shape * 64 + b->blocks_per_sm; }
@@ -169,9 +220,17 @@ size_t lb_batch_pool_bytes(const lb_params* ps, int n) {
   return e * sizeof(float);
 }
 
+size_t total_tiles_of(const lb_params* ps, int n, int TY) {
+  size_t t = 0;
+  for (int i = 0; i < n; ++i) t += size_t((ps[i].nx + kTileX - 1) / kTileX) * ((ps[i].ny + TY - 1) / TY);
+  return t;
+}
+
 size_t lb_batch_meta_bytes(const lb_params* ps, int n) {
   if (!ps || n < 1) return 0;
-  return size_t(n) * (kShapes * sizeof(BatchLattice) + sizeof(VCoef<f2>)) + 1024;
+  size_t tiles = 0;
+  for (int s = 0; s < kShapes; ++s) tiles += total_tiles_of(ps, n, kShapeTY[s]);
+  return size_t(n) * (kShapes * sizeof(BatchLattice) + sizeof(LatCoef<f2>)) + tiles * sizeof(TileRec) + 4096;
 }
 
 int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
@@ -197,7 +256,7 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     delete b;
     return code;
   };
-  std::vector<VCoef<f2>> h_coef(n);
+  std::vector<LatCoef<f2>> h_coef(n);
   std::vector<VCoef<double>> h_coefd(n);
   size_t off = 0, total_nodes = 0;
   for (int i = 0; i < n; ++i) {
@@ -209,7 +268,17 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
       return bail(LB_EINVAL, m);
     }
     b->p[i].rho_ref = double(float(ps[i].rho_ref));
-    h_coef[i] = make_vcoef<f2>(b->p[i], b->d[i]);
+    const VCoef<f2> full = make_vcoef<f2>(b->p[i], b->d[i]);
+    if (i == 0) b->common = full;
+    // Everything but the per-lattice part must agree across the batch.
+    const lb_derived& d0 = b->d[0];
+    const lb_derived& di = b->d[i];
+    if (ps[i].eos != ps[0].eos || ps[i].eos_a != ps[0].eos_a || ps[i].eos_b != ps[0].eos_b || di.k != d0.k ||
+        di.s_e != d0.s_e || di.s_eps != d0.s_eps || di.s_q != d0.s_q || di.s_p != d0.s_p)
+      return bail(LB_ENOTSUP,
+                  "lb_batch_init: lattices of one batch must share the EOS (kind, a, b), varpi and the relaxation rates");
+    h_coef[i] = LatCoef<f2>{full.G2,        full.rho_ref, full.m2rr, full.lam_RT, full.neg_lam_a,
+                            full.neg_2lam_a, full.g15,     full.Q1G2, full.Q2G2,   full.Q78G2};
     h_coefd[i] = make_vcoef<double>(b->p[i], b->d[i]);
     for (int s = 0; s < kShapes; ++s) {
       BatchLattice L;
@@ -231,16 +300,36 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     }
     b->total_tiles[s] = start;
   }
-  // Metadata in the caller's buffer: descriptors per tile shape, then coefficients.
-  char* m = static_cast<char*>(meta);
-  b->d_desc[0] = reinterpret_cast<BatchLattice*>(m);
-  b->d_desc[1] = b->d_desc[0] + n;
-  b->d_coef = reinterpret_cast<VCoef<f2>*>(((reinterpret_cast<uintptr_t>(b->d_desc[1] + n) + 255) / 256) * 256);
+  // Metadata in the caller's buffer: descriptors and tile records per tile shape,
+  // then coefficients, each 256-byte aligned.
+  auto align = [](uintptr_t v) { return (v + 255) / 256 * 256; };
+  std::vector<TileRec> h_tiles[kShapes];
+  for (int s = 0; s < kShapes; ++s) {
+    h_tiles[s].reserve(b->total_tiles[s]);
+    for (int i = 0; i < n; ++i) {
+      const int tyn = (ps[i].ny + kShapeTY[s] - 1) / kShapeTY[s];
+      for (int r = 0; r < tyn; ++r)
+        for (int q = 0; q < b->desc[s][i].tiles_x; ++q)
+          h_tiles[s].push_back(TileRec{i, q * kTileX, r * kShapeTY[s], ps[i].nx, ps[i].ny, 0, b->desc[s][i].offset});
+    }
+  }
+  uintptr_t m = align(reinterpret_cast<uintptr_t>(meta));
+  for (int s = 0; s < kShapes; ++s) {
+    b->d_desc[s] = reinterpret_cast<BatchLattice*>(m);
+    m = align(m + n * sizeof(BatchLattice));
+    b->d_tiles[s] = reinterpret_cast<TileRec*>(m);
+    m = align(m + h_tiles[s].size() * sizeof(TileRec));
+  }
+  b->d_coef = reinterpret_cast<LatCoef<f2>*>(m);
   cudaError_t e = cudaSuccess;
-  for (int s = 0; s < kShapes && e == cudaSuccess; ++s)
+  for (int s = 0; s < kShapes && e == cudaSuccess; ++s) {
     e = cudaMemcpyAsync(b->d_desc[s], b->desc[s].data(), n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_tiles[s], h_tiles[s].data(), h_tiles[s].size() * sizeof(TileRec),
+                          cudaMemcpyHostToDevice, b->stream);
+  }
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_coef, h_coef.data(), n * sizeof(VCoef<f2>), cudaMemcpyHostToDevice, b->stream);
+    e = cudaMemcpyAsync(b->d_coef, h_coef.data(), n * sizeof(LatCoef<f2>), cudaMemcpyHostToDevice, b->stream);
   int dev = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -306,7 +395,7 @@ int lb_batch_tune(lb_batch* b, int trial_steps, double* best_ms_per_step) {
   for (int s = 0; s < kShapes; ++s) {
     int mb = 1;
     if (max_blocks(b, s, &mb) != LB_OK) return LB_ECUDA;
-    for (int bps = 1; bps <= mb; ++bps) {
+    for (int bps = 0; bps <= mb; ++bps) {
       b->shape = s;
       b->blocks_per_sm = bps;
       launch_one(b, b->cur);  // warm-up (two launches keep the pool parity)
@@ -342,7 +431,7 @@ int lb_batch_config(const lb_batch* b, int* tile_y, int* blocks_per_sm, int* gri
   if (!b) return LB_EINVAL;
   if (tile_y) *tile_y = kShapeTY[b->shape];
   if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
-  if (grid) *grid = b->blocks_per_sm * b->sms;
+  if (grid) *grid = b->blocks_per_sm > 0 ? b->blocks_per_sm * b->sms : b->total_tiles[b->shape];
   return LB_OK;
 }
 

@@ -92,15 +92,28 @@ struct VCoef {
       quarter;
 };
 
+// The coefficients that depend on the lattice's temperature, pressure scale,
+// interaction strength and storage shift (everything else depends only on
+// varpi, the relaxation rates and the EOS constants a, b).
+template <typename V>
+struct LatCoef {
+  V G2, rho_ref, m2rr, lam_RT, neg_lam_a, neg_2lam_a, g15, Q1G2, Q2G2, Q78G2;
+};
+
+template <typename V>
+__device__ __forceinline__ LatCoef<V> lattice_part(const VCoef<V>& c) {
+  return LatCoef<V>{c.G2, c.rho_ref, c.m2rr, c.lam_RT, c.neg_lam_a, c.neg_2lam_a, c.g15, c.Q1G2, c.Q2G2, c.Q78G2};
+}
+
 // p_EOS / c^2 and d(p_EOS/c^2)/drho.  vdW: rho R T/(1 - b rho) - a rho^2;
 // Carnahan-Starling (Eq. 20) with t = b rho / 4.  Both times K_EOS / c^2.
 template <typename V>
-__device__ __forceinline__ void eos(const VCoef<V>& c, V rho, V& pe, V& dpe) {
+__device__ __forceinline__ void eos(const VCoef<V>& c, const LatCoef<V>& l, V rho, V& pe, V& dpe) {
   if (c.eos == LB_EOS_VDW) {
     const V io = rcp(fmav(c.neg_bq, rho, c.one));
-    const V q = c.lam_RT * io;                       // lam R T / (1 - b rho)
-    pe = rho * fmav(c.neg_lam_a, rho, q);            // lam (rho R T/(1 - b rho) - a rho^2)
-    dpe = fmav(q, io, c.neg_2lam_a * rho);           // lam (R T/(1 - b rho)^2 - 2 a rho)
+    const V q = l.lam_RT * io;                       // lam R T / (1 - b rho)
+    pe = rho * fmav(l.neg_lam_a, rho, q);            // lam (rho R T/(1 - b rho) - a rho^2)
+    dpe = fmav(q, io, l.neg_2lam_a * rho);           // lam (R T/(1 - b rho)^2 - 2 a rho)
   } else {
     const V t = c.bq * rho;
     const V io = rcp(c.one - t);
@@ -109,24 +122,30 @@ __device__ __forceinline__ void eos(const VCoef<V>& c, V rho, V& pe, V& dpe) {
     const V z = fmav(t2, c.one - t, c.one + t) * io3;                              // (1+t+t^2-t^3)/(1-t)^3
     const V poly = fmav(t2, fmav(t, t - c.four, c.four), fmav(c.four, t, c.one));  // 1+4t+4t^2-4t^3+t^4
     const V dz = poly * io3 * io;
-    pe = rho * fmav(c.neg_lam_a, rho, c.lam_RT * z);
-    dpe = fmav(c.lam_RT, dz, c.neg_2lam_a * rho);
+    pe = rho * fmav(l.neg_lam_a, rho, l.lam_RT * z);
+    dpe = fmav(l.lam_RT, dz, l.neg_2lam_a * rho);
   }
+}
+
+template <typename V>
+__device__ __forceinline__ void eos(const VCoef<V>& c, V rho, V& pe, V& dpe) {
+  eos(c, lattice_part(c), rho, pe, dpe);
 }
 
 // One node (or a pair of nodes for V = f2).  d: post-streaming populations
 // stored as deviations f_i - w_i rho_ref; (Sx, Sy) = sum_i omega_i rho(x + e_i) e_i
 // (Eq. 12, = grad rho of supplement Eq. 61); o: post-collision deviations.
 template <typename V>
-__device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx, V Sy, V (&o)[9]) {
+__device__ __forceinline__ void collide(const VCoef<V>& c, const LatCoef<V>& l, const V (&d)[9], V Sx, V Sy,
+                                        V (&o)[9]) {
   // Moment transform (supplement Eq. 4) with shared sums; M w = (1, -2, 1, 0, ...).
   const V a13 = d[1] + d[3], a24 = d[2] + d[4], a57 = d[5] + d[7], a68 = d[6] + d[8];
   const V s13 = d[1] - d[3], s24 = d[2] - d[4], s57 = d[5] - d[7], s68 = d[6] - d[8];
   const V axis = a13 + a24, diag = a57 + a68;
   const V rho_dev = d[0] + (axis + diag);
-  const V rho = rho_dev + c.rho_ref;
-  const V m1 = fmav(c.m4, d[0], fmav(c.two, diag, c.m2rr) - axis);       // -4 d0 - axis + 2 diag - 2 rho_ref
-  const V m2 = fmav(c.four, d[0], fmav(c.m2, axis, diag + c.rho_ref));   //  4 d0 - 2 axis + diag + rho_ref
+  const V rho = rho_dev + l.rho_ref;
+  const V m1 = fmav(c.m4, d[0], fmav(c.two, diag, l.m2rr) - axis);       // -4 d0 - axis + 2 diag - 2 rho_ref
+  const V m2 = fmav(c.four, d[0], fmav(c.m2, axis, diag + l.rho_ref));   //  4 d0 - 2 axis + diag + rho_ref
   const V dm = s57 - s68, dp = s57 + s68;
   const V jx = s13 + dm, jy = s24 + dp;
   const V m4 = fmav(c.m2, s13, dm);
@@ -135,7 +154,7 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx
   const V m8 = a57 - a68;
 
   // Interaction force (Eq. 12) and velocity (Eq. 5), c = 1.
-  const V G2rho = c.G2 * rho;
+  const V G2rho = l.G2 * rho;
   const V Fx = G2rho * Sx, Fy = G2rho * Sy;
   const V inv_rho = rcp(rho);
   const V ux = fmav(c.half, Fx, jx) * inv_rho;
@@ -144,8 +163,8 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx
   // Self-tuning EOS: p_LBE = p_EOS + G^2 rho^2/2 (Eq. 18) = c_s^2 (rho + eta);
   // grad p_LBE = (p_EOS' + G^2 rho) grad rho (supplement Eq. 61).
   V pe, dpe;
-  eos(c, rho, pe, dpe);
-  const V eta = fmav(c.three, pe, rho * fmav(c.g15, rho, c.mone));  // 3 pe + 1.5 G2 rho^2 - rho
+  eos(c, l, rho, pe, dpe);
+  const V eta = fmav(c.three, pe, rho * fmav(l.g15, rho, c.mone));  // 3 pe + 1.5 G2 rho^2 - rho
   const V g = G2rho + dpe;
 
   const V x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2;
@@ -192,18 +211,18 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx
   const V corr8 = fmav(c.R81 * xy, A1, fmav(c.R88 * u2, A8, cr8));
   // (5): mbar = m_eq - D + 2 A - corrections; (6): + S Q_m with |F~|^2 = G^2 |S|^2.
   const V sxx = Sx * Sx, syy = Sy * Sy, ss = sxx + syy;
-  const V mb1 = fmav(c.Q1G2, ss, fmav(c.two, A1, meq1 - D1) - corr1);
-  const V mb2 = fmav(c.Q2G2, ss, fmav(c.two, A2, meq2 - D2));
+  const V mb1 = fmav(l.Q1G2, ss, fmav(c.two, A1, meq1 - D1) - corr1);
+  const V mb2 = fmav(l.Q2G2, ss, fmav(c.two, A2, meq2 - D2));
   const V mb4 = fmav(c.two, A4, meq4 - D4);
   const V mb6 = fmav(c.two, A6, meq6 - D6);
-  const V mb7 = fmav(c.Q78G2, sxx - syy, fmav(c.two, A7, meq7 - D7) - corr7);
-  const V mb8 = fmav(c.Q78G2 * Sx, Sy, fmav(c.two, A8, meq8 - D8) - corr8);
+  const V mb7 = fmav(l.Q78G2, sxx - syy, fmav(c.two, A7, meq7 - D7) - corr7);
+  const V mb8 = fmav(l.Q78G2 * Sx, Sy, fmav(c.two, A8, meq8 - D8) - corr8);
 
   // Inverse transform M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4),
   // applied to mbar - rho_ref M w (deviation storage); conserved: rho, j + F.
   const V n0 = rho_dev * c.ninth;
-  const V n1 = fmav(c.two, c.rho_ref, mb1) * c.i36;
-  const V n2 = (mb2 - c.rho_ref) * c.i36;
+  const V n1 = fmav(c.two, l.rho_ref, mb1) * c.i36;
+  const V n2 = (mb2 - l.rho_ref) * c.i36;
   const V n3 = (jx + Fx) * c.sixth;
   const V n4 = mb4 * c.i12;
   const V n5 = (jy + Fy) * c.sixth;
@@ -223,6 +242,11 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx
   o[6] = bm8 + (qy - qx);
   o[7] = bd8 - (qx + qy);
   o[8] = bm8 + (qx - qy);
+}
+
+template <typename V>
+__device__ __forceinline__ void collide(const VCoef<V>& c, const V (&d)[9], V Sx, V Sy, V (&o)[9]) {
+  collide(c, lattice_part(c), d, Sx, Sy, o);
 }
 
 // Force stencil of Eq. 12 from the densities of the 8 neighbours

@@ -72,11 +72,18 @@ struct TileShape {
   static constexpr int ring = 2 * (kTileX + 2) + 2 * TY;
 };
 
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
 // rs: shared array of (TY + 2) x (TX + 2) densities.  (x0, y0): tile origin.
-template <typename V, typename store_t, int TY>
+// before_sync() runs after all phase-1 loads are issued and before the block
+// barrier (the batched kernel stores its lattice coefficients there).
+template <typename V, typename store_t, int TY, typename Hook = NoHook>
 __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
-                                          int ny, const VCoef<V>& c, int x0, int y0,
-                                          typename LaneType<V>::type (*rs)[kTileX + 2]) {
+                                          int ny, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
+                                          typename LaneType<V>::type (*rs)[kTileX + 2],
+                                          const Hook& before_sync = Hook()) {
   using real = typename LaneType<V>::type;
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
@@ -114,6 +121,7 @@ __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
   if (ring) rs[wy][wx] = sum9(g);
+  before_sync();
   __syncthreads();
 
   real Sx[kTileRows], Sy[kTileRows];
@@ -130,7 +138,7 @@ __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store
     for (int i = 0; i < 9; ++i) d[i].v = make_float2(f[0][i], f[1][i]);
     sx.v = make_float2(Sx[0], Sx[1]);
     sy.v = make_float2(Sy[0], Sy[1]);
-    collide(c, d, sx, sy, o);
+    collide(c, l, d, sx, sy, o);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       out[0][i] = o[i].v.x;
@@ -138,7 +146,7 @@ __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < kTileRows; ++k) collide(c, f[k], Sx[k], Sy[k], out[k]);
+    for (int k = 0; k < kTileRows; ++k) collide(c, l, f[k], Sx[k], Sy[k], out[k]);
   }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
@@ -155,7 +163,8 @@ template <typename V, typename store_t>
 __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
     k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c) {
   __shared__ typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
-  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, c, blockIdx.x * kTileX, blockIdx.y * kTileY, rs);
+  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
+                                rs);
 }
 
 // Two-pass variant, pass 1: density plane rho_dev(x) = sum_i fbar_i(x - e_i).

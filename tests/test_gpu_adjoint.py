@@ -184,3 +184,21 @@ def test_fused_segment_equals_single_steps(orc, precision, tol):
     torch.cuda.synchronize()
     assert float((a - c).abs().max()) <= tol * float(a.abs().max())
     assert float((th1 - th2).abs().max()) <= tol * float(th1.abs().max())
+
+
+def test_calibration_recovers_parameters():
+    """Gradient-based calibration through the adjoint: a target density field made at
+    reference (Tr, G2, K_int) is fitted from perturbed parameters."""
+    from paper_1809_02390_gb300.adjoint import RolloutSpec, calibrate, density, initial_state, rollout
+
+    n = 64
+    spec = RolloutSpec(n, n, precision="fp32", Tr_ref=0.8, K_int_ref=1.0)
+    ref = torch.tensor([0.8, spec.G2_ref, 1.0], dtype=torch.float64)
+    rho0 = inputs.ellipse(n, n, 12 * 1.5 ** 0.5, 12 / 1.5 ** 0.5, 4.0, spec.rho_g, spec.rho_l, noise=0.01, seed=1)
+    f0 = initial_state(spec, rho0, ref)
+    with torch.no_grad():
+        target = density(rollout(ref, f0, spec, 300), spec).detach()
+    start = ref * torch.tensor([0.96, 1.05, 0.93], dtype=torch.float64)
+    theta, losses = calibrate(spec, f0, target, start, 300, iterations=40, lr=0.01)
+    assert losses[-1] < 0.05 * losses[0]
+    assert float(((theta - ref) / ref).abs().max()) < 0.5 * float(((start - ref) / ref).abs().max())

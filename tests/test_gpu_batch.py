@@ -72,7 +72,7 @@ def test_autotune_keeps_the_trajectory():
     b = Batch(rhos, [dict(k) for k in kws])
     ms = b.tune(4)
     cfg = b.config()
-    assert ms > 0 and cfg["tile_y"] in (16, 32) and cfg["blocks_per_sm"] >= 1
+    assert ms > 0 and cfg["tile_y"] in (16, 32) and cfg["blocks_per_sm"] >= 0  # 0: one block per tile
     b.run(70)
     ref = _singles(rhos, kws, b.steps_done)
     for i in range(len(rhos)):
