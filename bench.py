@@ -34,10 +34,9 @@ TR = 0.8
 BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 populations
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
 # for the kernel sources they were measured on (sha256 of the files below).
-KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_02390_gb300/csrc/lbm_device.cuh"]
+KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_02390_gb300/csrc/lbm_device.cuh",
+                  "paper_1809_02390_gb300/csrc/lbm_tma.cuh"]
 NCU_TRAFFIC = {
-    # 2048^2 capture (profiles/k_step_fused_fp32_2048_full.md) scaled x4 to 4096^2.
-    ("k_step_fused<float,float>", "06e84bc8d90550ff"): 1079328768,
 }
 
 
@@ -356,6 +355,7 @@ def run_ours(args):
 
     # --- main measurement: FP32 fused, inputs resident in HBM -----------------
     lat = Lattice(rho0, precision="fp32", variant="fused", Tr=TR)
+    kernel = "k_step_tma<f2>" if capi.lb_uses_tma(lat.h) else "k_step_fused<f2,float>"
     lat.step(args.warmup)
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -419,10 +419,10 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
     src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(("k_step_fused<float,float>", src_hash))
+    traffic = NCU_TRAFFIC.get((kernel, src_hash))
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
-            "kernel": "k_step_fused<float,float>", "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
+            "kernel": kernel, "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
             "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
             "kernel_source_sha": src_hash}
     cpu = cpu_baseline(rho0) if world == 1 else None

@@ -239,6 +239,21 @@ void lb_batch_free(lb_batch* b);
 int lb_get_state(lb_handle* h, void* dst);
 int lb_set_state(lb_handle* h, const void* src);
 
+/* Synchronous health check: LB_ETIMEOUT if a kernel's bounded wait for an
+ * asynchronous tensor copy gave up since the last call (the flag is cleared),
+ * else LB_OK.  Kernels never spin without a limit. */
+int lb_status(lb_handle* h);
+
+/* 1 if the handle's FP32 fused step stages populations with tensor copies (TMA):
+ * FP32 storage, nx a multiple of 4, nx >= 104, ny >= 50; else 0. */
+int lb_uses_tma(const lb_handle* h);
+
+/* Grid of that persistent kernel (each block steps tiles b, b + blocks, ...):
+ * blocks > 0 fixes it (at most the tile count), 0 restores the default (as many
+ * blocks as can be resident).  LB_EINVAL if blocks < 0.  Results do not depend
+ * on it; it exists for tuning and for tests of the per-block tile loop. */
+int lb_set_step_blocks(lb_handle* h, int blocks);
+
 /* Derived parameters in use by the handle. */
 int lb_get_derived(const lb_handle* h, lb_derived* out);
 

@@ -82,6 +82,9 @@ SIGNATURES = [
     ("lb_get_state", ctypes.c_int, [_V, _V]),
     ("lb_set_state", ctypes.c_int, [_V, _V]),
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
+    ("lb_status", ctypes.c_int, [_V]),
+    ("lb_uses_tma", ctypes.c_int, [_V]),
+    ("lb_set_step_blocks", ctypes.c_int, [_V, ctypes.c_int]),
     ("lb_last_error", ctypes.c_char_p, [_V]),
     ("lb_free", None, [_V]),
 ]
@@ -267,6 +270,18 @@ def lb_batch_derived(b: int, i: int) -> dict:
 
 def lb_batch_free(b: int) -> None:
     lib().lb_batch_free(b)
+
+
+def lb_status(h: int) -> None:
+    check(lib().lb_status(h), h)
+
+
+def lb_uses_tma(h: int) -> bool:
+    return bool(lib().lb_uses_tma(h))
+
+
+def lb_set_step_blocks(h: int, blocks: int) -> None:
+    check(lib().lb_set_step_blocks(h, blocks), h)
 
 
 def lb_last_error(h: int | None = None) -> str:

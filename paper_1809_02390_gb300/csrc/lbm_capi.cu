@@ -7,8 +7,10 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "lbm_handle.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
@@ -146,6 +148,13 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
   const int nx = h->p.nx, ny = h->p.ny;
   if (h->variant == LB_FUSED) {
     const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
+    if constexpr (std::is_same<store_t, float>::value && std::is_same<V, f2>::value) {
+      if (h->use_tma) {
+        k_step_tma<V><<<h->tma_grid, kFusedThreads, kTmaSmem, h->stream>>>(h->tmap[h->cur], fin, fout, nx,
+                                                                                     ny, cv);
+        return;
+      }
+    }
     k_step_fused<V, store_t><<<grd, kFusedThreads, 0, h->stream>>>(fin, fout, nx, ny, cv);
   } else {
     real* rho = static_cast<real*>(h->scratch);
@@ -163,7 +172,55 @@ int configure_device(lb_handle* h) {
   return LB_OK;
 }
 
-int configure(lb_handle* h) { return configure_device(h); }
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 3-D map of one FP32 population buffer: x (nx), y (ny), plane (9); box of one
+// plane window (kTmaCols x kTmaRows).  False if the layout does not allow it.
+bool encode_map(CUtensorMap* map, void* base, int nx, int ny) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(nx) * 4) % 16 != 0) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), 9};
+  const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * ny * 4};
+  const cuuint32_t box[3] = {cuuint32_t(kTmaCols), cuuint32_t(kTmaRows), 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int configure(lb_handle* h) {
+  const int rc = configure_device(h);
+  if (rc != LB_OK) return rc;
+  // The tensor-copy path needs FP32 storage, rows of a multiple of 16 bytes and a
+  // lattice holding at least one interior tile; otherwise the plain fused kernel runs.
+  h->use_tma = h->p.precision == LB_FP32 && h->variant == LB_FUSED && h->p.nx % 4 == 0 &&
+               h->p.nx >= 2 * kTileX + kTmaCols && h->p.ny >= 2 * kTileY + kTmaRows &&
+               encode_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny) && encode_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny);
+  if (h->use_tma) {
+    // Persistent grid: as many blocks as can be resident.
+    LB_CUDA(h, cudaFuncSetAttribute(k_step_tma<f2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmem)));
+    int per_sm = 0, dev = 0, sms = 0;
+    LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<f2>, kFusedThreads, kTmaSmem));
+    LB_CUDA(h, cudaGetDevice(&dev));
+    LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int tiles = ((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY);
+    h->tma_grid_auto = per_sm < 1 ? sms : per_sm * sms;
+    if (h->tma_grid_auto > tiles) h->tma_grid_auto = tiles;
+    h->tma_grid = h->tma_grid_auto;
+  }
+  return LB_OK;
+}
 
 template <typename real, typename store_t>
 void launch_moments(lb_handle* h, real* rho, real* ux, real* uy, real rho_ref, real G2) {
@@ -382,6 +439,28 @@ int lb_set_state(lb_handle* h, const void* src) {
 int lb_get_derived(const lb_handle* h, lb_derived* out) {
   if (!h || !out) return LB_EINVAL;
   *out = h->d;
+  return LB_OK;
+}
+
+int lb_status(lb_handle* h) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  int v = 0, zero = 0;
+  LB_CUDA(h, cudaMemcpyFromSymbolAsync(&v, g_wait_error, sizeof(int), 0, cudaMemcpyDeviceToHost, h->stream));
+  LB_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (v) {
+    LB_CUDA(h, cudaMemcpyToSymbolAsync(g_wait_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, h->stream));
+    return fail(h, LB_ETIMEOUT, "a bounded wait for a tensor copy gave up");
+  }
+  return LB_OK;
+}
+
+int lb_uses_tma(const lb_handle* h) { return h && h->use_tma ? 1 : 0; }
+
+int lb_set_step_blocks(lb_handle* h, int blocks) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (blocks < 0) return fail(h, LB_EINVAL, "negative block count");
+  const int tiles = ((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY);
+  h->tma_grid = blocks == 0 ? h->tma_grid_auto : (blocks < tiles ? blocks : tiles);
   return LB_OK;
 }
 

@@ -1,6 +1,7 @@
 // Handle of one lattice (shared by the library's CUDA translation units).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_kernels.cuh"
@@ -16,6 +17,10 @@ struct lb_handle {
   int64_t steps;
   int variant;  // LB_FUSED or LB_TWO_PASS
   int reduce_blocks;
+  bool use_tma;           // FP32 fused step with tensor-copy staging (interior tiles)
+  int tma_grid;           // persistent grid of that kernel
+  int tma_grid_auto;      // its default: resident capacity, at most the tile count
+  CUtensorMap tmap[2];    // 3-D maps (x, y, plane) of f[0] and f[1]
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
   lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
   lbm::VCoef<double> cd;

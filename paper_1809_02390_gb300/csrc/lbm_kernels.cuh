@@ -72,58 +72,18 @@ struct TileShape {
   static constexpr int ring = 2 * (kTileX + 2) + 2 * TY;
 };
 
-struct NoHook {
-  __device__ void operator()() const {}
-};
-
-// rs: shared array of (TY + 2) x (TX + 2) densities.  (x0, y0): tile origin.
-// before_sync() runs after all phase-1 loads are issued and before the block
-// barrier (the batched kernel stores its lattice coefficients there).
-template <typename V, typename store_t, int TY, typename Hook = NoHook>
-__device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
-                                          int ny, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
-                                          typename LaneType<V>::type (*rs)[kTileX + 2],
-                                          const Hook& before_sync = Hook()) {
+// Phase 2 of a tile: force stencil of each thread's two nodes from the shared
+// densities, collision (one packed FP32x2 evaluation for V = f2), store.
+template <typename V, typename store_t, int TY>
+__device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
+                                             store_t* __restrict__ fout, int nx, int ny, const VCoef<V>& c,
+                                             const LatCoef<V>& l, int x0, int y0,
+                                             const typename LaneType<V>::type (*rs)[kTileX + 2]) {
   using real = typename LaneType<V>::type;
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
   const int plane = nx * ny;
-  const bool small = nx <= kTileX || ny <= TY;  // tiles may wrap more than once
   const int gx = x0 + tx;
-  const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
-  const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
-
-  real f[kTileRows][9];
-#pragma unroll
-  for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * Shape::stride;
-    pull_row(fin, plane, nx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
-  }
-  // Ring: the row above, the row below, then the left and right columns.
-  const int t = threadIdx.x;
-  const bool ring = t < Shape::ring;
-  int wx = 0, wy = 0;
-  real g[9];
-  if (ring) {
-    if (t < kTileX + 2) {
-      wx = t, wy = 0;
-    } else if (t < 2 * (kTileX + 2)) {
-      wx = t - (kTileX + 2), wy = TY + 1;
-    } else if (t < 2 * (kTileX + 2) + TY) {
-      wx = 0, wy = t - 2 * (kTileX + 2) + 1;
-    } else {
-      wx = kTileX + 1, wy = t - 2 * (kTileX + 2) - TY + 1;
-    }
-    const int hx = small ? wrap(x0 - 1 + wx, nx) : wrap1(x0 - 1 + wx, nx);
-    const int hy = small ? wrap(y0 - 1 + wy, ny) : wrap1(y0 - 1 + wy, ny);
-    pull_row(fin, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
-  }
-#pragma unroll
-  for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
-  if (ring) rs[wy][wx] = sum9(g);
-  before_sync();
-  __syncthreads();
-
   real Sx[kTileRows], Sy[kTileRows];
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
@@ -157,6 +117,68 @@ __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store
       for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), out[k][i]);
     }
   }
+}
+
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// Phase 1 of a tile with plain loads: pulls the populations of the thread's two
+// nodes into f and writes the densities of tile + ring to rs (shared array of
+// (TY + 2) x (TX + 2) densities).  (x0, y0): tile origin.  Periodic wrap.
+template <typename real, typename store_t, int TY>
+__device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int nx, int ny, int x0, int y0,
+                                          real (&f)[kTileRows][9], real (*rs)[kTileX + 2]) {
+  using Shape = TileShape<TY>;
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int plane = nx * ny;
+  const bool small = nx <= kTileX || ny <= TY;  // tiles may wrap more than once
+  const int gx = x0 + tx;
+  const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
+  const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * Shape::stride;
+    pull_row(fin, plane, nx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
+  }
+  // Ring: the row above, the row below, then the left and right columns.
+  const int t = threadIdx.x;
+  const bool ring = t < Shape::ring;
+  int wx = 0, wy = 0;
+  real g[9];
+  if (ring) {
+    if (t < kTileX + 2) {
+      wx = t, wy = 0;
+    } else if (t < 2 * (kTileX + 2)) {
+      wx = t - (kTileX + 2), wy = TY + 1;
+    } else if (t < 2 * (kTileX + 2) + TY) {
+      wx = 0, wy = t - 2 * (kTileX + 2) + 1;
+    } else {
+      wx = kTileX + 1, wy = t - 2 * (kTileX + 2) - TY + 1;
+    }
+    const int hx = small ? wrap(x0 - 1 + wx, nx) : wrap1(x0 - 1 + wx, nx);
+    const int hy = small ? wrap(y0 - 1 + wy, ny) : wrap1(y0 - 1 + wy, ny);
+    pull_row(fin, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
+  }
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
+  if (ring) rs[wy][wx] = sum9(g);
+}
+
+// One fused step of a tile: load_tile, block barrier, collide_tile.
+// before_sync() runs after all phase-1 loads are issued and before the block
+// barrier (the batched kernel stores its lattice coefficients there).
+template <typename V, typename store_t, int TY, typename Hook = NoHook>
+__device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
+                                          int ny, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
+                                          typename LaneType<V>::type (*rs)[kTileX + 2],
+                                          const Hook& before_sync = Hook()) {
+  using real = typename LaneType<V>::type;
+  real f[kTileRows][9];
+  load_tile<real, store_t, TY>(fin, nx, ny, x0, y0, f, rs);
+  before_sync();
+  __syncthreads();
+  collide_tile<V, store_t, TY>(f, fout, nx, ny, c, l, x0, y0, rs);
 }
 
 template <typename V, typename store_t>

@@ -161,3 +161,24 @@ def test_full_size_mass_conservation():
     r = lat.reduce()
     assert r["mass"] == pytest.approx(m0, rel=2e-6)
     assert rho0.sum() == pytest.approx(m0, rel=1e-6)
+
+
+def test_fp32_tma_path(orc):
+    """The FP32 fused step with tensor-copy staging (interior tiles) and the plain
+    path (tiles whose windows wrap) on one lattice, against the oracle, with many
+    tiles per block and with one; no bounded wait gave up."""
+    from paper_1809_02390_gb300 import capi
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    rho0 = inputs.droplet(160, 96, 30, 5, p.rho_g, p.rho_l, center=(70.3, 50.6))
+    lat = lattice(rho0, "fp32", Tr=0.85, K_int=1.0)
+    assert capi.lb_uses_tma(lat.h)
+    capi.lb_set_step_blocks(lat.h, 4)  # 30 tiles: each block steps 7 or 8, interior and wrapping mixed
+    lat.step(150)
+    capi.lb_set_step_blocks(lat.h, 0)
+    lat.step(150)
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), 300))[0]
+    rho = lat.moments(velocity=False).double().cpu().numpy()
+    assert rel_inf(rho, ref) <= 2e-5
+    capi.lb_status(lat.h)
+    assert not capi.lb_uses_tma(lattice(rho0[:, :150], "fp32", Tr=0.85, K_int=1.0).h)  # nx % 4 != 0
