@@ -263,7 +263,7 @@ def measure_batch(torch, single_mlups: float, steps: int) -> dict:
     b.close()
 
     return {"lattices": len(rhos), "nodes": nodes, "steps": steps, "ms": round(ms, 2), "MLUPS": round(mlups, 1),
-            "ratio_vs_single_lattice": round(mlups / single_mlups, 4), "tuned": cfg,
+            "ratio_vs_single_lattice": round(mlups / single_mlups, 4) if single_mlups else None, "tuned": cfg,
             "launch": "one multi-lattice kernel per step (blocks_per_sm 0: one block per tile, else persistent), "
                       "graph replay of 64 steps",
             "unstable_lattices": unstable,
@@ -351,6 +351,10 @@ def run_ours(args):
 
     lbuild.build()
     n = args.size
+    if args.only_adjoint or args.only_batch:  # profiling runs of one measurement
+        part = measure_adjoint(n, torch) if args.only_adjoint else measure_batch(torch, None, args.batch_steps)
+        print(json.dumps(part), flush=True)
+        return
     rho0, d = workload_rho(n, seed=rank)
     nodes = n * n
     pk = peaks()
@@ -451,6 +455,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=N_SIDE, help="lattice side (profiling runs use smaller cases)")
     ap.add_argument("--only-main", action="store_true", help="time the FP32 fused step only (profiling)")
+    ap.add_argument("--only-adjoint", action="store_true", help="time the FP32 adjoint at --size only (profiling)")
+    ap.add_argument("--only-batch", action="store_true", help="time the 256-lattice batch only (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batch and calibration runs")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the 256-lattice batch run")
     args = ap.parse_args()

@@ -177,8 +177,10 @@ __global__ void k_adj_theta(const double* __restrict__ partial, int nblocks, dou
 // s^n (with its density ring), mu' (pulled backwards) and Sb' (with a two-node
 // ring, staged in shared memory), forms lam at each node, and writes the local
 // VJP (mu, Sb) of step n: 124 B per node in FP32 against 196 B for
-// k_adj_local + k_adj_transpose.
-// 3 resident blocks per SM for FP32 (<= 85 registers), 2 for FP64.
+// k_adj_local + k_adj_transpose.  The VJP runs node by node in scalar FP32: as a
+// packed pair (two nodes per FFMA2) its live set needs 128 registers (2 blocks/SM)
+// or spills 350 bytes per thread at 80, and either way the step was 20% slower.
+// Resident blocks per SM: 3 for FP32 (<= 85 registers), 1 for FP64.
 template <typename real>
 constexpr int adj_min_blocks() {
   return sizeof(real) == 8 ? 1 : 3;
@@ -187,8 +189,8 @@ constexpr int adj_min_blocks() {
 template <typename real, typename store_t>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     k_adj_fused(const store_t* __restrict__ s, const real* __restrict__ mu_in, const real* __restrict__ sb_in,
-                real* __restrict__ mu, real* __restrict__ sbar, double* __restrict__ partial, int accumulate,
-                int nx, int ny, VCoef<real> c) {
+                real* __restrict__ mu, real* __restrict__ sbar, double* __restrict__ partial, int accumulate, int nx,
+                int ny, VCoef<real> c) {
   __shared__ real rs[kTileY + 2][kTileX + 2];   // density of s^n on tile + ring
   __shared__ real rb[kTileY + 2][kTileX + 2];   // rhob' on tile + ring
   __shared__ real sbx[kTileY + 4][kTileX + 4];  // Sb' on tile + two-node ring
@@ -197,18 +199,22 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   const int plane = nx * ny;
+  // Every coordinate below lies in [-2, n + 33); one conditional wrap suffices
+  // unless the lattice is smaller than a tile plus its two-node ring.
+  const bool small = nx < kTileX + 4 || ny < kTileY + 4;
+  auto wr = [&](int v, int n) { return small ? wrap(v, n) : wrap1(v, n); };
   const int gx = x0 + tx;
-  const int xc = wrap(gx, nx);
+  const int xc = wr(gx, nx);
   const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
   real f[kTileRows][9];
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
     const int gy = y0 + ty + k * kRowStride;
-    pull_row(s, plane, nx, ny, wrap(gy, ny), xm, xc, xp, f[k]);
+    pull_row(s, plane, nx, ny, wr(gy, ny), xm, xc, xp, f[k]);
   }
   for (int t = threadIdx.x; t < (kTileY + 4) * (kTileX + 4); t += kAdjThreads) {
     const int wy = t / (kTileX + 4), wx = t - wy * (kTileX + 4);
-    const int o = wrap(y0 - 2 + wy, ny) * nx + wrap(x0 - 2 + wx, nx);
+    const int o = wr(y0 - 2 + wy, ny) * nx + wr(x0 - 2 + wx, nx);
     sbx[wy][wx] = sb_in[o];
     sby[wy][wx] = sb_in[plane + o];
   }
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     } else {
       wx = kTileX + 1, wy = t - 2 * (kTileX + 2) - kTileY + 1;
     }
-    const int hx = wrap(x0 - 1 + wx, nx), hy = wrap(y0 - 1 + wy, ny);
+    const int hx = wr(x0 - 1 + wx, nx), hy = wr(y0 - 1 + wy, ny);
     real g[9];
     pull_row(s, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
     rs[wy][wx] = sum9(g);

@@ -7,264 +7,238 @@
 // ob of o, collide_vjp returns the cotangents of d, of S and of theta.  The
 // forward values are recomputed here (in the same order as collide) and then
 // every assignment is transposed in reverse order.
+//
+// Written once for a value type V (double, float, or f2 = two FP32 nodes per
+// packed FFMA2 / FADD2 / FMUL2 instruction, as in collide); every constant comes
+// from the VCoef<V> block.
 #pragma once
 
 #include "lbm_device.cuh"
 
 namespace lbm {
 
-template <typename real>
+template <typename V>
 struct AdjOut {
-  real d[9];         // cotangent of the pulled populations of the node
-  real Sx, Sy;       // cotangent of the force stencil sum
-  real RT, G2, lam;  // cotangents of the parameters
+  V d[9];         // cotangent of the pulled populations of the node
+  V Sx, Sy;       // cotangent of the force stencil sum
+  V RT, G2, lam;  // cotangents of the parameters
 };
 
-template <typename real>
-__device__ __forceinline__ void collide_vjp(const VCoef<real>& c, const real (&d)[9], real Sx, real Sy,
-                                            const real (&ob)[9], AdjOut<real>& r) {
-  // ---------------- forward recomputation (same formulas as collide) ----------------
-  const real a13 = d[1] + d[3], a24 = d[2] + d[4], a57 = d[5] + d[7], a68 = d[6] + d[8];
-  const real s13 = d[1] - d[3], s24 = d[2] - d[4], s57 = d[5] - d[7], s68 = d[6] - d[8];
-  const real axis = a13 + a24, diag = a57 + a68;
-  const real rho = d[0] + axis + diag + c.rho_ref;
-  const real m1 = real(-4) * d[0] - axis + real(2) * diag - real(2) * c.rho_ref;
-  const real m2 = real(4) * d[0] - real(2) * axis + diag + c.rho_ref;
-  const real jx = s13 + s57 - s68, jy = s24 + s57 + s68;
-  const real m4 = real(-2) * s13 + s57 - s68, m6 = real(-2) * s24 + s57 + s68;
-  const real m7 = a13 - a24, m8 = a57 - a68;
-  const real G2 = c.G2, lam = c.lam, RT = c.RT, a = c.a, bq = c.bq;
-  const real G2rho = G2 * rho;
-  const real Fx = G2rho * Sx, Fy = G2rho * Sy;
-  const real ir = real(1) / rho;
-  const real hx = jx + real(0.5) * Fx, hy = jy + real(0.5) * Fy;
-  const real ux = hx * ir, uy = hy * ir;
+template <typename V>
+__device__ __forceinline__ void collide_vjp(const VCoef<V>& c, const V (&d)[9], V Sx, V Sy, const V (&ob)[9],
+                                            AdjOut<V>& r) {
+  // ---------------- forward recomputation (the formulas of collide) ----------------
+  const V a13 = d[1] + d[3], a24 = d[2] + d[4], a57 = d[5] + d[7], a68 = d[6] + d[8];
+  const V s13 = d[1] - d[3], s24 = d[2] - d[4], s57 = d[5] - d[7], s68 = d[6] - d[8];
+  const V axis = a13 + a24, diag = a57 + a68;
+  const V rho = d[0] + (axis + diag) + c.rho_ref;
+  const V m1 = fmav(c.m4, d[0], fmav(c.two, diag, c.m2rr) - axis);
+  const V m2 = fmav(c.four, d[0], fmav(c.m2, axis, diag + c.rho_ref));
+  const V dm = s57 - s68, dp = s57 + s68;
+  const V jx = s13 + dm, jy = s24 + dp;
+  const V m4 = fmav(c.m2, s13, dm), m6 = fmav(c.m2, s24, dp);
+  const V m7 = a13 - a24, m8 = a57 - a68;
+  const V G2rho = c.G2 * rho;
+  const V Fx = G2rho * Sx, Fy = G2rho * Sy;
+  const V ir = rcp(rho);
+  const V hx = fmav(c.half, Fx, jx), hy = fmav(c.half, Fy, jy);
+  const V ux = hx * ir, uy = hy * ir;
   // EOS and its parameter dependence.
-  real pe, dpe;
-  real io = 0, q = 0, t = 0, z = 0, dz = 0, zt = 0, dzt = 0;
+  V pe, dpe, io, q, z, dz, zt, dzt;
   if (c.eos == LB_EOS_VDW) {
-    io = real(1) / (real(1) - bq * rho);
-    q = lam * RT * io;
-    pe = rho * (q - lam * a * rho);
-    dpe = q * io - real(2) * lam * a * rho;
+    io = rcp(fmav(c.neg_bq, rho, c.one));
+    q = c.lam_RT * io;
+    pe = rho * fmav(c.neg_lam_a, rho, q);
+    dpe = fmav(q, io, c.neg_2lam_a * rho);
+    z = dz = zt = dzt = q;  // unused
   } else {
-    t = bq * rho;
-    const real om = real(1) - t;
-    io = real(1) / om;
-    const real io3 = io * io * io, io4 = io3 * io;
-    z = (real(1) + t + t * t - t * t * t) * io3;
-    dz = (real(1) + real(4) * t + real(4) * t * t - real(4) * t * t * t + t * t * t * t) * io4;
-    zt = (real(4) + real(4) * t - real(2) * t * t) * io4;  // dz/dt
-    dzt = (real(8) + real(20) * t - real(4) * t * t) * io4 * io;  // d(dz)/dt
-    pe = rho * (lam * RT * z - lam * a * rho);
-    dpe = lam * RT * dz - real(2) * lam * a * rho;
+    const V t = c.bq * rho;
+    io = rcp(c.one - t);
+    const V io3 = io * io * io, io4 = io3 * io;
+    const V t2 = t * t;
+    z = fmav(t2, c.one - t, c.one + t) * io3;
+    dz = fmav(t2, fmav(t, t - c.four, c.four), fmav(c.four, t, c.one)) * io4;
+    zt = fmav(t, fmav(c.m2, t, c.four), c.four) * io4;              // dz/dt
+    dzt = fmav(t, fmav(c.m4, t, c.twenty), c.eight) * (io4 * io);  // d(dz)/dt
+    pe = rho * fmav(c.neg_lam_a, rho, c.lam_RT * z);
+    dpe = fmav(c.lam_RT, dz, c.neg_2lam_a * rho);
+    q = pe;  // unused
   }
-  const real eta = real(3) * pe + real(1.5) * G2 * rho * rho - rho;
-  const real g = G2rho + dpe;
-  const real x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2;
-  const real r3u2 = real(3) * rho * u2;
-  const real meq1 = real(2) * (eta - rho) + r3u2;
-  const real meq2 = real(9) * rho * x2 * y2 + c.beta2 * eta + rho - r3u2;
-  const real meq4 = rho * ux * (real(3) * y2 - real(1)), meq6 = rho * uy * (real(3) * x2 - real(1));
-  const real meq7 = rho * (x2 - y2), meq8 = rho * xy;
-  const real Fu = Fx * ux + Fy * uy, Fc = Fx * uy + Fy * ux;
-  const real Fm1 = real(6) * Fu;
-  const real Fm2 = real(18) * xy * Fc - real(6) * Fu;
-  const real Fm4 = real(3) * (Fx * y2 + real(2) * Fy * xy) - Fx;
-  const real Fm6 = real(3) * (Fy * x2 + real(2) * Fx * xy) - Fy;
-  const real Fm7 = real(2) * (Fx * ux - Fy * uy), Fm8 = Fc;
-  const real G1 = m1 - meq1 + real(0.5) * Fm1, Gm2 = m2 - meq2 + real(0.5) * Fm2;
-  const real G4 = m4 - meq4 + real(0.5) * Fm4, G6 = m6 - meq6 + real(0.5) * Fm6;
-  const real G7 = m7 - meq7 + real(0.5) * Fm7, G8 = m8 - meq8 + real(0.5) * Fm8;
-  const real uG = ux * G4 + uy * G6, vG = ux * G4 - uy * G6, wG = uy * G4 + ux * G6;
-  const real A1 = c.om_e * (G1 + c.hk_seps * Gm2 + c.hh_sq * uG);
-  const real A7 = c.om_p * (G7 + c.b_sq * vG), A8 = c.om_p * (G8 + c.hb_sq * wG);
-  const real ax = x2 * ux * Sx, ay = y2 * uy * Sy;
-  const real P1 = xy * (uy * Sx + ux * Sy), P7 = xy * (uy * Sx - ux * Sy);
-  const real K1 = g * c.X1 + c.negT1b, K7 = c.T7b + g * c.X7, K8 = c.T8 + g * c.X8;
-  const real B8 = (real(2) * x2 + y2) * uy * Sx + (real(2) * y2 + x2) * ux * Sy;
-  const real x2my2 = x2 - y2;
-  const real sxx = Sx * Sx, syy = Sy * Sy, ss = sxx + syy;
-  // Parameter-free parts of the S Q_m coefficients (they are proportional to G2).
-  const real q1 = c.Q1G2 / G2, q2 = c.Q2G2 / G2, q78 = c.Q78G2 / G2;
+  const V eta = fmav(c.three, pe, rho * fmav(c.g15, rho, c.mone));
+  const V g = G2rho + dpe;
+  const V x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2;
+  const V r3u2 = c.three * rho * u2;
+  const V meq1 = fmav(c.two, eta - rho, r3u2);
+  const V meq2 = fmav(c.nine * rho * x2, y2, fmav(c.beta2, eta, rho) - r3u2);
+  const V tx3 = fmav(c.three, y2, c.mone), ty3 = fmav(c.three, x2, c.mone);  // 3 uy^2 - 1, 3 ux^2 - 1
+  const V meq4 = rho * ux * tx3, meq6 = rho * uy * ty3;
+  const V x2my2 = x2 - y2;
+  const V meq7 = rho * x2my2, meq8 = rho * xy;
+  const V Fu = fmav(Fx, ux, Fy * uy), Fc = fmav(Fx, uy, Fy * ux);
+  const V Fm1 = c.six * Fu;
+  const V Fm2 = fmav(c.eighteen * xy, Fc, c.m6 * Fu);
+  const V Fm4 = fmav(c.three, fmav(Fx, y2, (c.two * Fy) * xy), c.mone * Fx);
+  const V Fm6 = fmav(c.three, fmav(Fy, x2, (c.two * Fx) * xy), c.mone * Fy);
+  const V Fm7 = c.two * (Fx * ux - Fy * uy), Fm8 = Fc;
+  const V G1 = fmav(c.half, Fm1, m1 - meq1), Gm2 = fmav(c.half, Fm2, m2 - meq2);
+  const V G4 = fmav(c.half, Fm4, m4 - meq4), G6 = fmav(c.half, Fm6, m6 - meq6);
+  const V G7 = fmav(c.half, Fm7, m7 - meq7), G8 = fmav(c.half, Fm8, m8 - meq8);
+  const V uG = fmav(ux, G4, uy * G6), vG = ux * G4 - uy * G6, wG = fmav(uy, G4, ux * G6);
+  const V A1 = c.om_e * fmav(c.hh_sq, uG, fmav(c.hk_seps, Gm2, G1));
+  const V A7 = c.om_p * fmav(c.b_sq, vG, G7), A8 = c.om_p * fmav(c.hb_sq, wG, G8);
+  const V ax = x2 * ux * Sx, ay = y2 * uy * Sy;
+  const V uSp = fmav(uy, Sx, ux * Sy), uSm = uy * Sx - ux * Sy;  // uy Sx +- ux Sy
+  const V P1 = xy * uSp, P7 = xy * uSm;
+  const V K1 = fmav(g, c.X1, c.negT1b), K7 = fmav(g, c.X7, c.T7b), K8 = fmav(g, c.X8, c.T8);
+  const V cx8 = fmav(c.two, x2, y2), cy8 = fmav(c.two, y2, x2);  // 2 x2 + y2, 2 y2 + x2
+  const V B8 = fmav(cx8 * uy, Sx, cy8 * ux * Sy);
+  const V sxx = Sx * Sx, syy = Sy * Sy, ss = sxx + syy;
 
   // ---------------- reverse pass ----------------
   // o = M^T n  =>  nb = M ob.
-  const real b13 = ob[1] + ob[3], b24 = ob[2] + ob[4], b57 = ob[5] + ob[7], b68 = ob[6] + ob[8];
-  const real c13 = ob[1] - ob[3], c24 = ob[2] - ob[4], c57 = ob[5] - ob[7], c68 = ob[6] - ob[8];
-  const real baxis = b13 + b24, bdiag = b57 + b68;
-  const real nb0 = ob[0] + baxis + bdiag;
-  const real nb1 = real(-4) * ob[0] - baxis + real(2) * bdiag;
-  const real nb2 = real(4) * ob[0] - real(2) * baxis + bdiag;
-  const real nb3 = c13 + c57 - c68, nb5 = c24 + c57 + c68;
-  const real nb4 = real(-2) * c13 + c57 - c68, nb6 = real(-2) * c24 + c57 + c68;
-  const real nb7 = b13 - b24, nb8 = b57 - b68;
+  const V b13 = ob[1] + ob[3], b24 = ob[2] + ob[4], b57 = ob[5] + ob[7], b68 = ob[6] + ob[8];
+  const V c13 = ob[1] - ob[3], c24 = ob[2] - ob[4], c57 = ob[5] - ob[7], c68 = ob[6] - ob[8];
+  const V baxis = b13 + b24, bdiag = b57 + b68;
+  const V cdm = c57 - c68, cdp = c57 + c68;
   // n0 = rho_dev/9, n1 = (mb1 + 2 rr)/36, n2 = (mb2 - rr)/36, n3 = (jx + Fx)/6, ...
-  real rho_b = nb0 * real(1.0 / 9.0);  // cotangent of rho (rho_dev and rho differ by a constant)
-  const real mb1b = nb1 * real(1.0 / 36.0), mb2b = nb2 * real(1.0 / 36.0);
-  const real mb4b = nb4 * real(1.0 / 12.0), mb6b = nb6 * real(1.0 / 12.0);
-  const real mb7b = nb7 * real(0.25), mb8b = nb8 * real(0.25);
-  real jxb = nb3 * real(1.0 / 6.0), jyb = nb5 * real(1.0 / 6.0);
-  real Fxb = jxb, Fyb = jyb;
-  real G2b = 0, lamb = 0, RTb = 0, Sxb = 0, Syb = 0;
+  V rho_b = (ob[0] + (baxis + bdiag)) * c.ninth;  // rho_dev and rho differ by a constant
+  const V mb1b = fmav(c.m4, ob[0], c.two * bdiag - baxis) * c.i36;
+  const V mb2b = fmav(c.four, ob[0], fmav(c.m2, baxis, bdiag)) * c.i36;
+  const V mb4b = fmav(c.m2, c13, cdm) * c.i12, mb6b = fmav(c.m2, c24, cdp) * c.i12;
+  const V mb7b = (b13 - b24) * c.quarter, mb8b = (b57 - b68) * c.quarter;
+  V jxb = (c13 + cdm) * c.sixth, jyb = (c24 + cdp) * c.sixth;
+  V Fxb = jxb, Fyb = jyb;
   // mbar_k = (S Q_m)_k + 2 A_k + m_eq,k - D_k - corr_k, D_k = m_k - m_eq,k.
-  real ssb = c.Q1G2 * mb1b + c.Q2G2 * mb2b;
-  G2b += q1 * ss * mb1b + q2 * ss * mb2b + q78 * ((sxx - syy) * mb7b + Sx * Sy * mb8b);
-  real sxxb = ssb + c.Q78G2 * mb7b, syyb = ssb - c.Q78G2 * mb7b;
-  Sxb += c.Q78G2 * Sy * mb8b;
-  Syb += c.Q78G2 * Sx * mb8b;
-  real A1b = real(2) * mb1b, A2b = real(2) * mb2b, A4b = real(2) * mb4b, A6b = real(2) * mb6b;
-  real A7b = real(2) * mb7b, A8b = real(2) * mb8b;
-  real meq1b = mb1b, meq2b = mb2b, meq4b = mb4b, meq6b = mb6b, meq7b = mb7b, meq8b = mb8b;
-  real D1b = -mb1b, D2b = -mb2b, D4b = -mb4b, D6b = -mb6b, D7b = -mb7b, D8b = -mb8b;
-  const real corr1b = -mb1b, corr7b = -mb7b, corr8b = -mb8b;
-  Sxb += real(2) * Sx * sxxb;
-  Syb += real(2) * Sy * syyb;
-  // corr8 = R81 xy A1 + R88 u2 A8 + cr8 ; corr7 ; corr1.
-  real xyb = c.R81 * A1 * corr8b + c.R18 * A8 * corr1b;
-  real u2b = c.R88 * A8 * corr8b + c.R77 * A7 * corr7b + c.R11 * A1 * corr1b;
-  real x2my2b = c.R71 * A1 * corr7b + c.R17 * A7 * corr1b;
-  A1b += c.R81 * xy * corr8b + c.R71 * x2my2 * corr7b + c.R11 * u2 * corr1b;
-  A8b += c.R88 * u2 * corr8b + c.R18 * xy * corr1b;
-  A7b += c.R77 * u2 * corr7b + c.R17 * x2my2 * corr1b;
-  const real cr8b = corr8b, cr7b = corr7b, cr1b = corr1b;
-  real x2b = x2my2b, y2b = -x2my2b;
-  real uxb = 0, uyb = 0, gb = 0;
-  // cr8 = K8 B8.
-  gb += c.X8 * B8 * cr8b;
-  const real B8b = K8 * cr8b;
-  x2b += (real(2) * uy * Sx + ux * Sy) * B8b;
-  y2b += (uy * Sx + real(2) * ux * Sy) * B8b;
-  uyb += (real(2) * x2 + y2) * Sx * B8b;
-  uxb += (real(2) * y2 + x2) * Sy * B8b;
-  Sxb += (real(2) * x2 + y2) * uy * B8b;
-  Syb += (real(2) * y2 + x2) * ux * B8b;
-  // cr7 = T7 (ax - ay) + K7 P7 ; cr1 = T1a (ax + ay) + K1 P1.
-  real axb = c.T7 * cr7b + c.T1a * cr1b, ayb = -c.T7 * cr7b + c.T1a * cr1b;
-  gb += c.X7 * P7 * cr7b + c.X1 * P1 * cr1b;
-  const real P7b = K7 * cr7b, P1b = K1 * cr1b;
-  xyb += (uy * Sx - ux * Sy) * P7b + (uy * Sx + ux * Sy) * P1b;
-  const real q7 = xy * P7b, q1b = xy * P1b;
-  uyb += Sx * (q7 + q1b);
-  uxb += Sy * (q1b - q7);
-  Sxb += uy * (q7 + q1b);
-  Syb += ux * (q1b - q7);
-  // ax = x2 ux Sx ; ay = y2 uy Sy.
-  x2b += ux * Sx * axb;
-  uxb += x2 * Sx * axb;
-  Sxb += x2 * ux * axb;
-  y2b += uy * Sy * ayb;
-  uyb += y2 * Sy * ayb;
-  Syb += y2 * uy * ayb;
-  // A8 = om_p (G8 + hb wG) ; A7 = om_p (G7 + b vG) ; A6, A4, A2 ; A1 = om_e (G1 + hk G2 + hh uG).
-  real G8b = c.om_p * A8b;
-  const real wGb = c.om_p * c.hb_sq * A8b;
-  real G7b = c.om_p * A7b;
-  const real vGb = c.om_p * c.b_sq * A7b;
-  real G6b = c.om_q * A6b, G4b = c.om_q * A4b, Gm2b = c.om_eps * A2b;
-  const real t1 = c.om_e * A1b;
-  real G1b = t1;
-  Gm2b += c.hk_seps * t1;
-  const real uGb = c.hh_sq * t1;
-  // uG, vG, wG.
-  uxb += G4 * (uGb + vGb) + G6 * wGb;
-  uyb += G6 * (uGb - vGb) + G4 * wGb;
-  G4b += ux * (uGb + vGb) + uy * wGb;
-  G6b += uy * (uGb - vGb) + ux * wGb;
-  // G_k = D_k + F_m,k / 2 ; D_k = m_k - m_eq,k.
-  D1b += G1b;
-  D2b += Gm2b;
-  D4b += G4b;
-  D6b += G6b;
-  D7b += G7b;
-  D8b += G8b;
-  const real Fm1b = real(0.5) * G1b, Fm2b = real(0.5) * Gm2b, Fm4b = real(0.5) * G4b;
-  const real Fm6b = real(0.5) * G6b, Fm7b = real(0.5) * G7b, Fm8b = real(0.5) * G8b;
-  const real m1b = D1b, m2b = D2b, m4b = D4b, m6b = D6b, m7b = D7b, m8b = D8b;
-  meq1b -= D1b;
-  meq2b -= D2b;
-  meq4b -= D4b;
-  meq6b -= D6b;
-  meq7b -= D7b;
-  meq8b -= D8b;
+  const V ssb = fmav(c.Q1G2, mb1b, c.Q2G2 * mb2b);
+  V G2b = fmav(ss, fmav(c.Q1, mb1b, c.Q2 * mb2b), c.Q78 * fmav(sxx - syy, mb7b, (Sx * Sy) * mb8b));
+  const V e8 = c.Q78G2 * mb8b;
+  V Sxb = fmav(c.two * Sx, fmav(c.Q78G2, mb7b, ssb), Sy * e8);
+  V Syb = fmav(c.two * Sy, ssb - c.Q78G2 * mb7b, Sx * e8);
+  // Cotangents of the corrections: corr_kb = -mb_kb.
+  const V k1 = c.mone * mb1b, k7 = c.mone * mb7b, k8 = c.mone * mb8b;
+  // corr8 = R81 xy A1 + R88 u2 A8 + cr8 ; corr7 = R71 x2my2 A1 + R77 u2 A7 + cr7 ;
+  // corr1 = R11 u2 A1 + R17 x2my2 A7 + R18 xy A8 + cr1.
+  V xyb = fmav(c.R81 * A1, k8, c.R18 * A8 * k1);
+  V u2b = fmav(c.R88 * A8, k8, fmav(c.R77 * A7, k7, c.R11 * A1 * k1));
+  const V x2my2b = fmav(c.R71 * A1, k7, c.R17 * A7 * k1);
+  const V A1b = fmav(c.two, mb1b, fmav(c.R81 * xy, k8, fmav(c.R71 * x2my2, k7, c.R11 * u2 * k1)));
+  const V A8b = fmav(c.two, mb8b, fmav(c.R88 * u2, k8, c.R18 * xy * k1));
+  const V A7b = fmav(c.two, mb7b, fmav(c.R77 * u2, k7, c.R17 * x2my2 * k1));
+  // cr8 = K8 B8 ; cr7 = T7 (ax - ay) + K7 P7 ; cr1 = T1a (ax + ay) + K1 P1.
+  V gb = fmav(c.X8 * B8, k8, fmav(c.X7 * P7, k7, c.X1 * P1 * k1));
+  const V B8b = K8 * k8;
+  const V P7b = K7 * k7, P1b = K1 * k1;
+  const V axb = fmav(c.T7, k7, c.T1a * k1), ayb = fmav(c.T1a, k1, c.mone * c.T7 * k7);
+  const V q7 = xy * P7b, q1 = xy * P1b;
+  const V qp = q7 + q1, qm = q1 - q7;
+  xyb = fmav(uSm, P7b, fmav(uSp, P1b, xyb));
+  V x2b = fmav(fmav(c.two * uy, Sx, ux * Sy), B8b, fmav(ux * Sx, axb, x2my2b));
+  V y2b = fmav(fmav(uy, Sx, (c.two * ux) * Sy), B8b, fmav(uy * Sy, ayb, c.mone * x2my2b));
+  V uxb = fmav(cy8 * Sy, B8b, fmav(Sy, qm, x2 * Sx * axb));
+  V uyb = fmav(cx8 * Sx, B8b, fmav(Sx, qp, y2 * Sy * ayb));
+  Sxb = fmav(cx8 * uy, B8b, fmav(uy, qp, fmav(x2 * ux, axb, Sxb)));
+  Syb = fmav(cy8 * ux, B8b, fmav(ux, qm, fmav(y2 * uy, ayb, Syb)));
+  // A8 = om_p (G8 + hb wG) ; A7 = om_p (G7 + b vG) ; A6 = om_q G6 ; A4 = om_q G4 ;
+  // A2 = om_eps G2 ; A1 = om_e (G1 + hk G2 + hh uG) ; mb_k gets 2 A_k.
+  const V G8b = c.om_p * A8b, wGb = c.om_p * c.hb_sq * A8b;
+  const V G7b = c.om_p * A7b, vGb = c.om_p * c.b_sq * A7b;
+  const V t1 = c.om_e * A1b;
+  const V G1b = t1;
+  const V Gm2b = fmav(c.hk_seps, t1, c.om_eps * (c.two * mb2b));
+  const V uGb = c.hh_sq * t1;
+  const V uvp = uGb + vGb, uvm = uGb - vGb;
+  uxb = fmav(G4, uvp, fmav(G6, wGb, uxb));
+  uyb = fmav(G6, uvm, fmav(G4, wGb, uyb));
+  const V G4b = fmav(ux, uvp, fmav(uy, wGb, c.om_q * (c.two * mb4b)));
+  const V G6b = fmav(uy, uvm, fmav(ux, wGb, c.om_q * (c.two * mb6b)));
+  // G_k = D_k + F_m,k / 2 ; D_k = m_k - m_eq,k, and mb_k holds -D_k.
+  const V m1b = G1b - mb1b, m2b = Gm2b - mb2b, m4b = G4b - mb4b;
+  const V m6b = G6b - mb6b, m7b = G7b - mb7b, m8b = G8b - mb8b;
+  const V meq1b = mb1b - m1b, meq2b = mb2b - m2b, meq4b = mb4b - m4b;
+  const V meq6b = mb6b - m6b, meq7b = mb7b - m7b, meq8b = mb8b - m8b;
+  const V Fm1b = c.half * G1b, Fm2b = c.half * Gm2b, Fm4b = c.half * G4b;
+  const V Fm6b = c.half * G6b, Fm7b = c.half * G7b, Fm8b = c.half * G8b;
   // Forcing.
-  real Fcb = Fm8b + real(18) * xy * Fm2b;
-  real Fub = real(6) * Fm1b - real(6) * Fm2b;
-  xyb += real(18) * Fc * Fm2b + real(6) * Fy * Fm4b + real(6) * Fx * Fm6b;
-  Fxb += real(2) * ux * Fm7b + (real(3) * y2 - real(1)) * Fm4b + real(6) * xy * Fm6b;
-  Fyb += real(-2) * uy * Fm7b + (real(3) * x2 - real(1)) * Fm6b + real(6) * xy * Fm4b;
-  uxb += real(2) * Fx * Fm7b;
-  uyb += real(-2) * Fy * Fm7b;
-  y2b += real(3) * Fx * Fm4b;
-  x2b += real(3) * Fy * Fm6b;
+  const V Fcb = fmav(c.eighteen * xy, Fm2b, Fm8b);
+  const V Fub = c.six * (Fm1b - Fm2b);
+  xyb = fmav(c.eighteen * Fc, Fm2b, fmav(c.six * Fy, Fm4b, fmav(c.six * Fx, Fm6b, xyb)));
+  Fxb = fmav(c.two * ux, Fm7b, fmav(tx3, Fm4b, fmav(c.six * xy, Fm6b, Fxb)));
+  Fyb = fmav(c.m2 * uy, Fm7b, fmav(ty3, Fm6b, fmav(c.six * xy, Fm4b, Fyb)));
+  uxb = fmav(c.two * Fx, Fm7b, uxb);
+  uyb = fmav(c.m2 * Fy, Fm7b, uyb);
+  y2b = fmav(c.three * Fx, Fm4b, y2b);
+  x2b = fmav(c.three * Fy, Fm6b, x2b);
   // Fc = Fx uy + Fy ux ; Fu = Fx ux + Fy uy.
-  Fxb += uy * Fcb + ux * Fub;
-  Fyb += ux * Fcb + uy * Fub;
-  uxb += Fy * Fcb + Fx * Fub;
-  uyb += Fx * Fcb + Fy * Fub;
+  Fxb = fmav(uy, Fcb, fmav(ux, Fub, Fxb));
+  Fyb = fmav(ux, Fcb, fmav(uy, Fub, Fyb));
+  uxb = fmav(Fy, Fcb, fmav(Fx, Fub, uxb));
+  uyb = fmav(Fx, Fcb, fmav(Fy, Fub, uyb));
   // Equilibrium.
-  rho_b += xy * meq8b + x2my2 * meq7b + uy * (real(3) * x2 - real(1)) * meq6b +
-           ux * (real(3) * y2 - real(1)) * meq4b + (real(9) * x2 * y2 + real(1)) * meq2b - real(2) * meq1b;
-  xyb += rho * meq8b;
-  x2b += rho * meq7b + real(3) * rho * uy * meq6b + real(9) * rho * y2 * meq2b;
-  y2b += -rho * meq7b + real(3) * rho * ux * meq4b + real(9) * rho * x2 * meq2b;
-  uyb += rho * (real(3) * x2 - real(1)) * meq6b;
-  uxb += rho * (real(3) * y2 - real(1)) * meq4b;
-  real etab = c.beta2 * meq2b + real(2) * meq1b;
-  const real r3u2b = meq1b - meq2b;
-  rho_b += real(3) * u2 * r3u2b;
-  u2b += real(3) * rho * r3u2b;
-  x2b += u2b;
-  y2b += u2b;
-  uxb += uy * xyb + real(2) * ux * x2b;
-  uyb += ux * xyb + real(2) * uy * y2b;
+  rho_b = fmav(xy, meq8b, fmav(x2my2, meq7b, fmav(uy * ty3, meq6b, fmav(ux * tx3, meq4b,
+          fmav(fmav(c.nine * x2, y2, c.one), meq2b, fmav(c.m2, meq1b, rho_b))))));
+  xyb = fmav(rho, meq8b, xyb);
+  const V r3 = c.three * rho, r9 = c.nine * rho;
+  x2b = fmav(rho, meq7b, fmav(r3 * uy, meq6b, fmav(r9 * y2, meq2b, x2b)));
+  y2b = fmav(r3 * ux, meq4b, fmav(r9 * x2, meq2b, y2b - rho * meq7b));
+  uyb = fmav(rho * ty3, meq6b, uyb);
+  uxb = fmav(rho * tx3, meq4b, uxb);
+  const V etab = fmav(c.beta2, meq2b, c.two * meq1b);
+  const V r3u2b = meq1b - meq2b;
+  rho_b = fmav(c.three * u2, r3u2b, rho_b);
+  u2b = fmav(r3, r3u2b, u2b);
+  x2b = x2b + u2b;
+  y2b = y2b + u2b;
+  uxb = fmav(uy, xyb, fmav(c.two * ux, x2b, uxb));
+  uyb = fmav(ux, xyb, fmav(c.two * uy, y2b, uyb));
   // g = G2 rho + dpe ; eta = 3 pe + 1.5 G2 rho^2 - rho.
-  real G2rhob = gb;
-  const real dpeb = gb;
-  const real peb = real(3) * etab;
-  G2b += real(1.5) * rho * rho * etab;
-  rho_b += (real(3) * G2 * rho - real(1)) * etab;
+  V G2rhob = gb;
+  const V dpeb = gb, peb = c.three * etab;
+  G2b = fmav(c.h15 * rho * rho, etab, G2b);
+  rho_b = fmav(fmav(c.two * c.g15, rho, c.mone), etab, rho_b);  // (3 G2 rho - 1) etab
   // EOS.
+  V lamb, RTb;
   if (c.eos == LB_EOS_VDW) {
     // pe = rho (q - lam a rho) ; dpe = q io - 2 lam a rho ; q = lam RT io ; io = 1/(1 - b rho).
-    rho_b += (q - real(2) * lam * a * rho) * peb - real(2) * lam * a * dpeb;
-    const real qb = rho * peb + io * dpeb;
-    lamb += -a * rho * rho * peb - real(2) * a * rho * dpeb + RT * io * qb;
-    RTb += lam * io * qb;
-    const real iob = q * dpeb + lam * RT * qb;
-    rho_b += bq * io * io * iob;  // d io / d rho = b io^2
+    rho_b = fmav(fmav(c.neg_2lam_a, rho, q), peb, fmav(c.neg_2lam_a, dpeb, rho_b));
+    const V qb = fmav(rho, peb, io * dpeb);
+    lamb = fmav(c.RT * io, qb, (c.neg_a * rho) * fmav(rho, peb, c.two * dpeb));
+    RTb = c.lam * io * qb;
+    const V iob = fmav(q, dpeb, c.lam_RT * qb);
+    rho_b = fmav(c.bq * io * io, iob, rho_b);  // d io / d rho = b io^2
   } else {
     // pe = rho (lam RT z - lam a rho) ; dpe = lam RT dz - 2 lam a rho ; z(t), dz(t), t = bq rho.
-    rho_b += (lam * RT * z - real(2) * lam * a * rho) * peb - real(2) * lam * a * dpeb;
-    const real zb = lam * RT * rho * peb, dzb = lam * RT * dpeb;
-    lamb += (RT * z - a * rho) * rho * peb + (RT * dz - real(2) * a * rho) * dpeb;
-    RTb += lam * z * rho * peb + lam * dz * dpeb;
-    rho_b += bq * (zt * zb + dzt * dzb);
+    rho_b = fmav(fmav(c.lam_RT, z, c.neg_2lam_a * rho), peb, fmav(c.neg_2lam_a, dpeb, rho_b));
+    const V rpeb = rho * peb;
+    lamb = fmav(fmav(c.RT, z, c.neg_a * rho), rpeb, fmav(c.RT, dz, (c.two * c.neg_a) * rho) * dpeb);
+    RTb = c.lam * fmav(z, rpeb, dz * dpeb);
+    rho_b = fmav(c.bq * c.lam_RT, fmav(zt, rpeb, dzt * dpeb), rho_b);
   }
   // Fx = G2rho Sx ; ux = (jx + Fx/2)/rho.
-  Fxb += real(0.5) * ir * uxb;
-  Fyb += real(0.5) * ir * uyb;
-  jxb += ir * uxb;
-  jyb += ir * uyb;
-  rho_b += -(hx * uxb + hy * uyb) * ir * ir;
-  G2rhob += Sx * Fxb + Sy * Fyb;
-  Sxb += G2rho * Fxb;
-  Syb += G2rho * Fyb;
-  G2b += rho * G2rhob;
-  rho_b += G2 * G2rhob;
+  Fxb = fmav(c.half * ir, uxb, Fxb);
+  Fyb = fmav(c.half * ir, uyb, Fyb);
+  jxb = fmav(ir, uxb, jxb);
+  jyb = fmav(ir, uyb, jyb);
+  rho_b = fmav(c.mone * fmav(hx, uxb, hy * uyb), ir * ir, rho_b);
+  G2rhob = fmav(Sx, Fxb, fmav(Sy, Fyb, G2rhob));
+  Sxb = fmav(G2rho, Fxb, Sxb);
+  Syb = fmav(G2rho, Fyb, Syb);
+  G2b = fmav(rho, G2rhob, G2b);
+  rho_b = fmav(c.G2, G2rhob, rho_b);
   // Moments: (rho, m1, m2, jx, m4, jy, m6, m7, m8) = M d  =>  db = M^T (their cotangents).
-  const real n0 = rho_b, n1 = m1b, n2 = m2b, n3 = jxb, n4 = m4b, n5 = jyb, n6 = m6b, n7 = m7b, n8 = m8b;
-  const real base_a = n0 - n1 - real(2) * n2, base_d = n0 + real(2) * n1 + n2;
-  const real px = n3 - real(2) * n4, py = n5 - real(2) * n6, qx = n3 + n4, qy = n5 + n6;
-  r.d[0] = n0 - real(4) * n1 + real(4) * n2;
-  r.d[1] = base_a + px + n7;
-  r.d[2] = base_a + py - n7;
-  r.d[3] = base_a - px + n7;
-  r.d[4] = base_a - py - n7;
-  r.d[5] = base_d + qx + qy + n8;
-  r.d[6] = base_d - qx + qy - n8;
-  r.d[7] = base_d - qx - qy + n8;
-  r.d[8] = base_d + qx - qy - n8;
+  const V n0 = rho_b, n1 = m1b, n2 = m2b, n3 = jxb, n4 = m4b, n5 = jyb, n6 = m6b, n7 = m7b, n8 = m8b;
+  const V base_a = fmav(c.m2, n2, n0 - n1), base_d = fmav(c.two, n1, n0 + n2);
+  const V px = fmav(c.m2, n4, n3), py = fmav(c.m2, n6, n5);
+  const V qx = n3 + n4, qy = n5 + n6;
+  const V ba7 = base_a + n7, bm7 = base_a - n7, bd8 = base_d + n8, bm8 = base_d - n8;
+  r.d[0] = fmav(c.four, n2 - n1, n0);
+  r.d[1] = ba7 + px;
+  r.d[2] = bm7 + py;
+  r.d[3] = ba7 - px;
+  r.d[4] = bm7 - py;
+  r.d[5] = bd8 + (qx + qy);
+  r.d[6] = bm8 + (qy - qx);
+  r.d[7] = bd8 - (qx + qy);
+  r.d[8] = bm8 + (qx - qy);
   r.Sx = Sxb;
   r.Sy = Syb;
   r.RT = RTb;

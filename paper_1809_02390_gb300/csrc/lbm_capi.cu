@@ -79,6 +79,13 @@ VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d) {
   c.Q1G2 = bc<V>(0.5 * (se - k * (0.5 * se - 1.0) * seps) * d.G2);
   c.Q2G2 = bc<V>(-0.5 * seps * d.G2);
   c.Q78G2 = bc<V>(sp / 12.0 * d.G2);
+  c.Q1 = bc<V>(0.5 * (se - k * (0.5 * se - 1.0) * seps));
+  c.Q2 = bc<V>(-0.5 * seps);
+  c.Q78 = bc<V>(sp / 12.0);
+  c.neg_a = bc<V>(-a);
+  c.h15 = bc<V>(1.5);
+  c.eight = bc<V>(8.0);
+  c.twenty = bc<V>(20.0);
   c.one = bc<V>(1.0);
   c.mone = bc<V>(-1.0);
   c.two = bc<V>(2.0);

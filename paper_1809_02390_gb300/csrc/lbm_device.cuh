@@ -90,6 +90,8 @@ struct VCoef {
   // literals and products of parameters with literals
   V one, mone, two, three, four, six, m6, nine, eighteen, half, m2, m4, m2rr, g15, ninth, i36, sixth, i12,
       quarter;
+  // used by the adjoint only: -a, 1.5, 8, 20 and the S Q_m factors without G^2
+  V neg_a, h15, eight, twenty, Q1, Q2, Q78;
 };
 
 // The coefficients that depend on the lattice's temperature, pressure scale,
