@@ -204,12 +204,15 @@ int lb_adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, 
 
 /* ---------------------------------------------------------------------------
  * Batched solver: n independent periodic lattices (each with its own size and
- * lb_params: Tr, K_int, rho_ref, ...) advanced together by one persistent kernel
- * launch per time step over a flat list of tiles of all lattices; runs of 64
- * steps are captured into CUDA graphs and replayed.  FP32 storage only.
+ * lb_params: Tr, K_int, rho_ref, ...) advanced together by one kernel launch per
+ * time step over a flat list of tiles of all lattices; runs of 64 steps are
+ * captured into CUDA graphs and replayed.  FP32 storage only.
  * Memory (all the caller's): two population pools of lb_batch_pool_bytes (lattice
- * i at element offset lb_batch_offset(i), layout f[9][ny][nx] as above) and a
- * metadata buffer of lb_batch_meta_bytes (descriptors, coefficients).
+ * i at element offset lb_batch_offset(i), layout f[9][ny][sx] with the row stride
+ * sx = lb_batch_row_stride(i) = nx rounded up to a multiple of 4; columns nx..sx-1
+ * are padding, never read or written) and a metadata buffer of
+ * lb_batch_meta_bytes (descriptors, coefficients, tensor maps; the maps hold the
+ * pools' addresses, so the pools must not move while the batch lives).
  * rho0: the initial densities of all lattices concatenated ([y][x] each), host
  * (staged through pool_b, synchronous) or device.  A stream of NULL (the legacy
  * default stream) cannot be captured: lb_batch_run then launches step by step. */
@@ -220,17 +223,31 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
                   size_t meta_bytes, const double* rho0, int rho0_on_device, void* stream);
 /* Advances every lattice by nsteps. */
 int lb_batch_run(lb_batch* b, int64_t nsteps);
-/* Autotuner: times each launch shape (tile height 16 or 32, register budget, and
- * either one block per tile or a persistent grid of 1..max resident blocks per SM)
- * for trial_steps steps on the batch itself (advancing it) and keeps the fastest;
+/* Autotuner: times each launch shape (plain loads: tile height 16 or 32, register
+ * budget, and either one block per tile or a persistent grid of 1..max resident
+ * blocks per SM; tensor copies: persistent grid of 1..max blocks per SM) for
+ * trial_steps steps on the batch itself (advancing it) and keeps the fastest;
  * writes its time per step.  lb_batch_config reports blocks_per_sm = 0 for the
- * one-block-per-tile grid. */
+ * one-block-per-tile grid; lb_batch_uses_tma is 1 when the tensor-copy kernel is
+ * the chosen shape. */
 int lb_batch_tune(lb_batch* b, int trial_steps, double* best_ms_per_step);
 int lb_batch_config(const lb_batch* b, int* tile_y, int* blocks_per_sm, int* grid);
+int lb_batch_uses_tma(const lb_batch* b);
+/* Sets the launch form by hand: shape 0, 1, 2 = plain loads with 32 x 16 tiles at
+ * 64 registers, 32 x 16 at 80, 32 x 32 at 64 (blocks_per_sm 0 = one block per tile,
+ * else a persistent grid); shape 3, 4 = the persistent tensor-copy kernel at 80 and
+ * 128 registers (blocks_per_sm >= 1).  LB_EINVAL outside the ranges (blocks_per_sm
+ * at most the resident maximum), LB_ENOTSUP for 3 and 4 when a lattice has no
+ * tensor map. */
+int lb_batch_set_config(lb_batch* b, int shape, int blocks_per_sm);
+/* Synchronous: LB_ETIMEOUT if a bounded wait of the tensor-copy kernel gave up
+ * since the last call (the flag is cleared), else LB_OK. */
+int lb_batch_status(lb_batch* b);
 /* Device pointer of the pool holding the current state; element offset of lattice i. */
 void* lb_batch_state(lb_batch* b);
 int64_t lb_batch_steps_done(const lb_batch* b);
 int64_t lb_batch_offset(const lb_batch* b, int i);
+int lb_batch_row_stride(const lb_batch* b, int i);
 int lb_batch_derived(const lb_batch* b, int i, lb_derived* out);
 const char* lb_batch_last_error(const lb_batch* b);
 void lb_batch_free(lb_batch* b);

@@ -165,17 +165,27 @@ class Batch:
     def config(self) -> dict:
         return capi.lb_batch_config(self.b)
 
+    def set_config(self, shape: int, blocks_per_sm: int) -> None:
+        """Launch form by hand (lb_batch_set_config): shapes 0-2 plain loads, 3-4 tensor copies."""
+        capi.lb_batch_set_config(self.b, shape, blocks_per_sm)
+
     @property
     def steps_done(self) -> int:
         return capi.lb_batch_steps_done(self.b)
 
     def state(self, i: int):
-        """Current state of lattice i: [9, ny, nx] view of the current pool (deviations)."""
+        """Current state of lattice i: [9, ny, nx] view of the current pool (deviations;
+        rows are strided by nx rounded up to a multiple of 4)."""
         self.stream.synchronize()
         pool = self.pool_a if capi.lb_batch_state(self.b) == self.pool_a.data_ptr() else self.pool_b
         off = capi.lb_batch_offset(self.b, i)
+        sx = capi.lb_batch_row_stride(self.b, i)
         ny, nx = self.shapes[i]
-        return pool[off:off + 9 * nx * ny].view(9, ny, nx)
+        return pool[off:off + 9 * sx * ny].view(9, ny, sx)[:, :, :nx]
+
+    def status(self) -> None:
+        """Raises LBError if a bounded wait of the tensor-copy kernel gave up."""
+        capi.lb_batch_status(self.b)
 
     def density(self, i: int):
         return self.state(i).double().sum(0) + self.rho_refs[i]

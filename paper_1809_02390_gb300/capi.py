@@ -76,6 +76,10 @@ SIGNATURES = [
     ("lb_batch_state", _V, [_V]),
     ("lb_batch_steps_done", ctypes.c_int64, [_V]),
     ("lb_batch_offset", ctypes.c_int64, [_V, ctypes.c_int]),
+    ("lb_batch_row_stride", ctypes.c_int, [_V, ctypes.c_int]),
+    ("lb_batch_uses_tma", ctypes.c_int, [_V]),
+    ("lb_batch_set_config", ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
+    ("lb_batch_status", ctypes.c_int, [_V]),
     ("lb_batch_derived", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(lb_derived)]),
     ("lb_batch_last_error", ctypes.c_char_p, [_V]),
     ("lb_batch_free", None, [_V]),
@@ -247,7 +251,16 @@ def lb_batch_tune(b: int, trial_steps: int) -> float:
 def lb_batch_config(b: int) -> dict:
     ty, bps, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     check_batch(lib().lb_batch_config(b, ctypes.byref(ty), ctypes.byref(bps), ctypes.byref(grid)), b)
-    return {"tile_y": ty.value, "blocks_per_sm": bps.value, "grid": grid.value}
+    return {"tile_y": ty.value, "blocks_per_sm": bps.value, "grid": grid.value,
+            "tensor_copies": bool(lib().lb_batch_uses_tma(b))}
+
+
+def lb_batch_set_config(b: int, shape: int, blocks_per_sm: int) -> None:
+    check_batch(lib().lb_batch_set_config(b, shape, blocks_per_sm), b)
+
+
+def lb_batch_status(b: int) -> None:
+    check_batch(lib().lb_batch_status(b), b)
 
 
 def lb_batch_state(b: int) -> int:
@@ -260,6 +273,10 @@ def lb_batch_steps_done(b: int) -> int:
 
 def lb_batch_offset(b: int, i: int) -> int:
     return lib().lb_batch_offset(b, i)
+
+
+def lb_batch_row_stride(b: int, i: int) -> int:
+    return lib().lb_batch_row_stride(b, i)
 
 
 def lb_batch_derived(b: int, i: int) -> dict:

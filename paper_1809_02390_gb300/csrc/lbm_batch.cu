@@ -1,20 +1,24 @@
 // Batched solver: many independent periodic lattices, each with its own size and
-// parameters, advanced together.  One persistent kernel launch per time step
-// walks a flat list of 32 x TY tiles spanning all lattices (each block takes
-// tiles blockIdx.x, blockIdx.x + gridDim.x, ...), stages the coefficients of the
+// parameters, advanced together.  One kernel launch per time step walks a flat
+// list of 32 x TY tiles spanning all lattices, stages the coefficients of the
 // tile's lattice in shared memory and runs the same tile code as the
-// single-lattice fused step.  Runs of steps are captured once into CUDA graphs
-// and replayed.  The autotuner times every (tile height, resident blocks per SM)
-// pair on the batch itself and keeps the fastest.
+// single-lattice fused step; the fastest form is the persistent tensor-copy
+// kernel of the single-lattice FP32 step with one tensor map per lattice.  Rows
+// are stored with a stride of nx rounded up to a multiple of 4 floats, as the
+// tensor copies require.  Runs of steps are captured once into CUDA graphs and
+// replayed.  The autotuner times every launch form on the batch itself and keeps
+// the fastest.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "lbm_handle.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 template <typename V>
@@ -27,23 +31,28 @@ using namespace lbm;
 
 struct BatchLattice {
   int nx, ny;
+  int sx;            // row stride: nx rounded up to a multiple of 4
   long long offset;  // element offset of the lattice's plane 0 in a pool
   int tile_start;    // index of its first tile in the flat tile list
   int tiles_x;       // tiles per row of tiles
 };
 
+__host__ __device__ constexpr int row_stride(int nx) { return (nx + 3) / 4 * 4; }
+
 // Launch shapes the autotuner chooses among: tile height and the register budget
-// the kernel is compiled for (resident blocks per SM it must allow).
-constexpr int kShapes = 3;
-constexpr int kShapeTY[kShapes] = {16, 16, 32};
-constexpr int kShapeMinBlocks[kShapes] = {4, 3, 2};
+// the kernel is compiled for (resident blocks per SM it must allow), plain loads;
+// shapes 3 and 4 are the persistent tensor-copy kernel (32 x 16 tiles, the tile
+// list of shape 0) at 80 and 128 registers.
+constexpr int kShapes = 5;
+constexpr int kShapeTMA = 3;  // first tensor-copy shape
+constexpr int kShapeTY[kShapes] = {16, 16, 32, 16, 16};
+__host__ __device__ constexpr bool is_tma(int shape) { return shape >= kShapeTMA; }
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: the pools end where they started)
 
-// Register budget of 64 per thread (4 blocks of 256 or 2 of 512 threads per SM),
-// as for the single-lattice kernel.
-// One record per tile: its lattice, origin and the lattice's size and pool offset.
+// One record per tile: its lattice, origin and the lattice's size, row stride and
+// pool offset.
 struct TileRec {
-  int lat, x0, y0, nx, ny, pad;
+  int lat, x0, y0, nx, ny, sx;
   long long offset;
 };
 
@@ -77,8 +86,8 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
   TileRec ti = tiles[t];
   int word = threadIdx.x < kCoefWords ? reinterpret_cast<const int*>(coef + ti.lat)[threadIdx.x] : 0;
   if constexpr (!PERSIST) {  // one block per tile
-    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, common, cs, ti.x0, ti.y0,
-                               rs, StoreCoef{&cs, word, true});
+    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, ti.sx, common, cs, ti.x0,
+                               ti.y0, rs, StoreCoef{&cs, word, true});
     return;
   }
   int last = -1;
@@ -92,13 +101,89 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
     }
     const StoreCoef hook{&cs, word, ti.lat != last};
     last = ti.lat;
-    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, common, cs, ti.x0, ti.y0,
-                               rs, hook);
+    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, ti.sx, common, cs, ti.x0,
+                               ti.y0, rs, hook);
     if (tn >= total_tiles) break;
     __syncthreads();  // shared densities and coefficients are reused by the next tile
     t = tn;
     ti = tin;
     word = wordn;
+  }
+}
+
+// Persistent tensor-copy form (the single-lattice k_step_tma over the tile list of
+// all lattices).  Per tile: thread 0 bulk-copies the lattice's coefficients into
+// shared memory on the mbarrier and, for an interior tile, issues the nine window
+// copies through that lattice's tensor map (maps[lat]); for a wrapping tile every
+// thread issues its asynchronous copies of the window.  The next tile is staged
+// once the current window is in registers, so it travels during the collision.
+// Tile records (written by thread 0 one tile ahead), coefficients and densities
+// are double-buffered in shared memory.  A wait that gives up sets *err.
+static_assert(sizeof(LatCoef<f2>) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+template <int MINB>
+__global__ void __launch_bounds__(kFusedThreads, MINB)
+    k_step_batch_tma(const float* __restrict__ pool_in, float* __restrict__ pool_out,
+                     const TileRec* __restrict__ tiles, const LatCoef<f2>* __restrict__ coef,
+                     const CUtensorMap* __restrict__ maps, int total_tiles, VCoef<f2> common, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
+  __shared__ float rs[2][kTileY + 2][kTileX + 2];
+  __shared__ __align__(16) LatCoef<f2> cs[2];
+  __shared__ TileRec rec[2];
+  __shared__ __align__(8) unsigned long long bar;
+  if (blockIdx.x >= total_tiles) return;
+  auto kind_of = [](const TileRec& r) { return tile_kind(r.x0, r.y0, r.nx, r.ny); };
+  // All threads: stage the tile of record r, its coefficients into cs[slot].
+  auto issue = [&](const TileRec& r, int slot) {
+    const int kind = kind_of(r);
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      if (kind == kTensorCopy)
+        issue_windows(win, maps + r.lat, r.x0, r.y0, &bar, sizeof(LatCoef<f2>));
+      else
+        mbar_expect_tx(&bar, sizeof(LatCoef<f2>));
+      bulk_load(&cs[slot], coef + r.lat, sizeof(LatCoef<f2>), &bar);
+    }
+    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, r.sx, r.x0, r.y0);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    rec[0] = tiles[blockIdx.x];
+  }
+  __syncthreads();
+  issue(rec[0], 0);
+  unsigned parity = 0;
+  int buf = 0;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    // The next record, for everyone after the barrier below (its slot was last read
+    // before the previous barrier).
+    if (threadIdx.x == 0 && tn < total_tiles) rec[buf ^ 1] = tiles[tn];
+    const TileRec ti = rec[buf];
+    const int kind = kind_of(ti);
+    const bool late = !mbar_wait(&bar, parity);
+    parity ^= 1u;
+    if (kind == kAsyncCopy) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    float f[kTileRows][9];
+    if (kind == kPlainLoad)
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, ti.sx, ti.x0, ti.y0, f, rs[buf]);
+    else  // read even after a failed wait (in bounds; the block then returns)
+      window_tile(win, f, rs[buf]);
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait(&bar, parity ^ 1u);
+      }
+      return;
+    }
+    if (tn < total_tiles) issue(rec[buf ^ 1], buf ^ 1);
+    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, ti.sx, common, cs[buf], ti.x0, ti.y0,
+                                    rs[buf]);
+    buf ^= 1;
   }
 }
 
@@ -117,7 +202,9 @@ const void* batch_kernel(int shape) {
   switch (shape) {
     case 0: return reinterpret_cast<const void*>(k_step_batch<float, 16, 4, true>);
     case 1: return reinterpret_cast<const void*>(k_step_batch<float, 16, 3, true>);
-    default: return reinterpret_cast<const void*>(k_step_batch<float, 32, 2, true>);
+    case 2: return reinterpret_cast<const void*>(k_step_batch<float, 32, 2, true>);
+    case 3: return reinterpret_cast<const void*>(k_step_batch_tma<3>);
+    default: return reinterpret_cast<const void*>(k_step_batch_tma<2>);
   }
 }
 
@@ -134,6 +221,9 @@ struct lb_batch {
   BatchLattice* d_desc[kShapes];
   TileRec* d_tiles[kShapes];
   LatCoef<f2>* d_coef;
+  CUtensorMap* d_maps;  // [2][n]: lattice maps in pool 0, then in pool 1
+  int* d_err;           // set by a bounded wait of the tensor-copy kernel that gave up
+  bool tma_ok;          // every lattice large enough to have interior tiles has its maps
   VCoef<f2> common;
   cudaStream_t stream;
   int sms;
@@ -157,12 +247,12 @@ int berr(lb_batch* b, int code, const char* fmt, const char* detail = "") {
   return code;
 }
 
-size_t lattice_elems(const lb_params& p) { return ((9 * size_t(p.nx) * p.ny + 63) / 64) * 64; }
+size_t lattice_elems(const lb_params& p) { return ((9 * size_t(row_stride(p.nx)) * p.ny + 63) / 64) * 64; }
 
 int max_blocks(lb_batch* b, int shape, int* out) {
   const void* k = batch_kernel(shape);
   const int threads = kShapeTY[shape] == 16 ? TileShape<16>::threads : TileShape<32>::threads;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, threads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, threads, is_tma(shape) ? kTmaSmem : 0);
   if (e != cudaSuccess) return berr(b, LB_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
   if (*out < 1) *out = 1;
   return LB_OK;
@@ -176,7 +266,16 @@ void launch_one(lb_batch* b, int from) {
   const int s = b->shape;
   const TileRec* tiles = b->d_tiles[s];
   const int total = b->total_tiles[s];
-  if (s == 0)
+  if (is_tma(s)) {
+    const int grid = std::min(b->blocks_per_sm * b->sms, total);
+    const CUtensorMap* maps = b->d_maps + from * b->n;
+    if (s == kShapeTMA)
+      k_step_batch_tma<3><<<grid, kFusedThreads, kTmaSmem, b->stream>>>(in, out, tiles, b->d_coef, maps, total,
+                                                                         b->common, b->d_err);
+    else
+      k_step_batch_tma<2><<<grid, kFusedThreads, kTmaSmem, b->stream>>>(in, out, tiles, b->d_coef, maps, total,
+                                                                         b->common, b->d_err);
+  } else if (s == 0)
     launch_shape<16, 4>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
   else if (s == 1)
     launch_shape<16, 3>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
@@ -226,11 +325,15 @@ size_t total_tiles_of(const lb_params* ps, int n, int TY) {
   return t;
 }
 
+// The tensor-copy shape walks the tile list of shape 0; the other shapes own one.
+constexpr int kTileLists = kShapeTMA;
+
 size_t lb_batch_meta_bytes(const lb_params* ps, int n) {
   if (!ps || n < 1) return 0;
   size_t tiles = 0;
-  for (int s = 0; s < kShapes; ++s) tiles += total_tiles_of(ps, n, kShapeTY[s]);
-  return size_t(n) * (kShapes * sizeof(BatchLattice) + sizeof(LatCoef<f2>)) + tiles * sizeof(TileRec) + 4096;
+  for (int s = 0; s < kTileLists; ++s) tiles += total_tiles_of(ps, n, kShapeTY[s]);
+  return size_t(n) * (kTileLists * sizeof(BatchLattice) + sizeof(LatCoef<f2>) + 2 * sizeof(CUtensorMap)) +
+         tiles * sizeof(TileRec) + 4096;
 }
 
 int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
@@ -280,10 +383,11 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     h_coef[i] = LatCoef<f2>{full.G2,        full.rho_ref, full.m2rr, full.lam_RT, full.neg_lam_a,
                             full.neg_2lam_a, full.g15,     full.Q1G2, full.Q2G2,   full.Q78G2};
     h_coefd[i] = make_vcoef<double>(b->p[i], b->d[i]);
-    for (int s = 0; s < kShapes; ++s) {
+    for (int s = 0; s < kTileLists; ++s) {
       BatchLattice L;
       L.nx = ps[i].nx;
       L.ny = ps[i].ny;
+      L.sx = row_stride(ps[i].nx);
       L.offset = (long long)off;
       L.tiles_x = (ps[i].nx + kTileX - 1) / kTileX;
       L.tile_start = 0;
@@ -292,7 +396,7 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     off += lattice_elems(ps[i]);
     total_nodes += size_t(ps[i].nx) * ps[i].ny;
   }
-  for (int s = 0; s < kShapes; ++s) {
+  for (int s = 0; s < kTileLists; ++s) {
     int start = 0;
     for (int i = 0; i < n; ++i) {
       b->desc[s][i].tile_start = start;
@@ -300,29 +404,54 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     }
     b->total_tiles[s] = start;
   }
-  // Metadata in the caller's buffer: descriptors and tile records per tile shape,
-  // then coefficients, each 256-byte aligned.
+  for (int s = kShapeTMA; s < kShapes; ++s) b->total_tiles[s] = b->total_tiles[0];
+  // Metadata in the caller's buffer: descriptors and tile records per tile list,
+  // coefficients, tensor maps, the wait-error word, each 256-byte aligned.
   auto align = [](uintptr_t v) { return (v + 255) / 256 * 256; };
-  std::vector<TileRec> h_tiles[kShapes];
-  for (int s = 0; s < kShapes; ++s) {
+  std::vector<TileRec> h_tiles[kTileLists];
+  for (int s = 0; s < kTileLists; ++s) {
     h_tiles[s].reserve(b->total_tiles[s]);
     for (int i = 0; i < n; ++i) {
+      const BatchLattice& L = b->desc[s][i];
       const int tyn = (ps[i].ny + kShapeTY[s] - 1) / kShapeTY[s];
       for (int r = 0; r < tyn; ++r)
-        for (int q = 0; q < b->desc[s][i].tiles_x; ++q)
-          h_tiles[s].push_back(TileRec{i, q * kTileX, r * kShapeTY[s], ps[i].nx, ps[i].ny, 0, b->desc[s][i].offset});
+        for (int q = 0; q < L.tiles_x; ++q)
+          h_tiles[s].push_back(TileRec{i, q * kTileX, r * kShapeTY[s], L.nx, L.ny, L.sx, L.offset});
     }
   }
   uintptr_t m = align(reinterpret_cast<uintptr_t>(meta));
-  for (int s = 0; s < kShapes; ++s) {
+  for (int s = 0; s < kTileLists; ++s) {
     b->d_desc[s] = reinterpret_cast<BatchLattice*>(m);
     m = align(m + n * sizeof(BatchLattice));
     b->d_tiles[s] = reinterpret_cast<TileRec*>(m);
     m = align(m + h_tiles[s].size() * sizeof(TileRec));
   }
+  for (int s = kShapeTMA; s < kShapes; ++s) {
+    b->d_desc[s] = b->d_desc[0];
+    b->d_tiles[s] = b->d_tiles[0];
+  }
   b->d_coef = reinterpret_cast<LatCoef<f2>*>(m);
+  m = align(m + n * sizeof(LatCoef<f2>));
+  b->d_maps = reinterpret_cast<CUtensorMap*>(m);
+  m = align(m + 2 * size_t(n) * sizeof(CUtensorMap));
+  b->d_err = reinterpret_cast<int*>(m);
+  // Tensor maps of every lattice in both pools.  A lattice below 40 x 18 has no
+  // interior tile (those need nx >= 68, ny >= 34) and keeps a zero map it never uses.
+  std::vector<CUtensorMap> h_maps(2 * size_t(n));
+  std::memset(h_maps.data(), 0, h_maps.size() * sizeof(CUtensorMap));
+  b->tma_ok = true;
+  for (int side = 0; side < 2; ++side)
+    for (int i = 0; i < n; ++i) {
+      const BatchLattice& L = b->desc[0][i];
+      if (L.nx < kTmaCols || L.ny < kTmaRows) continue;
+      float* base = static_cast<float*>(side ? pool_b : pool_a) + L.offset;
+      if (!encode_population_map(&h_maps[side * size_t(n) + i], base, L.nx, L.ny, L.sx)) b->tma_ok = false;
+    }
   cudaError_t e = cudaSuccess;
-  for (int s = 0; s < kShapes && e == cudaSuccess; ++s) {
+  e = cudaMemcpyAsync(b->d_maps, h_maps.data(), h_maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                      b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  for (int s = 0; s < kTileLists && e == cudaSuccess; ++s) {
     e = cudaMemcpyAsync(b->d_desc[s], b->desc[s].data(), n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->d_tiles[s], h_tiles[s].data(), h_tiles[s].size() * sizeof(TileRec),
@@ -343,7 +472,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const size_t N = size_t(ps[i].nx) * ps[i].ny;
     k_init_rest<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
-        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny, h_coefd[i]);
+        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny, b->desc[0][i].sx,
+        h_coefd[i]);
     e = cudaGetLastError();
     node_off += N;
   }
@@ -393,9 +523,10 @@ int lb_batch_tune(lb_batch* b, int trial_steps, double* best_ms_per_step) {
   int best_shape = b->shape, best_bps = b->blocks_per_sm;
   int64_t tuned_steps = 0;
   for (int s = 0; s < kShapes; ++s) {
+    if (is_tma(s) && !b->tma_ok) continue;
     int mb = 1;
     if (max_blocks(b, s, &mb) != LB_OK) return LB_ECUDA;
-    for (int bps = 0; bps <= mb; ++bps) {
+    for (int bps = is_tma(s) ? 1 : 0; bps <= mb; ++bps) {  // the tensor-copy kernel is persistent only
       b->shape = s;
       b->blocks_per_sm = bps;
       launch_one(b, b->cur);  // warm-up (two launches keep the pool parity)
@@ -435,6 +566,32 @@ int lb_batch_config(const lb_batch* b, int* tile_y, int* blocks_per_sm, int* gri
   return LB_OK;
 }
 
+int lb_batch_set_config(lb_batch* b, int shape, int blocks_per_sm) {
+  if (!b) return LB_EINVAL;
+  if (shape < 0 || shape >= kShapes) return berr(b, LB_EINVAL, "lb_batch_set_config: shape out of range%s");
+  if (is_tma(shape) && !b->tma_ok)
+    return berr(b, LB_ENOTSUP, "lb_batch_set_config: a lattice of the batch has no tensor map%s");
+  int mb = 1;
+  if (max_blocks(b, shape, &mb) != LB_OK) return LB_ECUDA;
+  if (blocks_per_sm < (is_tma(shape) ? 1 : 0) || blocks_per_sm > mb)
+    return berr(b, LB_EINVAL, "lb_batch_set_config: blocks_per_sm out of range for the shape%s");
+  b->shape = shape;
+  b->blocks_per_sm = blocks_per_sm;
+  return LB_OK;
+}
+
+int lb_batch_uses_tma(const lb_batch* b) { return b && is_tma(b->shape) ? 1 : 0; }
+
+int lb_batch_status(lb_batch* b) {
+  if (!b) return LB_EINVAL;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess && v) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "lb_batch_status: %s", cudaGetErrorString(e));
+  return v ? berr(b, LB_ETIMEOUT, "a bounded wait for a tensor copy gave up%s") : LB_OK;
+}
+
 void* lb_batch_state(lb_batch* b) { return b ? b->pool[b->cur] : nullptr; }
 
 int64_t lb_batch_steps_done(const lb_batch* b) { return b ? b->steps : -1; }
@@ -442,6 +599,11 @@ int64_t lb_batch_steps_done(const lb_batch* b) { return b ? b->steps : -1; }
 int64_t lb_batch_offset(const lb_batch* b, int i) {
   if (!b || i < 0 || i >= b->n) return -1;
   return b->desc[0][i].offset;
+}
+
+int lb_batch_row_stride(const lb_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return -1;
+  return b->desc[0][i].sx;
 }
 
 int lb_batch_derived(const lb_batch* b, int i, lb_derived* out) {

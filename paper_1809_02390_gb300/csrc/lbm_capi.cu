@@ -157,8 +157,8 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
     const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
     if constexpr (std::is_same<store_t, float>::value && std::is_same<V, f2>::value) {
       if (h->use_tma) {
-        k_step_tma<V><<<h->tma_grid, kFusedThreads, kTmaSmem, h->stream>>>(h->tmap[h->cur], fin, fout, nx,
-                                                                                     ny, cv);
+        k_step_tma<V, false><<<h->tma_grid, kFusedThreads, kTmaSmem, h->stream>>>(h->tmap[h->cur], fin, fout, nx, ny, cv,
+                                                                            h->wait_error);
         return;
       }
     }
@@ -184,9 +184,14 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// 3-D map of one FP32 population buffer: x (nx), y (ny), plane (9); box of one
-// plane window (kTmaCols x kTmaRows).  False if the layout does not allow it.
-bool encode_map(CUtensorMap* map, void* base, int nx, int ny) {
+}  // namespace
+
+namespace lbm {
+
+// 3-D map of one FP32 population buffer: x (nx), y (ny, row stride sx), plane
+// (9); box of one plane window (kTmaCols x kTmaRows).  False if the layout does
+// not allow it (base not 16-byte aligned, row stride not a multiple of 16 bytes).
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -196,15 +201,22 @@ bool encode_map(CUtensorMap* map, void* base, int nx, int ny) {
       return false;
     fn = reinterpret_cast<EncodeTiledFn>(p);
   }
-  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(nx) * 4) % 16 != 0) return false;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(sx) * 4) % 16 != 0 || sx < nx) return false;
   const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), 9};
-  const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * ny * 4};
+  const cuuint64_t strides[2] = {cuuint64_t(sx) * 4, cuuint64_t(sx) * ny * 4};
   const cuuint32_t box[3] = {cuuint32_t(kTmaCols), cuuint32_t(kTmaRows), 1};
   const cuuint32_t estride[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+}  // namespace lbm
+
+namespace {
+
+// Set by a bounded wait of the tensor-copy step that gave up (read and cleared by lb_status).
+__device__ int g_wait_error;
 
 int configure(lb_handle* h) {
   const int rc = configure_device(h);
@@ -213,12 +225,16 @@ int configure(lb_handle* h) {
   // lattice holding at least one interior tile; otherwise the plain fused kernel runs.
   h->use_tma = h->p.precision == LB_FP32 && h->variant == LB_FUSED && h->p.nx % 4 == 0 &&
                h->p.nx >= 2 * kTileX + kTmaCols && h->p.ny >= 2 * kTileY + kTmaRows &&
-               encode_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny) && encode_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny);
+               encode_population_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny, h->p.nx) &&
+               encode_population_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny, h->p.nx);
   if (h->use_tma) {
+    void* w = nullptr;
+    LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_error));
+    h->wait_error = static_cast<int*>(w);
     // Persistent grid: as many blocks as can be resident.
-    LB_CUDA(h, cudaFuncSetAttribute(k_step_tma<f2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmem)));
+    LB_CUDA(h, cudaFuncSetAttribute(k_step_tma<f2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmem)));
     int per_sm = 0, dev = 0, sms = 0;
-    LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<f2>, kFusedThreads, kTmaSmem));
+    LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<f2, false>, kFusedThreads, kTmaSmem));
     LB_CUDA(h, cudaGetDevice(&dev));
     LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int tiles = ((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY);
@@ -370,9 +386,9 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   }
   const unsigned blocks = unsigned((N + 255) / 256);
   switch (p->precision) {
-    case LB_FP64: k_init_rest<double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny, h->cd); break;
-    case LB_FP32: k_init_rest<float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, h->cd); break;
-    default: k_init_rest<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny, h->cd); break;
+    case LB_FP64: k_init_rest<double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny, p->nx, h->cd); break;
+    case LB_FP32: k_init_rest<float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, p->nx, h->cd); break;
+    default: k_init_rest<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny, p->nx, h->cd); break;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return bail(e, "init kernel launch");

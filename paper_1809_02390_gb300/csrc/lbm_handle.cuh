@@ -21,9 +21,16 @@ struct lb_handle {
   int tma_grid;           // persistent grid of that kernel
   int tma_grid_auto;      // its default: resident capacity, at most the tile count
   CUtensorMap tmap[2];    // 3-D maps (x, y, plane) of f[0] and f[1]
+  int* wait_error;        // device word set by a bounded wait that gave up
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
   lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
   lbm::VCoef<double> cd;
   char err[512];
 };
 
+namespace lbm {
+// 3-D tensor map (x, y, plane) of an FP32 population buffer with row stride sx,
+// box = one plane window of the tensor-copy step; false if the layout does not
+// allow one (lbm_capi.cu).
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx);
+}  // namespace lbm

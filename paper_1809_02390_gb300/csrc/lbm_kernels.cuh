@@ -20,13 +20,14 @@ __host__ __device__ __forceinline__ int wrap(int v, int n) {
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // Pulls the nine populations of row r at columns (cm, cc, cp) = (x-1, x, x+1):
-// f_i(x, r) = fbar_i(x - e_i, r - e_i) (supplement Eq. 2), periodic.  32-bit
-// offsets: the library limits 9 nx ny to below 2^31.
+// f_i(x, r) = fbar_i(x - e_i, r - e_i) (supplement Eq. 2), periodic.  sx: row
+// stride in elements (nx, or nx rounded up in the batched pools).  32-bit
+// offsets: the library limits 9 sx ny to below 2^31.
 template <typename real, typename store_t>
-__device__ __forceinline__ void pull_row(const store_t* __restrict__ fin, int plane, int nx, int ny, int r, int cm,
+__device__ __forceinline__ void pull_row(const store_t* __restrict__ fin, int plane, int sx, int ny, int r, int cm,
                                          int cc, int cp, real (&f)[9]) {
   const int rm = r == 0 ? ny - 1 : r - 1, rp = r == ny - 1 ? 0 : r + 1;
-  const int oc = r * nx, om = rm * nx, op = rp * nx;
+  const int oc = r * sx, om = rm * sx, op = rp * sx;
   f[0] = ld_st(fin + (oc + cc));
   f[1] = ld_st(fin + (plane + oc + cm));
   f[2] = ld_st(fin + (2 * plane + om + cc));
@@ -76,13 +77,13 @@ struct TileShape {
 // densities, collision (one packed FP32x2 evaluation for V = f2), store.
 template <typename V, typename store_t, int TY>
 __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
-                                             store_t* __restrict__ fout, int nx, int ny, const VCoef<V>& c,
+                                             store_t* __restrict__ fout, int nx, int ny, int sx, const VCoef<V>& c,
                                              const LatCoef<V>& l, int x0, int y0,
                                              const typename LaneType<V>::type (*rs)[kTileX + 2]) {
   using real = typename LaneType<V>::type;
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int plane = nx * ny;
+  const int plane = sx * ny;
   const int gx = x0 + tx;
   real Sx[kTileRows], Sy[kTileRows];
 #pragma unroll
@@ -112,7 +113,7 @@ __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&
   for (int k = 0; k < kTileRows; ++k) {
     const int gy = y0 + ty + k * Shape::stride;
     if (gx < nx && gy < ny) {
-      const int off = gy * nx + gx;
+      const int off = gy * sx + gx;
 #pragma unroll
       for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), out[k][i]);
     }
@@ -125,13 +126,14 @@ struct NoHook {
 
 // Phase 1 of a tile with plain loads: pulls the populations of the thread's two
 // nodes into f and writes the densities of tile + ring to rs (shared array of
-// (TY + 2) x (TX + 2) densities).  (x0, y0): tile origin.  Periodic wrap.
+// (TY + 2) x (TX + 2) densities).  (x0, y0): tile origin; sx: row stride.
+// Periodic wrap.
 template <typename real, typename store_t, int TY>
-__device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int nx, int ny, int x0, int y0,
+__device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int nx, int ny, int sx, int x0, int y0,
                                           real (&f)[kTileRows][9], real (*rs)[kTileX + 2]) {
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int plane = nx * ny;
+  const int plane = sx * ny;
   const bool small = nx <= kTileX || ny <= TY;  // tiles may wrap more than once
   const int gx = x0 + tx;
   const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
@@ -139,7 +141,7 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
     const int gy = y0 + ty + k * Shape::stride;
-    pull_row(fin, plane, nx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
+    pull_row(fin, plane, sx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
   }
   // Ring: the row above, the row below, then the left and right columns.
   const int t = threadIdx.x;
@@ -158,7 +160,7 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
     }
     const int hx = small ? wrap(x0 - 1 + wx, nx) : wrap1(x0 - 1 + wx, nx);
     const int hy = small ? wrap(y0 - 1 + wy, ny) : wrap1(y0 - 1 + wy, ny);
-    pull_row(fin, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
+    pull_row(fin, plane, sx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
   }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
@@ -170,22 +172,22 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
 // barrier (the batched kernel stores its lattice coefficients there).
 template <typename V, typename store_t, int TY, typename Hook = NoHook>
 __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
-                                          int ny, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
+                                          int ny, int sx, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
                                           typename LaneType<V>::type (*rs)[kTileX + 2],
                                           const Hook& before_sync = Hook()) {
   using real = typename LaneType<V>::type;
   real f[kTileRows][9];
-  load_tile<real, store_t, TY>(fin, nx, ny, x0, y0, f, rs);
+  load_tile<real, store_t, TY>(fin, nx, ny, sx, x0, y0, f, rs);
   before_sync();
   __syncthreads();
-  collide_tile<V, store_t, TY>(f, fout, nx, ny, c, l, x0, y0, rs);
+  collide_tile<V, store_t, TY>(f, fout, nx, ny, sx, c, l, x0, y0, rs);
 }
 
 template <typename V, typename store_t>
 __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
     k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c) {
   __shared__ typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
-  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
+  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, nx, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
                                 rs);
 }
 
@@ -226,12 +228,13 @@ __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restri
 // Rest equilibrium from an initial density (computed in FP64, rounded once):
 // m_eq(rho, u = 0) = (rho, -2 rho + 2 eta, rho + beta_2 eta, 0, ...), minus rho_ref M w.
 template <typename store_t>
-__global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny,
+__global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny, int sx,
                             VCoef<double> c) {
-  const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const size_t N = size_t(nx) * ny;
-  if (n >= N) return;
-  const double rho = rho0[n];
+  const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= size_t(nx) * ny) return;
+  const size_t N = size_t(sx) * ny;                            // plane stride
+  const size_t n = (k / nx) * size_t(sx) + k % nx;             // node (x, y) at row stride sx
+  const double rho = rho0[k];
   double pe, dpe;
   eos(c, rho, pe, dpe);
   const double eta = 3.0 * (pe + 0.5 * c.G2 * rho * rho) - rho;

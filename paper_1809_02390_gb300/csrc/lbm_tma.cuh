@@ -29,11 +29,13 @@ constexpr long long kWaitSpins = 1ll << 22;                 // bound of the mbar
 // A tensor copy's shared-memory destination must be 128-byte aligned.
 static_assert((kTmaPlane * 4) % 128 == 0, "plane windows must start on 128-byte boundaries");
 
-__device__ __constant__ const int kEX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__device__ __constant__ const int kEY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-
-// Set when a bounded wait gave up (read and cleared by lb_status).
-static __device__ int g_wait_error;
+// D2Q9 velocity components e_ix, e_iy (folded to constants in unrolled loops).
+__host__ __device__ constexpr int ex_of(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey_of(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -75,6 +77,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Plain bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to shared memory, completing on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 // Whether the TMA windows of the tile at (x0, y0) lie inside the lattice.
 __device__ __forceinline__ bool tma_interior(int x0, int y0, int nx, int ny) {
   return x0 >= 4 && x0 + kTmaCols - 4 <= nx && y0 >= 2 && y0 + kTmaRows <= ny;
@@ -103,19 +113,107 @@ __device__ __forceinline__ void ring_cell(int t, int& wx, int& wy) {
   }
 }
 
+// Windows of tiles that wrap, by per-thread asynchronous 4-byte copies (cp.async):
+// the window of such a tile gets the cells a tensor copy would deliver, with
+// periodic source coordinates, so that every tile of a lattice of at least
+// kTmaCols x kTmaRows nodes is staged ahead (every coordinate then lies in
+// [-4, 2n) and one conditional wrap suffices).  240 threads = 6 window rows x 40
+// columns per pass, 3 passes, 9 planes: 27 copies per thread.
+__device__ __forceinline__ bool async_window_ok(int nx, int ny) { return nx >= kTmaCols && ny >= kTmaRows; }
+
+constexpr int kAsyncThreads = 6 * kTmaCols;
+static_assert(kTmaRows % 6 == 0 && kAsyncThreads <= kFusedThreads, "window rows split in passes of 6");
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// All threads: the window of the (wrapping) tile at (x0, y0) of a lattice with
+// populations at fin (row stride sx) into win.  Plane i's window row r holds
+// lattice row y0 - 1 - e_iy + r, window column c lattice column x0 - 4 + c.
+__device__ __forceinline__ void issue_window_async(float* win, const float* __restrict__ fin, int nx, int ny,
+                                                   int sx, int x0, int y0) {
+  const int j = threadIdx.x;
+  if (j < kAsyncThreads) {
+    const int c = j % kTmaCols, r0 = j / kTmaCols;
+    const int gx = wrap1(x0 - 4 + c, nx);
+    const int plane = sx * ny;
+    int src[kTmaRows / 6][3];  // [pass][e_iy + 1]: offset of the source cell within a plane
+#pragma unroll
+    for (int q = 0; q < kTmaRows / 6; ++q)
+#pragma unroll
+      for (int e = 0; e < 3; ++e) src[q][e] = wrap1(y0 - e + r0 + 6 * q, ny) * sx + gx;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int q = 0; q < kTmaRows / 6; ++q)
+        cp_async4(win + i * kTmaPlane + (r0 + 6 * q) * kTmaCols + c, fin + (i * plane + src[q][ey_of(i) + 1]));
+  }
+  cp_async_commit();
+}
+
+// Phase 1 of an interior tile from its staged windows: the populations of the
+// thread's two nodes (window row ly + 1, column lx + 4 - e_ix for plane i) into f,
+// the densities of tile + ring into rs.
+__device__ __forceinline__ void window_tile(const float* __restrict__ win, float (&f)[kTileRows][9],
+                                            float (*rs)[kTileX + 2]) {
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int ly = ty + k * kRowStride;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[k][i] = win[i * kTmaPlane + (ly + 1) * kTmaCols + tx + 4 - ex_of(i)];
+    rs[ly + 1][tx + 1] = sum9(f[k]);
+  }
+  if (threadIdx.x < TileShape<kTileY>::ring) {
+    int wx, wy;
+    ring_cell(threadIdx.x, wx, wy);
+    float g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = win[i * kTmaPlane + wy * kTmaCols + wx + 3 - ex_of(i)];
+    rs[wy][wx] = sum9(g);
+  }
+}
+
+// The nine copies of the interior tile at (x0, y0) into win, completing on bar
+// (one thread).
+__device__ __forceinline__ void issue_windows(float* win, const CUtensorMap* map, int x0, int y0,
+                                              unsigned long long* bar, unsigned extra_bytes = 0) {
+  mbar_expect_tx(bar, kTmaBytes + extra_bytes);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) tma_load_3d(win + i * kTmaPlane, map, x0 - 4, y0 - 1 - ey_of(i), i, bar);
+}
+
+// How a tile's window is staged: by tensor copies (interior), by per-thread
+// asynchronous copies (wrapping tile of a lattice of at least 40 x 18), or not at
+// all (plain loads in phase 1).
+enum TileKind { kTensorCopy = 0, kAsyncCopy = 1, kPlainLoad = 2 };
+
+template <bool ASYNC_EDGES = true>
+__device__ __forceinline__ int tile_kind(int x0, int y0, int nx, int ny) {
+  return tma_interior(x0, y0, nx, ny) ? kTensorCopy
+                                      : (ASYNC_EDGES && async_window_ok(nx, ny) ? kAsyncCopy : kPlainLoad);
+}
+
 // Persistent form: block b takes tiles b, b + G, b + 2G, ... (G = gridDim.x, tiles
 // row-major over the lattice, so the tiles in flight at one time are neighbours
 // and their overlapping windows meet in L2).  One window buffer per block: once
 // every thread holds its tile's populations in registers and the densities are
-// in shared memory (the block barrier), the buffer is free and the nine copies
-// of the block's next tile are issued into it, so that they travel while the
-// block computes the force stencil and the collision of the current tile.  The
-// density tile is double-buffered, which leaves one barrier per tile.  Tiles
-// whose windows would wrap take the plain loads of load_tile.
-template <typename V>
+// in shared memory (the block barrier), the buffer is free and the block's next
+// tile is staged into it (tensor copies issued by thread 0 on the mbarrier, or
+// the per-thread copies of a wrapping tile), so that it travels while the block
+// computes the force stencil and the collision of the current tile.  The density
+// tile is double-buffered, which leaves one barrier per tile (two for a wrapping
+// tile: every thread's copies must have landed).  A wait that gives up sets *err.
+// ASYNC_EDGES = false leaves wrapping tiles to plain loads: the per-thread copies
+// cost registers (spills rise from 52 to 140 bytes per thread), which a lattice
+// with few wrapping tiles does not win back.
+template <typename V, bool ASYNC_EDGES>
 __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     k_step_tma(const __grid_constant__ CUtensorMap tin, const float* __restrict__ fin, float* __restrict__ fout,
-               int nx, int ny, VCoef<V> c) {
+               int nx, int ny, VCoef<V> c, int* __restrict__ err) {
   using real = float;
   extern __shared__ __align__(128) unsigned char dyn[];
   float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
@@ -123,71 +221,57 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   __shared__ __align__(8) unsigned long long bar;
   const int tiles_x = (nx + kTileX - 1) / kTileX;
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
-  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
   auto origin = [&](int t, int& x0, int& y0) {
     const int r = t / tiles_x;
     x0 = (t - r * tiles_x) * kTileX;
     y0 = r * kTileY;
   };
-  // Thread 0: the nine copies of tile t's windows, if the tile is interior.
+  // All threads: stage tile t (thread 0 the tensor copies, everyone the per-thread ones).
   auto issue = [&](int t) {
     int x0, y0;
     origin(t, x0, y0);
-    if (t < total && tma_interior(x0, y0, nx, ny)) {
-      mbar_expect_tx(&bar, kTmaBytes);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) tma_load_3d(win + i * kTmaPlane, &tin, x0 - 4, y0 - 1 - kEY[i], i, &bar);
+    const int kind = tile_kind<ASYNC_EDGES>(x0, y0, nx, ny);
+    if (kind == kTensorCopy && threadIdx.x == 0) {
+      fence_proxy_async();
+      issue_windows(win, &tin, x0, y0, &bar);
+    } else if (kind == kAsyncCopy) {
+      issue_window_async(win, fin, nx, ny, nx, x0, y0);
     }
   };
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    issue(blockIdx.x);
-  }
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
+  if (blockIdx.x < total) issue(blockIdx.x);
   unsigned parity = 0;
   int buf = 0;
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     int x0, y0;
     origin(t, x0, y0);
+    const int kind = tile_kind<ASYNC_EDGES>(x0, y0, nx, ny);
     real f[kTileRows][9];
     bool late = false;
-    if (tma_interior(x0, y0, nx, ny)) {
+    if (kind == kTensorCopy) {
       late = !mbar_wait(&bar, parity);
       parity ^= 1u;
-      // Pulled population i of tile node (lx, ly): window row ly + 1, column lx + 4 - e_ix.
-#pragma unroll
-      for (int k = 0; k < kTileRows; ++k) {
-        const int ly = ty + k * kRowStride;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[k][i] = win[i * kTmaPlane + (ly + 1) * kTmaCols + tx + 4 - kEX[i]];
-        rs[buf][ly + 1][tx + 1] = sum9(f[k]);
-      }
-      if (threadIdx.x < TileShape<kTileY>::ring) {
-        int wx, wy;
-        ring_cell(threadIdx.x, wx, wy);
-        real g[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = win[i * kTmaPlane + wy * kTmaCols + wx + 3 - kEX[i]];
-        rs[buf][wy][wx] = sum9(g);
-      }
-    } else {
-      load_tile<real, float, kTileY>(fin, nx, ny, x0, y0, f, rs[buf]);
+    } else if (kind == kAsyncCopy) {
+      cp_async_wait_all();
+      __syncthreads();
     }
+    if (kind == kPlainLoad)
+      load_tile<real, float, kTileY>(fin, nx, ny, nx, x0, y0, f, rs[buf]);
+    else  // read even after a failed wait (in bounds; the block then returns)
+      window_tile(win, f, rs[buf]);
     // The window is consumed and the densities are in place.  A wait that gave up
     // (uniform decision through the barrier) ends the block: it records the
     // failure, waits once more (bounded) for the copies it issued, and returns.
     if (__syncthreads_or(late)) {
       if (threadIdx.x == 0) {
-        atomicExch(&g_wait_error, 1);
+        atomicExch(err, 1);
         mbar_wait(&bar, parity ^ 1u);
       }
       return;
     }
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      issue(t + gridDim.x);
-    }
-    collide_tile<V, float, kTileY>(f, fout, nx, ny, c, lattice_part(c), x0, y0, rs[buf]);
+    if (t + gridDim.x < total) issue(t + gridDim.x);
+    collide_tile<V, float, kTileY>(f, fout, nx, ny, nx, c, lattice_part(c), x0, y0, rs[buf]);
     buf ^= 1;
   }
 }

@@ -91,3 +91,38 @@ def test_batch_lattice_matches_oracle(orc):
     ref = orc.macro(p, orc.step(p, orc.init_feq(p, r), 100))[0]
     assert rel_inf(b.density(1).cpu().numpy(), ref) <= 2e-5
     b.close()
+
+
+@pytest.mark.parametrize("shape,bps", [(0, 0), (0, 2), (1, 1), (2, 0), (3, 1), (3, 3), (4, 1), (4, 2)])
+def test_every_launch_form_equals_single_lattices(shape, bps):
+    """Each launch form by hand (plain loads one block per tile or persistent,
+    tensor copies persistent at both register budgets), with a 512 x 256 lattice
+    added so that persistent blocks walk several tiles (mixed interior and wrapping
+    tiles, lattices with and without a padded row stride), in graph replay and
+    single launches: bit-identical to the single-lattice step; no wait gave up."""
+    from paper_1809_02390_gb300 import Batch, derive
+
+    rhos, kws = _inputs()
+    d = derive(512, 256, Tr=0.8)
+    rhos.append(inputs.spinodal(512, 256, 0.5 * (d["rho_g"] + d["rho_l"]), 0.01, 3))
+    kws.append(dict(Tr=0.8))
+    b = Batch(rhos, [dict(k) for k in kws])
+    b.set_config(shape, bps)
+    assert b.config()["tensor_copies"] == (shape >= 3)
+    b.run(64 + 7)
+    b.status()
+    ref = _singles(rhos, kws, 64 + 7)
+    for i in range(len(rhos)):
+        assert torch.equal(b.state(i), ref[i]), i
+    b.close()
+
+
+def test_set_config_rejects_bad_forms():
+    from paper_1809_02390_gb300 import Batch, capi
+
+    rhos, kws = _inputs()
+    b = Batch(rhos, [dict(k) for k in kws])
+    for shape, bps in [(5, 1), (-1, 0), (3, 0), (0, 1000)]:
+        with pytest.raises(capi.LBError):
+            b.set_config(shape, bps)
+    b.close()
