@@ -275,6 +275,58 @@ def measure_batch(torch, single_mlups: float, steps: int) -> dict:
                                        "first_8": curve[:8]}}
 
 
+def measure_precision(torch, steps: int = 20000) -> dict:
+    """FP64 / FP32 / FP16-storage on 512 x 512 equilibria: flat slabs (liquid band
+    256 thick, two interfaces) at Tr = 0.7, 0.8, 0.9 and droplets of radius 20, 40,
+    80 at Tr = 0.8, all with a tanh start of the pressure-tensor width W1, run for
+    `steps` steps.  Per case: max |rho - rho_FP64| / max rho_FP64 of the reduced
+    precisions, the bulk densities against the Maxwell construction (slabs), and
+    Laplace's dp R against the pressure-tensor sigma (droplets).  FP16 storage runs
+    with stochastic rounding (the default) and with round-to-nearest."""
+    import numpy as np
+
+    from paper_1809_02390_gb300 import Lattice, derive, inputs
+
+    n = 512
+    cases = [("slab", tr, None) for tr in (0.7, 0.8, 0.9)] + [("droplet", 0.8, r) for r in (20, 40, 80)]
+    out = []
+    t0 = time.perf_counter()
+    for shape, tr, radius in cases:
+        d = derive(n, n, Tr=tr)
+        rg, rl = d["rho_g"], d["rho_l"]
+        if shape == "slab":
+            rho0 = inputs.slab(n, n, n / 2, d["W1"], rg, rl)
+        else:
+            rho0 = inputs.droplet(n, n, radius, d["W1"], rg, rl)
+        res = {"shape": shape, "Tr": tr}
+        if radius:
+            res["R0"] = radius
+        rho64 = None
+        for prec in ("fp64", "fp32", "fp16s", "fp16s_nearest"):
+            extra = {"rounding": 1} if prec == "fp16s_nearest" else {}
+            lat = Lattice(rho0, precision=prec.split("_")[0], Tr=tr, **extra)
+            lat.step(steps)
+            rho = lat.moments(velocity=False).double().cpu().numpy()
+            r = lat.reduce()
+            lat.close()
+            entry = {"mass_rel_drift": float(r["mass"] / rho0.sum() - 1.0)}
+            if rho64 is None:
+                rho64 = rho
+            else:
+                entry["rel_err_vs_fp64"] = float(np.abs(rho - rho64).max() / np.abs(rho64).max())
+            if shape == "slab":
+                entry["rho_liquid_rel_err"] = float(rho[n // 2, n // 2] / rl - 1.0)
+                entry["rho_gas_rel_err"] = float(rho[n // 2, 0] / rg - 1.0)
+            else:
+                radius_eq = float(np.sqrt(r["n_liquid"] / np.pi))
+                entry["R"] = round(radius_eq, 3)
+                entry["laplace_dpR_over_sigma"] = (r["p_center"] - r["p_corner"]) * radius_eq / (d["sigma1"] * d["lam"])
+            res[prec] = {k: (round(v, 8) if isinstance(v, float) else v) for k, v in entry.items()}
+        out.append(res)
+        torch.cuda.empty_cache()
+    return {"lattice": [n, n], "steps": steps, "seconds": round(time.perf_counter() - t0, 1), "cases": out}
+
+
 def measure_calibration(torch, iterations: int = 50) -> dict:
     """256 x 256 FP32, perturbed ellipse (axis ratio 1.5, area of an R = 40 disk),
     2,000 steps, checkpoints every 45; target made at (Tr, G2, K_int) = (0.8, G2_ref, 1)."""
@@ -351,8 +403,11 @@ def run_ours(args):
 
     lbuild.build()
     n = args.size
-    if args.only_adjoint or args.only_batch:  # profiling runs of one measurement
-        part = measure_adjoint(n, torch) if args.only_adjoint else measure_batch(torch, None, args.batch_steps)
+    if args.only_adjoint or args.only_batch or args.only_precision:  # runs of one measurement
+        if args.only_precision:
+            part = measure_precision(torch, args.precision_steps)
+        else:
+            part = measure_adjoint(n, torch) if args.only_adjoint else measure_batch(torch, None, args.batch_steps)
         print(json.dumps(part), flush=True)
         return
     rho0, d = workload_rho(n, seed=rank)
@@ -419,6 +474,7 @@ def run_ours(args):
         extras["batch"] = measure_batch(torch, value, args.batch_steps)
         torch.cuda.empty_cache()
         extras["calibration"] = measure_calibration(torch)
+        extras["precision"] = measure_precision(torch, args.precision_steps)
 
     if rank != 0:
         if world > 1:
@@ -457,6 +513,8 @@ def main():
     ap.add_argument("--only-main", action="store_true", help="time the FP32 fused step only (profiling)")
     ap.add_argument("--only-adjoint", action="store_true", help="time the FP32 adjoint at --size only (profiling)")
     ap.add_argument("--only-batch", action="store_true", help="time the 256-lattice batch only (profiling)")
+    ap.add_argument("--only-precision", action="store_true", help="run the FP64/FP32/FP16 study only")
+    ap.add_argument("--precision-steps", type=int, default=20000, help="steps of the precision study")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batch and calibration runs")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the 256-lattice batch run")
     args = ap.parse_args()

@@ -56,6 +56,7 @@ extern "C" {
 enum lb_precision { LB_FP64 = 0, LB_FP32 = 1, LB_FP16S = 2 };
 enum lb_eos_kind { LB_EOS_VDW = 0, LB_EOS_CS = 1 };
 enum lb_variant { LB_AUTO = 0, LB_FUSED = 1, LB_TWO_PASS = 2 };
+enum lb_rounding { LB_ROUND_STOCHASTIC = 0, LB_ROUND_NEAREST = 1 };
 
 /* Problem statement (main text Eqs. 6, 7, 16, 20-22; supplement Sec. V). */
 typedef struct lb_params {
@@ -64,7 +65,12 @@ typedef struct lb_params {
   int32_t eos;       /* enum lb_eos_kind: van der Waals p = rho R T/(1 - b rho) - a rho^2,
                         or Carnahan-Starling (Eq. 20); both times K_EOS */
   int32_t variant;   /* enum lb_variant: fused single-kernel step or density pass + collision */
-  int32_t reserved0;
+  int32_t rounding;  /* enum lb_rounding, FP16S only: rounding of the stored populations.
+                        Stochastic (default): a pseudo-random dither below the half
+                        mantissa, then truncation, so that rounding errors have zero mean
+                        and mass does not drift in stationary states; nearest: IEEE
+                        round-to-nearest-even (biased in a stationary state: the same
+                        errors repeat every step) */
   double eos_a, eos_b, R_gas; /* EOS constants a, b, R (> 0) */
   double Tr;                  /* reduced temperature T/Tc, in (0, 1) for two phases */
   double K_eos, K_int;        /* scaling factors of Eqs. 20-22 (> 0) */

@@ -21,7 +21,7 @@ LB_AUTO, LB_FUSED, LB_TWO_PASS = 0, 1, 2
 
 class lb_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("eos", ctypes.c_int32), ("variant", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("eos", ctypes.c_int32), ("variant", ctypes.c_int32), ("rounding", ctypes.c_int32),
                 ("eos_a", ctypes.c_double), ("eos_b", ctypes.c_double), ("R_gas", ctypes.c_double),
                 ("Tr", ctypes.c_double), ("K_eos", ctypes.c_double), ("K_int", ctypes.c_double),
                 ("G2", ctypes.c_double), ("lam", ctypes.c_double), ("varpi", ctypes.c_double),
@@ -120,8 +120,9 @@ def make_params(nx: int, ny: int, precision: int = LB_FP32, eos: int = LB_EOS_VD
                 eos_a: float = 9.0 / 49.0, eos_b: float = 2.0 / 21.0, R_gas: float = 1.0, Tr: float = 0.85,
                 K_eos: float = 1.0, K_int: float = 1.0, G2: float = 0.0, lam: float = 0.0,
                 varpi: float = 1.0 / 6.0, s_p: float = 1.0, s_q: float = 0.0, s_e: float = 0.0,
-                s_eps: float = 0.0, s_0: float = 0.0, s_j: float = 0.0, rho_ref: float = 0.0) -> lb_params:
-    return lb_params(nx=nx, ny=ny, precision=precision, eos=eos, variant=variant, reserved0=0, eos_a=eos_a,
+                s_eps: float = 0.0, s_0: float = 0.0, s_j: float = 0.0, rho_ref: float = 0.0,
+                rounding: int = 0) -> lb_params:
+    return lb_params(nx=nx, ny=ny, precision=precision, eos=eos, variant=variant, rounding=rounding, eos_a=eos_a,
                      eos_b=eos_b, R_gas=R_gas, Tr=Tr, K_eos=K_eos, K_int=K_int, G2=G2, lam=lam, varpi=varpi,
                      s_p=s_p, s_q=s_q, s_e=s_e, s_eps=s_eps, s_0=s_0, s_j=s_j, rho_ref=rho_ref)
 

@@ -153,21 +153,23 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
   const store_t* fin = static_cast<const store_t*>(h->f[h->cur]);
   store_t* fout = static_cast<store_t*>(h->f[1 - h->cur]);
   const int nx = h->p.nx, ny = h->p.ny;
+  // FP16 stores: a fresh dither sequence every step (seed from the step count).
+  const Rounding rnd{mix32(unsigned(h->steps) * 2654435761u + 12345u), h->p.rounding == LB_ROUND_STOCHASTIC};
   if (h->variant == LB_FUSED) {
     const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
     if constexpr (std::is_same<store_t, float>::value && std::is_same<V, f2>::value) {
       if (h->use_tma) {
-        k_step_tma<V, false><<<h->tma_grid, kFusedThreads, kTmaSmem, h->stream>>>(h->tmap[h->cur], fin, fout, nx, ny, cv,
-                                                                            h->wait_error);
+        k_step_tma<V, false><<<h->tma_grid, kFusedThreads, kTmaSmem, h->stream>>>(h->tmap[h->cur], fin, fout, nx, ny,
+                                                                                 cv, h->wait_error);
         return;
       }
     }
-    k_step_fused<V, store_t><<<grd, kFusedThreads, 0, h->stream>>>(fin, fout, nx, ny, cv);
+    k_step_fused<V, store_t><<<grd, kFusedThreads, 0, h->stream>>>(fin, fout, nx, ny, cv, rnd);
   } else {
     real* rho = static_cast<real*>(h->scratch);
     const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
     k_density<real, store_t><<<grd, blk, 0, h->stream>>>(fin, rho, nx, ny);
-    k_collide_rho<real, store_t><<<grd, blk, 0, h->stream>>>(fin, fout, rho, nx, ny, c);
+    k_collide_rho<real, store_t><<<grd, blk, 0, h->stream>>>(fin, fout, rho, nx, ny, c, rnd);
   }
 }
 

@@ -79,6 +79,57 @@ __device__ __forceinline__ void st_st(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_st(double* p, double v) { *p = v; }
 __device__ __forceinline__ void st_st(__half* p, float v) { *p = __float2half_rn(v); }
 
+// 32-bit integer mixer (xor-shift-multiply rounds; constants of the published
+// "lowbias32" hash).
+__host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// FP32 -> FP16 with stochastic rounding: a dither of 13 bits (the mantissa bits a
+// half drops) is added to the magnitude's bit pattern, then the result is
+// truncated toward zero.  A value between two halves goes up with probability
+// equal to its distance from the lower one, so the rounding error has zero mean
+// (for normal halves; below 2^-14 the dither covers only part of the dropped bits).
+__device__ __forceinline__ void st_st_sr(__half* p, float v, unsigned dither) {
+  *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (dither & 0x1fffu)));
+}
+
+// Rounding of FP16 stores: stochastic with per-step seed, or nearest.
+struct Rounding {
+  unsigned seed;
+  int stochastic;
+};
+
+// Stores the nine populations of node `node` (index within the lattice) at
+// p + i * plane; stochastic rounding draws nine dithers from a linear
+// congruential sequence started at a hash of (node, seed).
+template <typename store_t>
+__device__ __forceinline__ void store9(store_t* p, int plane, const float (&o)[9], unsigned node, Rounding r) {
+  if constexpr (sizeof(store_t) == 2) {
+    if (r.stochastic) {
+      unsigned s = mix32(node * 0x9e3779b9u + r.seed);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        s = s * 1664525u + 1013904223u;
+        st_st_sr(p + i * plane, o[i], s >> 19);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) st_st(p + i * plane, o[i]);
+}
+template <typename store_t>
+__device__ __forceinline__ void store9(store_t* p, int plane, const double (&o)[9], unsigned, Rounding) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) st_st(p + i * plane, o[i]);
+}
+
 // ---------------------------------------------------------------------------
 // Collision constants for value type V (host: make_vcoef).
 template <typename V>

@@ -79,7 +79,8 @@ template <typename V, typename store_t, int TY>
 __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
                                              store_t* __restrict__ fout, int nx, int ny, int sx, const VCoef<V>& c,
                                              const LatCoef<V>& l, int x0, int y0,
-                                             const typename LaneType<V>::type (*rs)[kTileX + 2]) {
+                                             const typename LaneType<V>::type (*rs)[kTileX + 2],
+                                             Rounding rnd = Rounding{0u, 0}) {
   using real = typename LaneType<V>::type;
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
@@ -114,8 +115,7 @@ __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&
     const int gy = y0 + ty + k * Shape::stride;
     if (gx < nx && gy < ny) {
       const int off = gy * sx + gx;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), out[k][i]);
+      store9(fout + off, plane, out[k], unsigned(off), rnd);
     }
   }
 }
@@ -174,21 +174,22 @@ template <typename V, typename store_t, int TY, typename Hook = NoHook>
 __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
                                           int ny, int sx, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
                                           typename LaneType<V>::type (*rs)[kTileX + 2],
-                                          const Hook& before_sync = Hook()) {
+                                          const Hook& before_sync = Hook(), Rounding rnd = Rounding{0u, 0}) {
   using real = typename LaneType<V>::type;
   real f[kTileRows][9];
   load_tile<real, store_t, TY>(fin, nx, ny, sx, x0, y0, f, rs);
   before_sync();
   __syncthreads();
-  collide_tile<V, store_t, TY>(f, fout, nx, ny, sx, c, l, x0, y0, rs);
+  collide_tile<V, store_t, TY>(f, fout, nx, ny, sx, c, l, x0, y0, rs, rnd);
 }
 
 template <typename V, typename store_t>
 __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
-    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c) {
+    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c,
+                 Rounding rnd) {
   __shared__ typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
   step_tile<V, store_t, kTileY>(fin, fout, nx, ny, nx, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
-                                rs);
+                                rs, NoHook(), rnd);
 }
 
 // Two-pass variant, pass 1: density plane rho_dev(x) = sum_i fbar_i(x - e_i).
@@ -204,7 +205,7 @@ __global__ void k_density(const store_t* __restrict__ fin, real* __restrict__ rh
 // Two-pass variant, pass 2: pull, force stencil from the density plane, collide.
 template <typename real, typename store_t>
 __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restrict__ fout,
-                              const real* __restrict__ rho, int nx, int ny, VCoef<real> c) {
+                              const real* __restrict__ rho, int nx, int ny, VCoef<real> c, Rounding rnd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
@@ -221,8 +222,7 @@ __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restri
   real o[9];
   collide(c, f, Sx, Sy, o);
   const int off = y * nx + x;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) st_st(fout + (i * plane + off), o[i]);
+  store9(fout + off, plane, o, unsigned(off), rnd);
 }
 
 // Rest equilibrium from an initial density (computed in FP64, rounded once):

@@ -182,3 +182,51 @@ def test_fp32_tma_path(orc):
     assert rel_inf(rho, ref) <= 2e-5
     capi.lb_status(lat.h)
     assert not capi.lb_uses_tma(lattice(rho0[:, :150], "fp32", Tr=0.85, K_int=1.0).h)  # nx % 4 != 0
+
+
+# (oracle keywords, library keywords): relaxation rates other than s_p = 1 (so
+# s_q, s_e and every R, T, X, Q_m coefficient move), another varpi, and the
+# Carnahan-Starling EOS with the paper's a = 1, b = 4 and K_EOS, K_INT != 1.
+PARAM_SETS = [
+    (dict(Tr=0.85, K_int=1.0, s_p=1.5), dict(Tr=0.85, K_int=1.0, s_p=1.5)),
+    (dict(Tr=0.75, K_int=1.3, s_p=0.8), dict(Tr=0.75, K_int=1.3, s_p=0.8)),
+    (dict(Tr=0.85, K_int=1.0, varpi=0.3, s_p=1.1), dict(Tr=0.85, K_int=1.0, varpi=0.3, s_p=1.1)),
+    (dict(eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.7, K_eos=0.2, K_int=2.0, s_p=1.3),
+     dict(eos="cs", eos_a=1.0, eos_b=4.0, R_gas=1.0, Tr=0.7, K_eos=0.2, K_int=2.0, s_p=1.3)),
+]
+
+
+@pytest.mark.parametrize("okw,lkw", PARAM_SETS, ids=["sp1.5", "sp0.8", "varpi0.3", "cs"])
+def test_fp64_parameters_with_flow(orc, okw, lkw):
+    """FP64 step against the oracle for 100 steps from a state with a random
+    velocity field, away from the default rates, varpi and EOS."""
+    p = oracle_params(**okw)
+    nx, ny = 70, 45
+    rng = np.random.default_rng(7)
+    rho = inputs.droplet(nx, ny, 12, 6, p.rho_g, p.rho_l) * (1 + 0.01 * rng.uniform(-1, 1, (ny, nx)))
+    f0 = orc.init_eq(p, rho, 0.03 * rng.uniform(-1, 1, (ny, nx)), 0.03 * rng.uniform(-1, 1, (ny, nx)))
+    ref = orc.step(p, f0, 100)
+    lat = lattice(rho, "fp64", **lkw)
+    set_state_fp64(lat, f0)
+    lat.step(100)
+    torch.cuda.synchronize()
+    assert rel_inf(gpu_populations(lat), ref) <= 1e-12
+
+
+def test_fp16_stochastic_rounding_keeps_mass():
+    """A stationary flat interface (Tr = 0.9, 256 x 8, 5,000 steps) in FP16 storage:
+    round-to-nearest repeats the same rounding errors every step and the mass
+    drifts by percents; stochastic rounding (the default) makes the errors zero-mean,
+    leaving a random walk of order 2^-11 sqrt(steps / nodes)."""
+    from paper_1809_02390_gb300 import derive
+
+    d = derive(256, 8, Tr=0.9)
+    rho0 = inputs.slab(256, 8, 128, d["W1"], d["rho_g"], d["rho_l"])
+    drift = {}
+    for name, rounding in (("stochastic", 0), ("nearest", 1)):
+        lat = lattice(rho0, "fp16s", Tr=0.9, rounding=rounding)
+        lat.step(5000)
+        drift[name] = abs(lat.reduce()["mass"] / rho0.sum() - 1)
+        lat.close()
+    assert drift["stochastic"] < 3e-3
+    assert drift["nearest"] > 1e-2
