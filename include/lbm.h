@@ -147,6 +147,12 @@ int64_t lb_steps_done(const lb_handle* h);
  * uy may be NULL. */
 int lb_moments(lb_handle* h, void* rho, void* ux, void* uy);
 
+/* Pressure field p_EOS(rho)/c^2 of the current state (the EOS of Eq. 20 or van
+ * der Waals, times K_EOS, in the lattice units of the step: multiply by c^2 of
+ * lb_derived for the paper's units).  p: device array of nx*ny elements ([y][x]),
+ * double for LB_FP64, float otherwise.  Asynchronous on the handle's stream. */
+int lb_pressure(lb_handle* h, void* p);
+
 /* FP64 reductions of the current state, synchronous (waits on the stream):
  * out[0] = total mass, out[1..2] = total momentum sum_x rho u,
  * out[3] = p_EOS/c^2 at the lattice centre (nx/2, ny/2), out[4] = p_EOS/c^2 at

@@ -111,6 +111,13 @@ class Lattice:
                         uy.data_ptr() if velocity else None)
         return (rho, ux, uy) if velocity else rho
 
+    def pressure(self):
+        """p_EOS / c^2 at every node ([ny, nx] tensor of the compute type)."""
+        torch = _torch()
+        p = torch.empty((self.ny, self.nx), dtype=self.real, device=self.f_a.device)
+        capi.lb_pressure(self.h, p.data_ptr())
+        return p
+
     def reduce(self) -> dict:
         v = capi.lb_reduce(self.h)
         keys = ("mass", "mom_x", "mom_y", "p_center", "p_corner", "n_liquid", "rho_min", "rho_max")

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("lb_set_state", ctypes.c_int, [_V, _V]),
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
     ("lb_status", ctypes.c_int, [_V]),
+    ("lb_pressure", ctypes.c_int, [_V, _V]),
     ("lb_uses_tma", ctypes.c_int, [_V]),
     ("lb_set_step_blocks", ctypes.c_int, [_V, ctypes.c_int]),
     ("lb_last_error", ctypes.c_char_p, [_V]),
@@ -288,6 +289,10 @@ def lb_batch_derived(b: int, i: int) -> dict:
 
 def lb_batch_free(b: int) -> None:
     lib().lb_batch_free(b)
+
+
+def lb_pressure(h: int, p: int) -> None:
+    check(lib().lb_pressure(h, p), h)
 
 
 def lb_status(h: int) -> None:

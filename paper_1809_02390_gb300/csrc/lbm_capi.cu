@@ -438,6 +438,25 @@ int lb_moments(lb_handle* h, void* rho, void* ux, void* uy) {
   return LB_OK;
 }
 
+int lb_pressure(lb_handle* h, void* p) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (!p) return fail(h, LB_EINVAL, "null output");
+  const size_t N = size_t(h->p.nx) * h->p.ny;
+  const unsigned blocks = unsigned((N + 255) / 256);
+  const void* f = h->f[h->cur];
+  if (h->p.precision == LB_FP64)
+    k_pressure<double, double><<<blocks, 256, 0, h->stream>>>(static_cast<const double*>(f), static_cast<double*>(p),
+                                                              h->p.nx, h->p.ny, h->cd);
+  else if (h->p.precision == LB_FP32)
+    k_pressure<float, float><<<blocks, 256, 0, h->stream>>>(static_cast<const float*>(f), static_cast<float*>(p),
+                                                            h->p.nx, h->p.ny, h->cf);
+  else
+    k_pressure<float, __half><<<blocks, 256, 0, h->stream>>>(static_cast<const __half*>(f), static_cast<float*>(p),
+                                                             h->p.nx, h->p.ny, h->cf);
+  LB_CUDA(h, cudaGetLastError());
+  return LB_OK;
+}
+
 int lb_reduce(lb_handle* h, double out[8]) {
   if (!h) return fail(nullptr, LB_EINVAL, "null handle");
   if (!out) return fail(h, LB_EINVAL, "null output");

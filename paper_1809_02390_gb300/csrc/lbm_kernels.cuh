@@ -265,6 +265,20 @@ __global__ void k_rho_local(const store_t* __restrict__ f, real* __restrict__ rh
   rho[n] = s + rho_ref;
 }
 
+// p_EOS / c^2 at every node from rho = sum_i fbar_i + rho_ref (Eq. 20 or vdW, times K_EOS).
+template <typename real, typename store_t>
+__global__ void k_pressure(const store_t* __restrict__ f, real* __restrict__ p, int nx, int ny, VCoef<real> c) {
+  const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t N = size_t(nx) * ny;
+  if (n >= N) return;
+  real s = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s += ld_st(f + i * N + n);
+  real pe, dpe;
+  eos(c, s + c.rho_ref, pe, dpe);
+  p[n] = pe;
+}
+
 // rho u = sum_i e_i fbar_i - F/2 with F from the density plane.
 template <typename real, typename store_t>
 __global__ void k_velocity(const store_t* __restrict__ f, const real* __restrict__ rho, real* __restrict__ ux,

@@ -1,0 +1,213 @@
+"""Dynamic validation runs of the time step (through the public Lattice API).
+
+elliptic_oscillation: the paper's dynamic test (main text, after Fig. 2): an
+elliptic droplet with semi-axes 96.0 and 42.7 on a 512 x 512 periodic lattice,
+Carnahan-Starling EOS with a = 1, b = 4, R = 1, Tr = 0.6, surface tension 0.01
+and interface thickness 10.  K_INT and K_EOS follow from the two prescriptions
+through the pressure-tensor constants of a flat interface (Eq. 23): W = W1 K_INT,
+sigma = sigma1 K_EOS K_INT.  The shape mode n = 2 oscillates and decays; its
+period and decay rate are fitted to the half-difference of the droplet's extents
+along x and y through the centre.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def oscillation_params(n: int = 512, Tr: float = 0.6, sigma: float = 0.01, W: float = 10.0, s_p: float = 1.0):
+    """Library keywords of the oscillation case and its derived parameters."""
+    from . import derive
+
+    base = dict(eos="cs", eos_a=1.0, eos_b=4.0, R_gas=1.0, Tr=Tr)
+    d1 = derive(n, n, **base)
+    K_int = W / d1["W1"]
+    K_eos = sigma / (d1["sigma1"] * K_int)
+    kw = dict(base, K_int=K_int, K_eos=K_eos, s_p=s_p)
+    return kw, derive(n, n, **kw)
+
+
+def _extent(v: np.ndarray, level: float) -> float:
+    """Length of the run of v above `level` (the droplet's chord), with linear
+    interpolation of both crossings."""
+    idx = np.nonzero(v > level)[0]
+    i, j = idx[0], idx[-1]
+    left = i - (v[i] - level) / (v[i] - v[i - 1])
+    right = j + (v[j] - level) / (v[j] - v[j + 1])
+    return right - left
+
+
+def elliptic_oscillation(precision: str = "fp32", steps: int = 60000, every: int = 50, semi=(96.0, 42.7),
+                         n: int = 512, s_p: float = 1.0, fit_from: int = 8000) -> dict:
+    """Runs the oscillation and fits A exp(-g t) cos(w t + phi) + c to the shape
+    signal from step `fit_from` on (after the first, strongly nonlinear swing).
+    Returns the damped period 2 pi / w, the decay rate g, the undamped period
+    2 pi / sqrt(w^2 + g^2), and the inviscid two-dimensional n = 2 period of a
+    droplet of the same area, 2 pi sqrt((rho_l + rho_g) R^3 / (6 sigma')), with
+    sigma' = sigma / c^2 the surface tension in the lattice units of the run."""
+    from scipy.optimize import curve_fit
+
+    from . import Lattice, inputs
+
+    kw, d = oscillation_params(n=n, s_p=s_p)
+    rg, rl = d["rho_g"], d["rho_l"]
+    rho0 = inputs.ellipse(n, n, semi[0], semi[1], 10.0, rg, rl)
+    lat = Lattice(rho0, precision=precision, **kw)
+    level = 0.5 * (rg + rl)
+    ts, sig = [], []
+    finite = True
+    for k in range(steps // every + 1):
+        if k:
+            lat.step(every)
+        rho = lat.moments(velocity=False)
+        row = rho[n // 2].double().cpu().numpy()
+        col = rho[:, n // 2].double().cpu().numpy()
+        if not (np.isfinite(row).all() and np.isfinite(col).all()):
+            finite = False
+            break
+        ts.append(k * every)
+        sig.append(0.5 * (_extent(row, level) - _extent(col, level)))
+    mass_drift = lat.reduce()["mass"] / rho0.sum() - 1.0
+    lat.close()
+    R = math.sqrt(semi[0] * semi[1])
+    sigma_lat = 0.01 / d["c2"]
+    out = {"precision": precision, "steps": steps, "s_p": s_p, "finite": finite, "R": R,
+           "T_rayleigh": 2 * math.pi * math.sqrt((rl + rg) * R ** 3 / (6 * sigma_lat)),
+           "mass_rel_drift": float(mass_drift)}
+    if not finite:
+        return out
+    t, s = np.array(ts, dtype=float), np.array(sig)
+    m = t >= fit_from
+    # Initial guess: the period of the Rayleigh mode, decay over about one period.
+    w0 = 2 * math.pi / out["T_rayleigh"]
+    p0 = [abs(s[m]).max(), 0.5 * w0 / math.pi, w0, 0.0, 0.0]
+    (A, g, w, ph, c), _ = curve_fit(lambda tt, A, g, w, ph, c: A * np.exp(-g * tt) * np.cos(w * tt + ph) + c,
+                                    t[m], s[m], p0=p0, maxfev=20000)
+    w, g = abs(w), float(g)
+    out.update({"T_damped": 2 * math.pi / w, "decay_rate": g, "T_undamped": 2 * math.pi / math.sqrt(w * w + g * g),
+                "shape_signal_start": float(s[0]), "first_extremum": float(s[m][0])})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Interface thickness and surface tension against K_INT and K_EOS (supplement
+# Sec. V, Figs. 1, 3, 4): CS EOS, a = 1, b = 4, R = 1, varpi = 1/6.
+
+CS = dict(eos="cs", eos_a=1.0, eos_b=4.0, R_gas=1.0)
+
+# The 5%-95% thickness of rho = mid - (rho_l - rho_g)/2 tanh(2 d / w) is
+# w atanh(0.9): tanh starts take w = W / TANH_5_95 to begin at the target thickness.
+TANH_5_95 = math.atanh(0.9)
+
+
+def interface_thickness(profile: np.ndarray, rho_g: float, rho_l: float) -> float:
+    """Mean 5%-95% thickness (linear interpolation of the crossings of
+    0.95 rho_g + 0.05 rho_l and 0.05 rho_g + 0.95 rho_l, with the coexistence
+    densities of the EOS) of the two interfaces of a periodic slab profile with the
+    liquid in the middle; NaN if a level is not crossed."""
+    n = len(profile)
+    lo, hi = 0.95 * rho_g + 0.05 * rho_l, 0.05 * rho_g + 0.95 * rho_l
+    half = profile[: n // 2], profile[n // 2:][::-1]  # both interfaces rise towards the centre
+
+    def cross(p, level):
+        idx = np.nonzero((p[:-1] < level) & (p[1:] >= level))[0]
+        if len(idx) == 0:
+            return float("nan")
+        i = idx[-1]
+        return i + (level - p[i]) / (p[i + 1] - p[i])
+
+    return float(np.mean([cross(p, hi) - cross(p, lo) for p in half]))
+
+
+def flat_interface_W(Tr: float, K_int: float, n: int = 1024, steps: int = 40000, precision: str = "fp32") -> dict:
+    """Flat interfaces on an n x 4 periodic lattice (liquid slab n/2 thick, started
+    from a tanh of the predicted width): measured thickness after `steps` steps."""
+    from . import Lattice, derive, inputs
+
+    kw = dict(CS, Tr=Tr, K_int=K_int)
+    d = derive(n, 4, **kw)
+    rho0 = inputs.slab(n, 4, n / 2, d["W1"] * K_int / TANH_5_95, d["rho_g"], d["rho_l"])
+    lat = Lattice(rho0, precision=precision, **kw)
+    lat.step(steps)
+    prof = lat.moments(velocity=False)[0].double().cpu().numpy()
+    lat.close()
+    finite = bool(np.isfinite(prof).all())
+    return {"Tr": Tr, "K_int": K_int,
+            "W": interface_thickness(prof, d["rho_g"], d["rho_l"]) if finite else float("nan"),
+            "W_predicted": d["W1"] * K_int, "rho_g": float(prof[0]), "rho_l": float(prof[n // 2]),
+            "finite": finite}
+
+
+def droplet_sigma(Tr: float, K_int: float, K_eos: float = 1.0, n: int = 1024, radius: float = 256.0,
+                  steps: int = 20000, avg_steps: int = 20000, every: int = 25, precision: str = "fp32") -> dict:
+    """Circular droplet on an n x n periodic lattice: surface tension from Laplace's
+    law, sigma = (p_in - p_out) D / 2 in the paper's pressure units (p_EOS with
+    K_EOS; the lattice runs with p / c^2), D from the area inside the mid density.
+    p_in and p_out are means of p_EOS over the inner disk (r < R / 2) and over the
+    nodes farther than R + 2 W from the centre; after `steps` steps of relaxation
+    the difference is averaged over `avg_steps` more (sampled every `every`), which
+    removes the standing pressure waves of the periodic box (their damping time,
+    about L^2 / (nu (2 pi)^2), far exceeds any affordable run)."""
+    import torch
+
+    from . import Lattice, derive, inputs
+
+    kw = dict(CS, Tr=Tr, K_int=K_int, K_eos=K_eos)
+    d = derive(n, n, **kw)
+    W = d["W1"] * K_int
+    rho0 = inputs.droplet(n, n, radius, W / TANH_5_95, d["rho_g"], d["rho_l"])
+    lat = Lattice(rho0, precision=precision, **kw)
+    lat.step(steps)
+    R = math.sqrt(lat.reduce()["n_liquid"] / math.pi)
+    dev = lat.f_a.device
+    y, x = torch.meshgrid(torch.arange(n, device=dev, dtype=torch.float64),
+                          torch.arange(n, device=dev, dtype=torch.float64), indexing="ij")
+    dist = torch.hypot(x - n / 2.0, y - n / 2.0)
+    inner, outer = dist < 0.5 * R, dist > R + 2 * W
+    samples = []
+    for _ in range(avg_steps // every):
+        lat.step(every)
+        p = lat.pressure().double()
+        samples.append(p[inner].mean() - p[outer].mean())
+    dp = torch.stack(samples).cpu().numpy()
+    R_end = math.sqrt(lat.reduce()["n_liquid"] / math.pi)
+    lat.close()
+    Rm = 0.5 * (R + R_end)
+    return {"Tr": Tr, "K_int": K_int, "K_eos": K_eos, "R": Rm, "sigma": float(dp.mean() * d["c2"] * Rm),
+            "sigma_spread": float(dp.std() * d["c2"] * Rm), "sigma_predicted": d["sigma1"] * K_eos * K_int,
+            "finite": bool(np.isfinite(dp).all())}
+
+
+def slope(xs, ys) -> tuple[float, float]:
+    """Least-squares line y = s x + b."""
+    s, b = np.polyfit(np.asarray(xs, float), np.asarray(ys, float), 1)
+    return float(s), float(b)
+
+
+# K_INT ranges of the sweeps: thin interfaces at low Tr are unstable (the paper
+# notes the same for Tr = 0.5), so their ranges start higher.
+W_SWEEP = {0.9: (1, 2, 3, 4), 0.8: (1, 2, 3, 4), 0.7: (2, 3, 4, 5), 0.6: (2, 3, 4, 5), 0.5: (3, 4, 5, 6)}
+SIGMA_SWEEP = {0.9: (1, 2, 3, 4), 0.8: (1, 2, 3, 4), 0.7: (2, 3, 4, 5)}
+
+
+def thickness_slopes(trs=tuple(W_SWEEP), steps: int = 40000) -> dict:
+    """W against K_INT per Tr (supplement Fig. 1): fitted slope and intercept."""
+    out = {}
+    for Tr in trs:
+        runs = [flat_interface_W(Tr, k, steps=steps) for k in W_SWEEP[Tr]]
+        s, b = slope(W_SWEEP[Tr], [r["W"] for r in runs])
+        out[Tr] = {"slope": s, "intercept": b, "W": [r["W"] for r in runs], "K_int": list(W_SWEEP[Tr])}
+    return out
+
+
+def sigma_slopes(trs=tuple(SIGMA_SWEEP), n: int = 512, radius: float = 128.0, steps: int = 100000,
+                 avg_steps: int = 20000) -> dict:
+    """sigma against K_INT per Tr (supplement Fig. 3) from droplets of radius n/4:
+    fitted slope and intercept."""
+    out = {}
+    for Tr in trs:
+        runs = [droplet_sigma(Tr, k, n=n, radius=radius, steps=steps, avg_steps=avg_steps) for k in SIGMA_SWEEP[Tr]]
+        s, b = slope(SIGMA_SWEEP[Tr], [r["sigma"] for r in runs])
+        out[Tr] = {"slope": s, "intercept": b, "sigma": [r["sigma"] for r in runs], "K_int": list(SIGMA_SWEEP[Tr])}
+    return out
