@@ -27,11 +27,26 @@ __device__ __forceinline__ f2 operator+(f2 a, f2 b) { return {__fadd2_rn(a.v, b.
 __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return {__fmul2_rn(a.v, b.v)}; }
 __device__ __forceinline__ f2 fmav(f2 a, f2 b, f2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
 __device__ __forceinline__ f2 operator-(f2 a, f2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
-__device__ __forceinline__ f2 rcp(f2 x) { return {make_float2(__frcp_rn(x.v.x), __frcp_rn(x.v.y))}; }
+// FP32 reciprocal: the hardware approximation (rcp.approx.ftz, within 1 ulp) when
+// LBM_FAST_RCP is set, else the correctly rounded __frcp_rn.  The densities and
+// 1 - b rho it inverts are normal numbers far from the flush-to-zero range.
+#ifndef LBM_FAST_RCP
+#define LBM_FAST_RCP 1
+#endif
+__device__ __forceinline__ float rcp32(float x) {
+#if LBM_FAST_RCP
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return __frcp_rn(x);
+#endif
+}
+__device__ __forceinline__ f2 rcp(f2 x) { return {make_float2(rcp32(x.v.x), rcp32(x.v.y))}; }
 
 __device__ __forceinline__ float fmav(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmav(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp(float x) { return rcp32(x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // Lanes of a value (1 for scalars, 2 for f2).
