@@ -513,6 +513,7 @@ def run_ours(args):
     extras = {}
     if world == 1 and not args.no_extras:
         extras["adjoint"] = measure_adjoint(n, torch)
+        extras["adjoint_256"] = measure_adjoint(256, torch)  # the calibration lattice
         torch.cuda.empty_cache()
         extras["batch"] = measure_batch(torch, value, args.batch_steps)
         torch.cuda.empty_cache()

@@ -15,6 +15,7 @@
 
 #include "lbm_adjoint.cuh"
 #include "lbm_handle.cuh"
+#include "lbm_tma.cuh"
 
 namespace {
 
@@ -195,7 +196,11 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
   __shared__ real rb[kTileY + 2][kTileX + 2];   // rhob' on tile + ring
   __shared__ real sbx[kTileY + 4][kTileX + 4];  // Sb' on tile + two-node ring
   __shared__ real sby[kTileY + 4][kTileX + 4];
-  __shared__ double red[kAdjThreads / 32][3];
+  // mu'_i(x + e_i) at the tile's nodes, staged for FP32 (in FP64 the 37 KB would
+  // exceed the static shared-memory limit next to the rest; FP64 reads directly).
+  constexpr bool kStageMu = sizeof(real) == 4;
+  __shared__ real mus[kStageMu ? 9 : 1][kTileY][kTileX];
+  __shared__ real red[kAdjThreads / 32][3];
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   const int plane = nx * ny;
@@ -206,17 +211,38 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
   const int gx = x0 + tx;
   const int xc = wr(gx, nx);
   const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
+  // The cotangent reads go first, as asynchronous copies into shared memory, so
+  // that they travel while the state is pulled: mu'_i at x + e_i for the thread's
+  // nodes (wrapped coordinates also past a ragged edge: in bounds, unused), and Sb'
+  // on the tile with its two-node ring.
+#pragma unroll
+  for (int k = 0; k < (kStageMu ? kTileRows : 0); ++k) {
+    const int ly = ty + k * kRowStride;
+    const int yc = wr(y0 + ly, ny);
+    const int ym = yc == 0 ? ny - 1 : yc - 1, yp = yc == ny - 1 ? 0 : yc + 1;
+    const int oc = yc * nx, om = ym * nx, op = yp * nx;
+    cp_async_elem(&mus[0][ly][tx], mu_in + (oc + xc));
+    cp_async_elem(&mus[1][ly][tx], mu_in + (plane + oc + xp));
+    cp_async_elem(&mus[2][ly][tx], mu_in + (2 * plane + op + xc));
+    cp_async_elem(&mus[3][ly][tx], mu_in + (3 * plane + oc + xm));
+    cp_async_elem(&mus[4][ly][tx], mu_in + (4 * plane + om + xc));
+    cp_async_elem(&mus[5][ly][tx], mu_in + (5 * plane + op + xp));
+    cp_async_elem(&mus[6][ly][tx], mu_in + (6 * plane + op + xm));
+    cp_async_elem(&mus[7][ly][tx], mu_in + (7 * plane + om + xm));
+    cp_async_elem(&mus[8][ly][tx], mu_in + (8 * plane + om + xp));
+  }
+  for (int t = threadIdx.x; t < (kTileY + 4) * (kTileX + 4); t += kAdjThreads) {
+    const int wy = t / (kTileX + 4), wx = t - wy * (kTileX + 4);
+    const int o = wr(y0 - 2 + wy, ny) * nx + wr(x0 - 2 + wx, nx);
+    cp_async_elem(&sbx[wy][wx], sb_in + o);
+    cp_async_elem(&sby[wy][wx], sb_in + (plane + o));
+  }
+  cp_async_commit();
   real f[kTileRows][9];
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
     const int gy = y0 + ty + k * kRowStride;
     pull_row(s, plane, nx, ny, wr(gy, ny), xm, xc, xp, f[k]);
-  }
-  for (int t = threadIdx.x; t < (kTileY + 4) * (kTileX + 4); t += kAdjThreads) {
-    const int wy = t / (kTileX + 4), wx = t - wy * (kTileX + 4);
-    const int o = wr(y0 - 2 + wy, ny) * nx + wr(x0 - 2 + wx, nx);
-    sbx[wy][wx] = sb_in[o];
-    sby[wy][wx] = sb_in[plane + o];
   }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
@@ -236,6 +262,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     pull_row(s, plane, nx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
     rs[wy][wx] = sum9(g);
   }
+  cp_async_wait_all();
   __syncthreads();
   // rhob'(y) = sum_j omega_j e_j . Sb'(y - e_j) on tile + ring (smem index of y is (wy + 1, wx + 1)).
   const real third = real(1.0 / 3.0), twelfth = real(1.0 / 12.0);
@@ -262,19 +289,35 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     real Sx, Sy;
     stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
             rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx, Sy);
-    const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
-    const int oc = gy * nx, om = ym * nx, op = yp * nx, off = oc + gx;
+    const int off = gy * nx + gx;
     // lam_i(x) = mu'_i(x + e_i) + rhob'(x + e_i).
+    real mu9[9];
+    if constexpr (kStageMu) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) mu9[i] = mus[i][ly - 1][tx];
+    } else {
+      const int ym = gy == 0 ? ny - 1 : gy - 1, yp = gy == ny - 1 ? 0 : gy + 1;
+      const int oc = gy * nx, om = ym * nx, op = yp * nx;
+      mu9[0] = mu_in[off];
+      mu9[1] = mu_in[plane + oc + xp];
+      mu9[2] = mu_in[2 * plane + op + gx];
+      mu9[3] = mu_in[3 * plane + oc + xm];
+      mu9[4] = mu_in[4 * plane + om + gx];
+      mu9[5] = mu_in[5 * plane + op + xp];
+      mu9[6] = mu_in[6 * plane + op + xm];
+      mu9[7] = mu_in[7 * plane + om + xm];
+      mu9[8] = mu_in[8 * plane + om + xp];
+    }
     real ob[9];
-    ob[0] = mu_in[off] + rb[ly][lx];
-    ob[1] = mu_in[plane + oc + xp] + rb[ly][lx + 1];
-    ob[2] = mu_in[2 * plane + op + gx] + rb[ly + 1][lx];
-    ob[3] = mu_in[3 * plane + oc + xm] + rb[ly][lx - 1];
-    ob[4] = mu_in[4 * plane + om + gx] + rb[ly - 1][lx];
-    ob[5] = mu_in[5 * plane + op + xp] + rb[ly + 1][lx + 1];
-    ob[6] = mu_in[6 * plane + op + xm] + rb[ly + 1][lx - 1];
-    ob[7] = mu_in[7 * plane + om + xm] + rb[ly - 1][lx - 1];
-    ob[8] = mu_in[8 * plane + om + xp] + rb[ly - 1][lx + 1];
+    ob[0] = mu9[0] + rb[ly][lx];
+    ob[1] = mu9[1] + rb[ly][lx + 1];
+    ob[2] = mu9[2] + rb[ly + 1][lx];
+    ob[3] = mu9[3] + rb[ly][lx - 1];
+    ob[4] = mu9[4] + rb[ly - 1][lx];
+    ob[5] = mu9[5] + rb[ly + 1][lx + 1];
+    ob[6] = mu9[6] + rb[ly + 1][lx - 1];
+    ob[7] = mu9[7] + rb[ly - 1][lx - 1];
+    ob[8] = mu9[8] + rb[ly - 1][lx + 1];
     AdjOut<real> r;
     collide_vjp(c, f[k], Sx, Sy, ob, r);
 #pragma unroll
@@ -291,15 +334,17 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     real v = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[w][k] = double(v);
+    if (lane == 0) red[w][k] = v;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
-    double v = 0.0;
+    // The block's partial in the compute type, widened once: one FP64 add per
+    // block and parameter per step.
+    real v = real(0);
     for (int j = 0; j < kAdjThreads / 32; ++j) v += red[j][threadIdx.x];
     // Each block owns its slot; successive steps on one stream accumulate in order.
     double* slot = partial + (size_t(blockIdx.y) * gridDim.x + blockIdx.x) * 3 + threadIdx.x;
-    *slot = accumulate ? *slot + v : v;
+    *slot = accumulate ? *slot + double(v) : double(v);
   }
 }
 

@@ -127,6 +127,11 @@ static_assert(kTmaRows % 6 == 0 && kAsyncThreads <= kFusedThreads, "window rows 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+// One element (4 or 8 bytes, naturally aligned) by cp.async.
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src) { cp_async4(dst, src); }
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
