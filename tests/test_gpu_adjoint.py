@@ -151,13 +151,16 @@ def test_rollout_gradient_vs_oracle_complex_step(orc):
     assert np.allclose(g, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("nx,ny", [(45, 38), (33, 17), (130, 70)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_fused_segment_equals_single_steps(orc, precision, tol):
-    """lb_adjoint_steps (fused, one kernel per step) against k calls of lb_adjoint_step."""
+def test_fused_segment_equals_single_steps(orc, precision, tol, nx, ny):
+    """lb_adjoint_steps (fused, one kernel per step) against k calls of lb_adjoint_step,
+    on lattices where the FP32 fused step stages the state window by asynchronous
+    copies (at least 40 x 18, several tiles) and where it pulls directly (33 x 17)."""
     from paper_1809_02390_gb300 import capi
 
     p = oracle_params(Tr=0.85, K_int=1.0)
-    nx, ny, k = 45, 38, 5
+    k = 5
     f0 = _flow_state(orc, p, nx, ny, 3)
     lat = lattice(np.full((ny, nx), 2.0), precision, Tr=0.85, G2=p.G2, lam=p.lam, rho_ref=0.0)
     real = torch.float64 if precision == "fp64" else torch.float32
