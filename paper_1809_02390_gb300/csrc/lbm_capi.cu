@@ -86,6 +86,8 @@ VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d) {
   c.h15 = bc<V>(1.5);
   c.eight = bc<V>(8.0);
   c.twenty = bc<V>(20.0);
+  c.third = bc<V>(1.0 / 3.0);
+  c.twelfth = bc<V>(1.0 / 12.0);
   c.one = bc<V>(1.0);
   c.mone = bc<V>(-1.0);
   c.two = bc<V>(2.0);

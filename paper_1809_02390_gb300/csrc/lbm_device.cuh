@@ -158,6 +158,8 @@ struct VCoef {
       quarter;
   // used by the adjoint only: -a, 1.5, 8, 20 and the S Q_m factors without G^2
   V neg_a, h15, eight, twenty, Q1, Q2, Q78;
+  // stencil weights omega = 1/3 (axes), 1/12 (diagonals) of Eq. 12
+  V third, twelfth;
 };
 
 // The coefficients that depend on the lattice's temperature, pressure scale,

@@ -86,21 +86,23 @@ __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
   const int plane = sx * ny;
   const int gx = x0 + tx;
-  real Sx[kTileRows], Sy[kTileRows];
-#pragma unroll
-  for (int k = 0; k < kTileRows; ++k) {
-    const int ly = ty + k * Shape::stride + 1, lx = tx + 1;
-    stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
-            rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx[k], Sy[k]);
-  }
   real out[kTileRows][9];
   if constexpr (Lanes<V>::n == 2) {
-    V d[9], o[9], sx, sy;
+    // Both nodes' stencils as one packed evaluation: lane k reads row ty + k stride.
+    const int lx = tx + 1, l0 = ty + 1, l1 = ty + Shape::stride + 1;
+    auto pair = [&](int dy, int dx) {
+      V v;
+      v.v = make_float2(rs[l0 + dy][lx + dx], rs[l1 + dy][lx + dx]);
+      return v;
+    };
+    const V ml = pair(-1, -1), mc = pair(-1, 0), mr = pair(-1, 1), cl = pair(0, -1), cr = pair(0, 1);
+    const V pl = pair(1, -1), pc = pair(1, 0), pr = pair(1, 1);
+    const V Sxp = fmav(c.third, cr - cl, c.twelfth * ((pr - pl) + (mr - ml)));
+    const V Syp = fmav(c.third, pc - mc, c.twelfth * ((pr + pl) - (mr + ml)));
+    V d[9], o[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i].v = make_float2(f[0][i], f[1][i]);
-    sx.v = make_float2(Sx[0], Sx[1]);
-    sy.v = make_float2(Sy[0], Sy[1]);
-    collide(c, l, d, sx, sy, o);
+    collide(c, l, d, Sxp, Syp, o);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       out[0][i] = o[i].v.x;
@@ -108,7 +110,13 @@ __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < kTileRows; ++k) collide(c, l, f[k], Sx[k], Sy[k], out[k]);
+    for (int k = 0; k < kTileRows; ++k) {
+      const int ly = ty + k * Shape::stride + 1, lx = tx + 1;
+      real Sx, Sy;
+      stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
+              rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx, Sy);
+      collide(c, l, f[k], Sx, Sy, out[k]);
+    }
   }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {

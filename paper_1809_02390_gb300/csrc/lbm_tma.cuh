@@ -170,8 +170,15 @@ __device__ __forceinline__ void window_tile(const float* __restrict__ win, float
     const int ly = ty + k * kRowStride;
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[k][i] = win[i * kTmaPlane + (ly + 1) * kTmaCols + tx + 4 - ex_of(i)];
-    rs[ly + 1][tx + 1] = sum9(f[k]);
   }
+  // Both densities as one packed sum (lane k = node k; the same additions in the
+  // same order as the scalar sum).
+  f2 d[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) d[i].v = make_float2(f[0][i], f[1][i]);
+  const f2 rho = sum9(d);
+  rs[ty + 1][tx + 1] = rho.v.x;
+  rs[ty + kRowStride + 1][tx + 1] = rho.v.y;
   if (threadIdx.x < TileShape<kTileY>::ring) {
     int wx, wy;
     ring_cell(threadIdx.x, wx, wy);
@@ -226,15 +233,21 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   __shared__ __align__(8) unsigned long long bar;
   const int tiles_x = (nx + kTileX - 1) / kTileX;
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
-  auto origin = [&](int t, int& x0, int& y0) {
-    const int r = t / tiles_x;
-    x0 = (t - r * tiles_x) * kTileX;
-    y0 = r * kTileY;
+  // Tile t sits at column t mod tiles_x, row t / tiles_x; the walk t -> t + G
+  // advances the origin by a fixed step (two divisions per block, none per tile).
+  const int step_r = gridDim.x / tiles_x, step_c = gridDim.x - step_r * tiles_x;
+  auto advance = [&](int& c0, int& r0) {
+    c0 += step_c;
+    r0 += step_r;
+    if (c0 >= tiles_x) {
+      c0 -= tiles_x;
+      ++r0;
+    }
   };
-  // All threads: stage tile t (thread 0 the tensor copies, everyone the per-thread ones).
-  auto issue = [&](int t) {
-    int x0, y0;
-    origin(t, x0, y0);
+  // All threads: stage the tile at tile column c0, row r0 (thread 0 the tensor
+  // copies, everyone the per-thread ones).
+  auto issue = [&](int c0, int r0) {
+    const int x0 = c0 * kTileX, y0 = r0 * kTileY;
     const int kind = tile_kind<ASYNC_EDGES>(x0, y0, nx, ny);
     if (kind == kTensorCopy && threadIdx.x == 0) {
       fence_proxy_async();
@@ -245,12 +258,12 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   };
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (blockIdx.x < total) issue(blockIdx.x);
+  int tr = blockIdx.x / tiles_x, tc = blockIdx.x - tr * tiles_x;  // current tile
+  if (blockIdx.x < total) issue(tc, tr);
   unsigned parity = 0;
   int buf = 0;
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
-    int x0, y0;
-    origin(t, x0, y0);
+    const int x0 = tc * kTileX, y0 = tr * kTileY;
     const int kind = tile_kind<ASYNC_EDGES>(x0, y0, nx, ny);
     real f[kTileRows][9];
     bool late = false;
@@ -275,7 +288,8 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       }
       return;
     }
-    if (t + gridDim.x < total) issue(t + gridDim.x);
+    advance(tc, tr);
+    if (t + gridDim.x < total) issue(tc, tr);
     collide_tile<V, float, kTileY>(f, fout, nx, ny, nx, c, lattice_part(c), x0, y0, rs[buf]);
     buf ^= 1;
   }
