@@ -273,8 +273,9 @@ int lb_set_state(lb_handle* h, const void* src);
  * else LB_OK.  Kernels never spin without a limit. */
 int lb_status(lb_handle* h);
 
-/* 1 if the handle's FP32 fused step stages populations with tensor copies (TMA):
- * FP32 storage, nx a multiple of 4, nx >= 104, ny >= 50; else 0. */
+/* 1 if the handle's fused step stages populations with tensor copies (TMA):
+ * FP32 storage with nx a multiple of 4 and nx >= 104, or FP16 storage with nx a
+ * multiple of 8 and nx >= 112; ny >= 50.  Else 0. */
 int lb_uses_tma(const lb_handle* h);
 
 /* Grid of that persistent kernel (each block steps tiles b, b + blocks, ...):

@@ -159,10 +159,10 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
   const Rounding rnd{mix32(unsigned(h->steps) * 2654435761u + 12345u), h->p.rounding == LB_ROUND_STOCHASTIC};
   if (h->variant == LB_FUSED) {
     const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
-    if constexpr (std::is_same<store_t, float>::value && std::is_same<V, f2>::value) {
+    if constexpr (sizeof(store_t) <= 4 && std::is_same<V, f2>::value) {
       if (h->use_tma) {
-        k_step_tma<V, false><<<h->tma_grid, kFusedThreads, kTmaSmem, h->stream>>>(h->tmap[h->cur], fin, fout, nx, ny,
-                                                                                 cv, h->wait_error);
+        k_step_tma<V, store_t, false><<<h->tma_grid, kFusedThreads, Win<store_t>::smem, h->stream>>>(
+            h->tmap[h->cur], fin, fout, nx, ny, cv, h->wait_error, rnd);
         return;
       }
     }
@@ -192,10 +192,11 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 namespace lbm {
 
-// 3-D map of one FP32 population buffer: x (nx), y (ny, row stride sx), plane
-// (9); box of one plane window (kTmaCols x kTmaRows).  False if the layout does
-// not allow it (base not 16-byte aligned, row stride not a multiple of 16 bytes).
-bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx) {
+// 3-D map of one FP32 (elem_bytes 4) or FP16 (2) population buffer: x (nx), y (ny,
+// row stride sx), plane (9); box of one plane window (40 x 18 floats or 48 x 18
+// halves).  False if the layout does not allow it (base not 16-byte aligned, row
+// stride not a multiple of 16 bytes).
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -205,12 +206,17 @@ bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx)
       return false;
     fn = reinterpret_cast<EncodeTiledFn>(p);
   }
-  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(sx) * 4) % 16 != 0 || sx < nx) return false;
+  if (elem_bytes != 4 && elem_bytes != 2) return false;
+  const size_t eb = size_t(elem_bytes);
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(sx) * eb) % 16 != 0 || sx < nx) return false;
+  const int cols = elem_bytes == 4 ? Win<float>::cols : Win<__half>::cols;
+  if (nx < cols || ny < kTmaRows) return false;
   const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), 9};
-  const cuuint64_t strides[2] = {cuuint64_t(sx) * 4, cuuint64_t(sx) * ny * 4};
-  const cuuint32_t box[3] = {cuuint32_t(kTmaCols), cuuint32_t(kTmaRows), 1};
+  const cuuint64_t strides[2] = {cuuint64_t(sx) * eb, cuuint64_t(sx) * ny * eb};
+  const cuuint32_t box[3] = {cuuint32_t(cols), cuuint32_t(kTmaRows), 1};
   const cuuint32_t estride[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return fn(map, dt, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -225,20 +231,26 @@ __device__ int g_wait_error;
 int configure(lb_handle* h) {
   const int rc = configure_device(h);
   if (rc != LB_OK) return rc;
-  // The tensor-copy path needs FP32 storage, rows of a multiple of 16 bytes and a
-  // lattice holding at least one interior tile; otherwise the plain fused kernel runs.
-  h->use_tma = h->p.precision == LB_FP32 && h->variant == LB_FUSED && h->p.nx % 4 == 0 &&
-               h->p.nx >= 2 * kTileX + kTmaCols && h->p.ny >= 2 * kTileY + kTmaRows &&
-               encode_population_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny, h->p.nx) &&
-               encode_population_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny, h->p.nx);
+  // The tensor-copy path needs FP32 or FP16 storage, rows of a multiple of 16
+  // bytes and a lattice holding at least one interior tile; otherwise the plain
+  // fused kernel runs.
+  const bool fp32 = h->p.precision == LB_FP32, fp16 = h->p.precision == LB_FP16S;
+  const int eb = fp32 ? 4 : 2, cols = fp32 ? Win<float>::cols : Win<__half>::cols;
+  h->use_tma = (fp32 || fp16) && h->variant == LB_FUSED && (h->p.nx * eb) % 16 == 0 &&
+               h->p.nx >= 2 * kTileX + cols && h->p.ny >= 2 * kTileY + kTmaRows &&
+               encode_population_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny, h->p.nx, eb) &&
+               encode_population_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny, h->p.nx, eb);
   if (h->use_tma) {
     void* w = nullptr;
     LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_error));
     h->wait_error = static_cast<int*>(w);
     // Persistent grid: as many blocks as can be resident.
-    LB_CUDA(h, cudaFuncSetAttribute(k_step_tma<f2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmem)));
+    const void* k = fp32 ? reinterpret_cast<const void*>(k_step_tma<f2, float, false>)
+                         : reinterpret_cast<const void*>(k_step_tma<f2, __half, false>);
+    const int smem = int(fp32 ? Win<float>::smem : Win<__half>::smem);
+    LB_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0, dev = 0, sms = 0;
-    LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_tma<f2, false>, kFusedThreads, kTmaSmem));
+    LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFusedThreads, smem));
     LB_CUDA(h, cudaGetDevice(&dev));
     LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int tiles = ((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY);

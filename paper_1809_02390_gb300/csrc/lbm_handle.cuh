@@ -29,8 +29,8 @@ struct lb_handle {
 };
 
 namespace lbm {
-// 3-D tensor map (x, y, plane) of an FP32 population buffer with row stride sx,
-// box = one plane window of the tensor-copy step; false if the layout does not
-// allow one (lbm_capi.cu).
-bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx);
+// 3-D tensor map (x, y, plane) of an FP32 (elem_bytes 4) or FP16 (2) population
+// buffer with row stride sx, box = one plane window of the tensor-copy step; false
+// if the layout does not allow one (lbm_capi.cu).
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes = 4);
 }  // namespace lbm

@@ -1,4 +1,4 @@
-// Fused FP32 step with TMA staging of the populations (sm_103a).
+// Fused step with TMA staging of the populations (sm_103a), FP32 or FP16 storage.
 //
 // For an interior 32 x 16 tile, one thread issues nine 3-D tensor copies
 // (cp.async.bulk.tensor, one per population plane) of the 40 x 18 window that
@@ -9,8 +9,9 @@
 // memory.  Plane i's window starts at (x0 - 4, y0 - 1 - e_iy): x0 - 4 keeps the
 // innermost coordinate a multiple of 4 floats (16 bytes, as the tensor copy
 // requires) and covers the columns x0 - 2 .. x0 + 33 that any direction reads.
-// Tiles whose window would leave the lattice (the periodic wrap) take the
-// plain loads of load_tile.
+// FP16 storage uses 48 x 18 windows from x0 - 8 (16 bytes of halves).  Tiles
+// whose window would leave the lattice (the periodic wrap) take the plain loads
+// of load_tile.
 #pragma once
 
 #include <cuda.h>
@@ -28,6 +29,28 @@ constexpr unsigned kTmaSmem = 9u * kTmaPlane * 4 + 128;     // dynamic shared me
 constexpr long long kWaitSpins = 1ll << 22;                 // bound of the mbarrier wait loop
 // A tensor copy's shared-memory destination must be 128-byte aligned.
 static_assert((kTmaPlane * 4) % 128 == 0, "plane windows must start on 128-byte boundaries");
+// FP16 storage: 48-half windows from x0 - 8 (the innermost coordinate a multiple of 8).
+constexpr int kTmaColsH = kTileX + 16;
+constexpr int kTmaBoxH = kTmaColsH * kTmaRows;              // halves per plane (1728 B)
+constexpr int kTmaPlaneH = (kTmaBoxH * 2 + 127) / 128 * 64;  // plane stride in shared memory, halves (1792 B)
+static_assert((kTmaPlaneH * 2) % 128 == 0, "plane windows must start on 128-byte boundaries");
+
+// Window geometry per storage type: columns, column offset of x0, plane stride (elements),
+// bytes a tile's nine copies deliver, dynamic shared memory of the kernel.
+template <typename S>
+struct Win;
+template <>
+struct Win<float> {
+  static constexpr int cols = kTmaCols, xoff = 4, plane = kTmaPlane;
+  static constexpr unsigned bytes = kTmaBytes, smem = kTmaSmem;
+  __device__ static float get(float v) { return v; }
+};
+template <>
+struct Win<__half> {
+  static constexpr int cols = kTmaColsH, xoff = 8, plane = kTmaPlaneH;
+  static constexpr unsigned bytes = 9u * kTmaBoxH * 2, smem = 9u * kTmaPlaneH * 2 + 128;
+  __device__ static float get(__half v) { return __half2float(v); }
+};
 
 // D2Q9 velocity components e_ix, e_iy (folded to constants in unrolled loops).
 __host__ __device__ constexpr int ex_of(int i) {
@@ -86,8 +109,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 }
 
 // Whether the TMA windows of the tile at (x0, y0) lie inside the lattice.
+template <typename S = float>
 __device__ __forceinline__ bool tma_interior(int x0, int y0, int nx, int ny) {
-  return x0 >= 4 && x0 + kTmaCols - 4 <= nx && y0 >= 2 && y0 + kTmaRows <= ny;
+  return x0 >= Win<S>::xoff && x0 + Win<S>::cols - Win<S>::xoff <= nx && y0 >= 2 && y0 + kTmaRows <= ny;
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -160,16 +184,18 @@ __device__ __forceinline__ void issue_window_async(float* win, const float* __re
 }
 
 // Phase 1 of an interior tile from its staged windows: the populations of the
-// thread's two nodes (window row ly + 1, column lx + 4 - e_ix for plane i) into f,
-// the densities of tile + ring into rs.
-__device__ __forceinline__ void window_tile(const float* __restrict__ win, float (&f)[kTileRows][9],
+// thread's two nodes (window row ly + 1, column lx + xoff - e_ix for plane i) into
+// f, the densities of tile + ring into rs.
+template <typename S>
+__device__ __forceinline__ void window_tile(const S* __restrict__ win, float (&f)[kTileRows][9],
                                             float (*rs)[kTileX + 2]) {
+  using W = Win<S>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
     const int ly = ty + k * kRowStride;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[k][i] = win[i * kTmaPlane + (ly + 1) * kTmaCols + tx + 4 - ex_of(i)];
+    for (int i = 0; i < 9; ++i) f[k][i] = W::get(win[i * W::plane + (ly + 1) * W::cols + tx + W::xoff - ex_of(i)]);
   }
   // Both densities as one packed sum (lane k = node k; the same additions in the
   // same order as the scalar sum).
@@ -184,18 +210,20 @@ __device__ __forceinline__ void window_tile(const float* __restrict__ win, float
     ring_cell(threadIdx.x, wx, wy);
     float g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = win[i * kTmaPlane + wy * kTmaCols + wx + 3 - ex_of(i)];
+    for (int i = 0; i < 9; ++i) g[i] = W::get(win[i * W::plane + wy * W::cols + wx + W::xoff - 1 - ex_of(i)]);
     rs[wy][wx] = sum9(g);
   }
 }
 
 // The nine copies of the interior tile at (x0, y0) into win, completing on bar
 // (one thread).
-__device__ __forceinline__ void issue_windows(float* win, const CUtensorMap* map, int x0, int y0,
+template <typename S>
+__device__ __forceinline__ void issue_windows(S* win, const CUtensorMap* map, int x0, int y0,
                                               unsigned long long* bar, unsigned extra_bytes = 0) {
-  mbar_expect_tx(bar, kTmaBytes + extra_bytes);
+  using W = Win<S>;
+  mbar_expect_tx(bar, W::bytes + extra_bytes);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) tma_load_3d(win + i * kTmaPlane, map, x0 - 4, y0 - 1 - ey_of(i), i, bar);
+  for (int i = 0; i < 9; ++i) tma_load_3d(win + i * W::plane, map, x0 - W::xoff, y0 - 1 - ey_of(i), i, bar);
 }
 
 // How a tile's window is staged: by tensor copies (interior), by per-thread
@@ -203,10 +231,10 @@ __device__ __forceinline__ void issue_windows(float* win, const CUtensorMap* map
 // all (plain loads in phase 1).
 enum TileKind { kTensorCopy = 0, kAsyncCopy = 1, kPlainLoad = 2 };
 
-template <bool ASYNC_EDGES = true>
+template <bool ASYNC_EDGES = true, typename S = float>
 __device__ __forceinline__ int tile_kind(int x0, int y0, int nx, int ny) {
-  return tma_interior(x0, y0, nx, ny) ? kTensorCopy
-                                      : (ASYNC_EDGES && async_window_ok(nx, ny) ? kAsyncCopy : kPlainLoad);
+  return tma_interior<S>(x0, y0, nx, ny) ? kTensorCopy
+                                         : (ASYNC_EDGES && async_window_ok(nx, ny) ? kAsyncCopy : kPlainLoad);
 }
 
 // Persistent form: block b takes tiles b, b + G, b + 2G, ... (G = gridDim.x, tiles
@@ -221,14 +249,16 @@ __device__ __forceinline__ int tile_kind(int x0, int y0, int nx, int ny) {
 // tile: every thread's copies must have landed).  A wait that gives up sets *err.
 // ASYNC_EDGES = false leaves wrapping tiles to plain loads: the per-thread copies
 // cost registers (spills rise from 52 to 140 bytes per thread), which a lattice
-// with few wrapping tiles does not win back.
-template <typename V, bool ASYNC_EDGES>
+// with few wrapping tiles does not win back (and they exist for FP32 only).
+// S: storage type (float, or __half with the stores rounded as rnd says).
+template <typename V, typename S, bool ASYNC_EDGES>
 __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
-    k_step_tma(const __grid_constant__ CUtensorMap tin, const float* __restrict__ fin, float* __restrict__ fout,
-               int nx, int ny, VCoef<V> c, int* __restrict__ err) {
+    k_step_tma(const __grid_constant__ CUtensorMap tin, const S* __restrict__ fin, S* __restrict__ fout, int nx,
+               int ny, VCoef<V> c, int* __restrict__ err, Rounding rnd) {
+  static_assert(!ASYNC_EDGES || sizeof(S) == 4, "asynchronous edge windows exist for FP32 storage only");
   using real = float;
   extern __shared__ __align__(128) unsigned char dyn[];
-  float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
+  S* win = reinterpret_cast<S*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
   __shared__ real rs[2][kTileY + 2][kTileX + 2];
   __shared__ __align__(8) unsigned long long bar;
   const int tiles_x = (nx + kTileX - 1) / kTileX;
@@ -248,12 +278,12 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   // copies, everyone the per-thread ones).
   auto issue = [&](int c0, int r0) {
     const int x0 = c0 * kTileX, y0 = r0 * kTileY;
-    const int kind = tile_kind<ASYNC_EDGES>(x0, y0, nx, ny);
+    const int kind = tile_kind<ASYNC_EDGES, S>(x0, y0, nx, ny);
     if (kind == kTensorCopy && threadIdx.x == 0) {
       fence_proxy_async();
       issue_windows(win, &tin, x0, y0, &bar);
     } else if (kind == kAsyncCopy) {
-      issue_window_async(win, fin, nx, ny, nx, x0, y0);
+      if constexpr (ASYNC_EDGES) issue_window_async(win, fin, nx, ny, nx, x0, y0);
     }
   };
   if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -264,7 +294,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   int buf = 0;
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     const int x0 = tc * kTileX, y0 = tr * kTileY;
-    const int kind = tile_kind<ASYNC_EDGES>(x0, y0, nx, ny);
+    const int kind = tile_kind<ASYNC_EDGES, S>(x0, y0, nx, ny);
     real f[kTileRows][9];
     bool late = false;
     if (kind == kTensorCopy) {
@@ -275,7 +305,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       __syncthreads();
     }
     if (kind == kPlainLoad)
-      load_tile<real, float, kTileY>(fin, nx, ny, nx, x0, y0, f, rs[buf]);
+      load_tile<real, S, kTileY>(fin, nx, ny, nx, x0, y0, f, rs[buf]);
     else  // read even after a failed wait (in bounds; the block then returns)
       window_tile(win, f, rs[buf]);
     // The window is consumed and the densities are in place.  A wait that gave up
@@ -290,7 +320,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     }
     advance(tc, tr);
     if (t + gridDim.x < total) issue(tc, tr);
-    collide_tile<V, float, kTileY>(f, fout, nx, ny, nx, c, lattice_part(c), x0, y0, rs[buf]);
+    collide_tile<V, S, kTileY>(f, fout, nx, ny, nx, c, lattice_part(c), x0, y0, rs[buf], rnd);
     buf ^= 1;
   }
 }

@@ -184,6 +184,27 @@ def test_fp32_tma_path(orc):
     assert not capi.lb_uses_tma(lattice(rho0[:, :150], "fp32", Tr=0.85, K_int=1.0).h)  # nx % 4 != 0
 
 
+def test_fp16_tma_path(orc):
+    """FP16 storage with tensor-copy staging (48-half windows; interior tiles) and
+    plain loads (wrapping tiles) on one lattice, many tiles per block and one,
+    against the oracle within the FP16 tolerance of 500 steps; no wait gave up."""
+    from paper_1809_02390_gb300 import capi
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    rho0 = inputs.droplet(160, 96, 30, 5, p.rho_g, p.rho_l, center=(70.3, 50.6))
+    lat = lattice(rho0, "fp16s", Tr=0.85, K_int=1.0)
+    assert capi.lb_uses_tma(lat.h)
+    capi.lb_set_step_blocks(lat.h, 4)
+    lat.step(250)
+    capi.lb_set_step_blocks(lat.h, 0)
+    lat.step(250)
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), 500))[0]
+    rho = lat.moments(velocity=False).double().cpu().numpy()
+    assert rel_inf(rho, ref) <= 8e-3
+    capi.lb_status(lat.h)
+    assert not capi.lb_uses_tma(lattice(rho0[:, :156], "fp16s", Tr=0.85, K_int=1.0).h)  # nx % 8 != 0
+
+
 # (oracle keywords, library keywords): relaxation rates other than s_p = 1 (so
 # s_q, s_e and every R, T, X, Q_m coefficient move), another varpi, and the
 # Carnahan-Starling EOS with the paper's a = 1, b = 4 and K_EOS, K_INT != 1.
