@@ -191,7 +191,7 @@ template <typename real, typename store_t>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     k_adj_fused(const store_t* __restrict__ s, const real* __restrict__ mu_in, const real* __restrict__ sb_in,
                 real* __restrict__ mu, real* __restrict__ sbar, double* __restrict__ partial, int accumulate, int nx,
-                int ny, VCoef<real> c) {
+                int ny, VCoef<real> c, int stage_state) {
   __shared__ real rs[kTileY + 2][kTileX + 2];   // density of s^n on tile + ring
   __shared__ real rb[kTileY + 2][kTileX + 2];   // rhob' on tile + ring
   __shared__ real sbx[kTileY + 4][kTileX + 4];  // Sb' on tile + two-node ring
@@ -239,14 +239,32 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
   }
   cp_async_commit();
   real f[kTileRows][9];
-#pragma unroll
-  for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * kRowStride;
-    pull_row(s, plane, nx, ny, wr(gy, ny), xm, xc, xp, f[k]);
+  // stage_state (FP32, lattices of at least 40 x 18 with several waves of tiles): the
+  // state's pull window too (the window of the forward step, in dynamic shared
+  // memory), so that every global read of the block is in flight before the first
+  // is used.
+  bool staged = false;
+  if constexpr (kStageMu) {
+    if (stage_state) {  // uniform over the grid
+      extern __shared__ __align__(128) unsigned char dyn[];
+      float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
+      issue_window_async(win, s, nx, ny, nx, x0, y0);
+      cp_async_wait_all();
+      __syncthreads();
+      window_tile(win, f, rs);
+      staged = true;
+    }
   }
+  if (!staged) {
 #pragma unroll
-  for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
-  for (int t = threadIdx.x; t < 2 * (kTileX + 2) + 2 * kTileY; t += kAdjThreads) {
+    for (int k = 0; k < kTileRows; ++k) {
+      const int gy = y0 + ty + k * kRowStride;
+      pull_row(s, plane, nx, ny, wr(gy, ny), xm, xc, xp, f[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  }
+  for (int t = threadIdx.x; t < (staged ? 0 : 2 * (kTileX + 2) + 2 * kTileY); t += kAdjThreads) {
     int wx, wy;
     if (t < kTileX + 2) {
       wx = t, wy = 0;
@@ -392,12 +410,32 @@ int adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, dou
   else
     c = &h->cf;
   const dim3 blk(32, 8), pgrd((nx + 31) / 32, (ny + 7) / 8);
+  // FP32 stages the state's pull window in dynamic shared memory (above the 48 KB
+  // default together with the static arrays, hence the opt-in) when the lattice has
+  // several waves of tiles; on small lattices (one wave) waiting for the whole
+  // window before any work measured slower (256^2: 8.7 against 7.2 us per step).
+  size_t win_smem = 0;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 0;
+  if constexpr (sizeof(real) == 4) {
+    if (async_window_ok(nx, ny) && sms > 0 && size_t(grd.x) * grd.y >= size_t(4) * 3 * sms) {
+      win_smem = kTmaSmem;
+      const cudaError_t a = cudaFuncSetAttribute(k_adj_fused<real, store_t>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(win_smem));
+      if (a != cudaSuccess) {
+        std::snprintf(h->err, sizeof(h->err), "adjoint kernels: %s", cudaGetErrorString(a));
+        return LB_ECUDA;
+      }
+    }
+  }
   k_adj_push<real><<<pgrd, blk, 0, h->stream>>>(static_cast<const real*>(lam), mu[0], sb[0], nx, ny);
   int cur = 0;
   for (int j = k - 1; j >= 0; --j) {
-    k_adj_fused<real, store_t><<<grd, kAdjThreads, 0, h->stream>>>(static_cast<const store_t*>(states[j]), mu[cur],
-                                                                   sb[cur], mu[1 - cur], sb[1 - cur], partial,
-                                                                   j < k - 1, nx, ny, *c);
+    k_adj_fused<real, store_t><<<grd, kAdjThreads, win_smem, h->stream>>>(
+        static_cast<const store_t*>(states[j]), mu[cur], sb[cur], mu[1 - cur], sb[1 - cur], partial, j < k - 1, nx,
+        ny, *c, win_smem > 0 ? 1 : 0);
     cur = 1 - cur;
   }
   if (dtheta) k_adj_theta<<<1, 256, 0, h->stream>>>(partial, int(grd.x * grd.y), h->p.R_gas, dtheta);

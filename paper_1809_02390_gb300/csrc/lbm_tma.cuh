@@ -143,7 +143,9 @@ __device__ __forceinline__ void ring_cell(int t, int& wx, int& wy) {
 // kTmaCols x kTmaRows nodes is staged ahead (every coordinate then lies in
 // [-4, 2n) and one conditional wrap suffices).  240 threads = 6 window rows x 40
 // columns per pass, 3 passes, 9 planes: 27 copies per thread.
-__device__ __forceinline__ bool async_window_ok(int nx, int ny) { return nx >= kTmaCols && ny >= kTmaRows; }
+__host__ __device__ __forceinline__ bool async_window_ok(int nx, int ny) {
+  return nx >= kTmaCols && ny >= kTmaRows;
+}
 
 constexpr int kAsyncThreads = 6 * kTmaCols;
 static_assert(kTmaRows % 6 == 0 && kAsyncThreads <= kFusedThreads, "window rows split in passes of 6");

@@ -151,12 +151,13 @@ def test_rollout_gradient_vs_oracle_complex_step(orc):
     assert np.allclose(g, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("nx,ny", [(45, 38), (33, 17), (130, 70)])
+@pytest.mark.parametrize("nx,ny", [(45, 38), (33, 17), (130, 70), (1540, 644)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_fused_segment_equals_single_steps(orc, precision, tol, nx, ny):
     """lb_adjoint_steps (fused, one kernel per step) against k calls of lb_adjoint_step,
-    on lattices where the FP32 fused step stages the state window by asynchronous
-    copies (at least 40 x 18, several tiles) and where it pulls directly (33 x 17)."""
+    on small lattices where the fused FP32 step pulls the state directly and on one
+    with several waves of tiles (1540 x 644, ragged) where it stages the state
+    window by asynchronous copies."""
     from paper_1809_02390_gb300 import capi
 
     p = oracle_params(Tr=0.85, K_int=1.0)
