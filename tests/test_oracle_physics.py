@@ -189,3 +189,22 @@ def test_complex_step_matches_finite_differences(orc):
     assert np.abs(jvp - fd).max() < 1e-7 * np.abs(jvp).max()
     re, _ = orc.step_cs(p, f, None, (0, 0, 0), nsteps=3)
     assert np.array_equal(re, orc.step(p, f, 3))
+
+
+@pytest.mark.parametrize("Tr,gas_off", [(0.8, 0.1), (0.9, 0.03)])
+def test_q_term_is_what_recovers_maxwell(orc, Tr, gas_off):
+    """The force term Q_m (Eq. 14) removes the extra stress R_add of the recovered
+    pressure tensor (supplement Eq. 59); with it the flat-interface gas density
+    follows the Maxwell construction (0.5%), without it (the collision of Eq. 10
+    alone) the gas density misses by more than `gas_off` (34% at Tr = 0.8). This pins
+    Q_m itself: a dropped, halved or mis-signed Q_m moves the gas branch by far
+    more than the tolerance of the coexistence test."""
+    e = thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, Tr)
+    W = thermo.interface(e, 1.0)["W"]
+    gas = {}
+    for form in (13, 10):
+        p = op.from_physical(Tr=Tr, K_int=1.0, form=form)
+        f = orc.step(p, orc.init_feq(p, inputs.slab(128, 2, 64, W, p.rho_g, p.rho_l)), 8000)
+        gas[form] = orc.macro(p, f)[0][0, 0] / p.rho_g - 1
+    assert abs(gas[13]) < 5e-3
+    assert abs(gas[10]) > gas_off
