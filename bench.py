@@ -141,13 +141,22 @@ def time_steps(lat, steps: int, torch) -> float:
 
 
 def max_over_ranks(v: float, torch, world: int) -> float:
+    """Largest value over the ranks (the slowest rank's time): one all_reduce, on
+    the GPU under NCCL, on the host under gloo."""
     if world == 1:
         return v
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_mlups(world: int, nodes: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: every rank advances its own lattice of `nodes` nodes by
+    `steps` steps; `ms` is the slowest rank's time (weak scaling)."""
+    return world * nodes * steps / (ms * 1e-3) / 1e6
 
 
 def barrier(world: int):
@@ -466,7 +475,7 @@ def run_ours(args):
         ms = time_steps(lat, args.steps, torch)
     ms = max_over_ranks(ms, torch, world)
     ms_step = ms / args.steps
-    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    value = aggregate_mlups(world, nodes, args.steps, ms)
     achieved = BYTES_PER_LU["fp32"] * nodes / (ms_step * 1e-3) / 1e9
     sane = lat.reduce()
     lat.close()
