@@ -273,6 +273,15 @@ int lb_set_state(lb_handle* h, const void* src);
  * else LB_OK.  Kernels never spin without a limit. */
 int lb_status(lb_handle* h);
 
+/* Check of the reporting above, for users and tests (no counterpart in the paper):
+ * runs one block whose bounded wait can never succeed (an mbarrier expecting bytes
+ * that no copy delivers), polling it `polls` times (1 .. 2^22; the kernels' waits
+ * also give up after 1 s, whichever comes first), then returns what
+ * lb_status returns: LB_ETIMEOUT when the give-up was recorded and read back (the
+ * expected result; the flag is cleared), LB_OK if it was lost.  Synchronous.  No
+ * memory is touched but the device flag, and the context stays usable. */
+int lb_wait_selftest(lb_handle* h, long long polls);
+
 /* 1 if the handle's fused step stages populations with tensor copies (TMA):
  * FP32 storage with nx a multiple of 4 and nx >= 104, or FP16 storage with nx a
  * multiple of 8 and nx >= 112; ny >= 50.  Else 0. */

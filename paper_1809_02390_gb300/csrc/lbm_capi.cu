@@ -228,6 +228,21 @@ namespace {
 // Set by a bounded wait of the tensor-copy step that gave up (read and cleared by lb_status).
 __device__ int g_wait_error;
 
+// A bounded wait that cannot succeed: the mbarrier's single arrival comes with 16
+// expected bytes that no copy delivers, so its phase never completes.  Every thread
+// polls it `polls` times, the block agrees through the barrier that the wait gave
+// up, and thread 0 reports it the way the step kernels do.  No copy is in flight.
+__global__ void k_wait_selftest(long long polls, int* __restrict__ err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  const bool done = mbar_wait(&bar, 0, polls);
+  if (__syncthreads_or(!done) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 int configure(lb_handle* h) {
   const int rc = configure_device(h);
   if (rc != LB_OK) return rc;
@@ -510,6 +525,16 @@ int lb_status(lb_handle* h) {
     return fail(h, LB_ETIMEOUT, "a bounded wait for a tensor copy gave up");
   }
   return LB_OK;
+}
+
+int lb_wait_selftest(lb_handle* h, long long polls) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (polls < 1 || polls > (1ll << 22)) return fail(h, LB_EINVAL, "polls must be in [1, 2^22]");
+  void* w = nullptr;
+  LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_error));
+  k_wait_selftest<<<1, 128, 0, h->stream>>>(polls, static_cast<int*>(w));
+  LB_CUDA(h, cudaGetLastError());
+  return lb_status(h);
 }
 
 int lb_uses_tma(const lb_handle* h) { return h && h->use_tma ? 1 : 0; }

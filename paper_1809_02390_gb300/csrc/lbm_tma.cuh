@@ -26,7 +26,8 @@ constexpr int kTmaBox = kTmaCols * kTmaRows;                // floats copied per
 constexpr int kTmaPlane = (kTmaBox * 4 + 127) / 128 * 32;   // plane stride in shared memory, floats (2944 B)
 constexpr unsigned kTmaBytes = 9u * kTmaBox * 4;            // bytes a tile's nine copies deliver
 constexpr unsigned kTmaSmem = 9u * kTmaPlane * 4 + 128;     // dynamic shared memory (+ alignment slack)
-constexpr long long kWaitSpins = 1ll << 22;                 // bound of the mbarrier wait loop
+constexpr long long kWaitSpins = 1ll << 22;                 // bound of the mbarrier wait loop (polls)
+constexpr unsigned long long kWaitNs = 1000000000ull;      // and of its duration (1 s)
 // A tensor copy's shared-memory destination must be 128-byte aligned.
 static_assert((kTmaPlane * 4) % 128 == 0, "plane windows must start on 128-byte boundaries");
 // FP16 storage: 48-half windows from x0 - 8 (the innermost coordinate a multiple of 8).
@@ -84,10 +85,22 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 
-// Bounded wait: false if the barrier did not complete within kWaitSpins polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
-  for (long long i = 0; i < kWaitSpins; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: false if the barrier did not complete within `polls` polls or
+// kWaitNs nanoseconds, whichever comes first (a poll may suspend the thread for a
+// while, so the time bound is the one that holds in every case).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase, long long polls = kWaitSpins) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long i = 1; i < polls; ++i) {
     if (mbar_try_wait(bar, phase)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 

@@ -252,3 +252,20 @@ def test_fp16_stochastic_rounding_keeps_mass():
         lat.close()
     assert drift["stochastic"] < 1e-3
     assert drift["nearest"] > 2 * drift["stochastic"]
+
+
+def test_bounded_wait_gives_up_and_is_reported(orc):
+    """A wait that nothing completes (lb_wait_selftest) ends after its poll budget,
+    is reported as LB_ETIMEOUT once (the flag is then clear), and the context stays
+    usable: the tensor-copy step still matches the oracle afterwards."""
+    from paper_1809_02390_gb300 import capi
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    rho0 = inputs.droplet(160, 96, 30, 5, p.rho_g, p.rho_l)
+    lat = lattice(rho0, "fp32", Tr=0.85, K_int=1.0)
+    assert capi.lb_wait_selftest(lat.h, 2000) == capi.LB_ETIMEOUT
+    capi.lb_status(lat.h)  # cleared: no error now
+    lat.step(100)
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), 100))[0]
+    assert rel_inf(lat.moments(velocity=False).double().cpu().numpy(), ref) <= 2e-5
+    capi.lb_status(lat.h)
