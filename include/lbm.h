@@ -64,7 +64,8 @@ typedef struct lb_params {
   int32_t precision; /* enum lb_precision: storage type; FP16S computes in FP32 */
   int32_t eos;       /* enum lb_eos_kind: van der Waals p = rho R T/(1 - b rho) - a rho^2,
                         or Carnahan-Starling (Eq. 20); both times K_EOS */
-  int32_t variant;   /* enum lb_variant: fused single-kernel step or density pass + collision */
+  int32_t variant;   /* enum lb_variant: fused single-kernel step or density pass + collision;
+                        LB_AUTO selects the fused step (the faster one on this GPU) */
   int32_t rounding;  /* enum lb_rounding, FP16S only: rounding of the stored populations.
                         Stochastic (default): a pseudo-random dither below the half
                         mantissa, then truncation, so that rounding errors have zero mean
