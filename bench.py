@@ -38,7 +38,7 @@ KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_023
                   "paper_1809_02390_gb300/csrc/lbm_tma.cuh"]
 NCU_TRAFFIC = {
     # 2048^2 capture (profiles/k_step_tma_fp32_2048_full.md) scaled x4 to 4096^2.
-    ("k_step_tma<f2>", "ac80adf64d035855"): 1035771904,
+    ("k_step_tma<f2>", "eb0531ee237550db"): 1032412160,
 }
 
 
