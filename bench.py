@@ -478,6 +478,19 @@ def run_ours(args):
     value = aggregate_mlups(world, nodes, args.steps, ms)
     achieved = BYTES_PER_LU["fp32"] * nodes / (ms_step * 1e-3) / 1e9
     sane = lat.reduce()
+    # Ceiling of the access pattern: the same nine read and nine write streams with
+    # no arithmetic (lb_stream_copy), timed like the step.
+    for _ in range(5):
+        capi.lb_stream_copy(lat.h)
+    s_ = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s_)
+    for _ in range(50):
+        capi.lb_stream_copy(lat.h)
+    e1.record(s_)
+    torch.cuda.synchronize()
+    pattern_gbs = BYTES_PER_LU["fp32"] * nodes * 50 / (e0.elapsed_time(e1) * 1e-3) / 1e9
     lat.close()
     del lat
     torch.cuda.empty_cache()
@@ -541,7 +554,9 @@ def run_ours(args):
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "kernel": kernel, "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
             "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
-            "kernel_source_sha": src_hash}
+            "kernel_source_sha": src_hash,
+            "pattern_ceiling": {"GBps": round(pattern_gbs, 1), "frac": round(achieved / pattern_gbs, 4),
+                                "what": "lb_stream_copy: the step's 9 read + 9 write SoA streams, no arithmetic"}}
     cpu = cpu_baseline(rho0) if world == 1 else None
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",

@@ -288,6 +288,14 @@ int lb_wait_selftest(lb_handle* h, long long polls);
  * multiple of 8 and nx >= 112; ny >= 50.  Else 0. */
 int lb_uses_tma(const lb_handle* h);
 
+/* Measurement aid (no counterpart in the paper): one pass with the step's memory
+ * traffic and none of its arithmetic, a copy of the state into the other buffer
+ * reading and writing every population in place (nine read and nine write
+ * streams, as the step).  The state is unchanged (the copy is exact and becomes
+ * the current buffer).  Asynchronous on the handle's stream; the pass's bandwidth
+ * is the ceiling the step's SoA access pattern allows. */
+int lb_stream_copy(lb_handle* h);
+
 /* Grid of that persistent kernel (each block steps tiles b, b + blocks, ...):
  * blocks > 0 fixes it (at most the tile count), 0 restores the default (as many
  * blocks as can be resident).  LB_EINVAL if blocks < 0.  Results do not depend

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
     ("lb_status", ctypes.c_int, [_V]),
     ("lb_wait_selftest", ctypes.c_int, [_V, ctypes.c_longlong]),
+    ("lb_stream_copy", ctypes.c_int, [_V]),
     ("lb_pressure", ctypes.c_int, [_V, _V]),
     ("lb_uses_tma", ctypes.c_int, [_V]),
     ("lb_set_step_blocks", ctypes.c_int, [_V, ctypes.c_int]),
@@ -299,6 +300,10 @@ def lb_pressure(h: int, p: int) -> None:
 def lb_wait_selftest(h: int, polls: int) -> int:
     """Return code of lb_wait_selftest (LB_ETIMEOUT = -5 when the give-up is reported)."""
     return lib().lb_wait_selftest(h, polls)
+
+
+def lb_stream_copy(h: int) -> None:
+    check(lib().lb_stream_copy(h), h)
 
 
 def lb_status(h: int) -> None:

@@ -228,6 +228,22 @@ namespace {
 // Set by a bounded wait of the tensor-copy step that gave up (read and cleared by lb_status).
 __device__ int g_wait_error;
 
+// The step's memory traffic without its arithmetic: every node's nine populations
+// read from their nine planes and written to the same places of the other buffer
+// (grid-stride loop, coalesced per plane).  Its bandwidth is the ceiling of the
+// SoA access pattern (nine read and nine write streams at once).
+template <typename T>
+__global__ void k_stream_soa(const T* __restrict__ in, T* __restrict__ out, long long N) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += stride) {
+    T v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = in[i * N + x];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i * N + x] = v[i];
+  }
+}
+
 // A bounded wait that cannot succeed: the mbarrier's single arrival comes with 16
 // expected bytes that no copy delivers, so its phase never completes.  Every thread
 // polls it `polls` times, the block agrees through the barrier that the wait gave
@@ -535,6 +551,30 @@ int lb_wait_selftest(lb_handle* h, long long polls) {
   k_wait_selftest<<<1, 128, 0, h->stream>>>(polls, static_cast<int*>(w));
   LB_CUDA(h, cudaGetLastError());
   return lb_status(h);
+}
+
+int lb_stream_copy(lb_handle* h) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  const long long N = (long long)h->p.nx * h->p.ny;
+  int dev = 0, sms = 0;
+  LB_CUDA(h, cudaGetDevice(&dev));
+  LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const void* in = h->f[h->cur];
+  void* out = h->f[1 - h->cur];
+  const unsigned grid = unsigned(sms * 8);
+  switch (h->p.precision) {
+    case LB_FP64:
+      k_stream_soa<<<grid, 256, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), N);
+      break;
+    case LB_FP32:
+      k_stream_soa<<<grid, 256, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), N);
+      break;
+    default:
+      k_stream_soa<<<grid, 256, 0, h->stream>>>(static_cast<const __half*>(in), static_cast<__half*>(out), N);
+  }
+  LB_CUDA(h, cudaGetLastError());
+  h->cur = 1 - h->cur;  // same data in the other buffer: the state is unchanged
+  return LB_OK;
 }
 
 int lb_uses_tma(const lb_handle* h) { return h && h->use_tma ? 1 : 0; }

@@ -269,3 +269,23 @@ def test_bounded_wait_gives_up_and_is_reported(orc):
     ref = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), 100))[0]
     assert rel_inf(lat.moments(velocity=False).double().cpu().numpy(), ref) <= 2e-5
     capi.lb_status(lat.h)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_stream_copy_leaves_the_state(precision):
+    """lb_stream_copy (the step's memory traffic without its arithmetic) moves the
+    state to the other buffer bit for bit; the lattice then steps as before."""
+    from paper_1809_02390_gb300 import capi, derive
+
+    d = derive(130, 70, Tr=0.8)
+    rho0 = inputs.droplet(130, 70, 15, 4, d["rho_g"], d["rho_l"])
+    a = lattice(rho0, precision, Tr=0.8)
+    b = lattice(rho0, precision, Tr=0.8)
+    a.step(3)
+    b.step(3)
+    before = a.state().clone()
+    capi.lb_stream_copy(a.h)
+    assert torch.equal(a.state(), before)
+    a.step(5)
+    b.step(5)
+    assert torch.equal(a.state(), b.state())
