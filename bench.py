@@ -36,9 +36,9 @@ BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 popula
 # for the kernel sources they were measured on (sha256 of the files below).
 KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_02390_gb300/csrc/lbm_device.cuh",
                   "paper_1809_02390_gb300/csrc/lbm_tma.cuh"]
+# DRAM bytes per launch of the timed kernel from one ncu capture, keyed by kernel,
+# layout and the hash of its sources (a changed kernel has no figure until recaptured).
 NCU_TRAFFIC = {
-    # 2048^2 capture (profiles/k_step_tma_fp32_2048_full.md) scaled x4 to 4096^2.
-    ("k_step_tma<f2>", "eb0531ee237550db"): 1032412160,
 }
 
 
@@ -467,7 +467,7 @@ def run_ours(args):
     pk = peaks()
 
     # --- main measurement: FP32 fused, inputs resident in HBM -----------------
-    lat = Lattice(rho0, precision="fp32", variant="fused", Tr=TR)
+    lat = Lattice(rho0, precision="fp32", variant="fused", Tr=TR, layout=args.layout)
     kernel = "k_step_tma<f2>" if capi.lb_uses_tma(lat.h) else "k_step_fused<f2,float>"
     lat.step(args.warmup)
     barrier(world)
@@ -496,17 +496,21 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if args.only_main:
         if rank == 0:
-            print(json.dumps({"only_main": True, "size": n, "MLUPS": round(value, 1), "ms_per_step": ms_step}))
+            print(json.dumps({"only_main": True, "size": n, "layout": args.layout, "MLUPS": round(value, 1),
+                              "ms_per_step": ms_step, "pattern_GBps": round(pattern_gbs, 1)}))
         return
 
     # --- other variants / precisions (shorter runs, same workload) -------------
     variants = {}
-    for prec, var, k in (("fp32", "two_pass", max(50, args.steps // 4)), ("fp16s", "fused", max(50, args.steps // 4)),
-                         ("fp64", "fused", 30)):
-        lt = Lattice(rho0, precision=prec, variant=var, Tr=TR)
+    other = "planes" if args.layout == "rows" else "rows"
+    quarter = max(50, args.steps // 4)
+    for prec, var, lay, k in (("fp32", "fused", other, quarter), ("fp32", "two_pass", args.layout, quarter),
+                              ("fp16s", "fused", args.layout, quarter), ("fp16s", "fused", other, quarter),
+                              ("fp64", "fused", args.layout, 30)):
+        lt = Lattice(rho0, precision=prec, variant=var, Tr=TR, layout=lay)
         lt.step(3)
         m = time_steps(lt, k, torch) / k
-        variants["%s_%s" % (prec, var)] = {
+        variants["%s_%s_%s" % (prec, var, lay)] = {
             "MLUPS": round(nodes / (m * 1e-3) / 1e6, 1), "ms_per_step": round(m, 4),
             "algorithmic_GBps": round(BYTES_PER_LU[prec] * nodes / (m * 1e-3) / 1e9, 1)}
         lt.close()
@@ -519,7 +523,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    lt = Lattice(rho_host, precision="fp32", variant="fused", Tr=TR)
+    lt = Lattice(rho_host, precision="fp32", variant="fused", Tr=TR, layout=args.layout)
     lt.step(args.steps)
     rho_dev = lt.moments(velocity=False)
     out_host.copy_(rho_dev, non_blocking=True)
@@ -549,20 +553,22 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
     src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get((kernel, src_hash))
+    traffic = NCU_TRAFFIC.get((kernel, args.layout, src_hash))
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "kernel": kernel, "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
             "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
             "kernel_source_sha": src_hash,
             "pattern_ceiling": {"GBps": round(pattern_gbs, 1), "frac": round(achieved / pattern_gbs, 4),
-                                "what": "lb_stream_copy: the step's 9 read + 9 write SoA streams, no arithmetic"}}
+                                "what": "lb_stream_copy: the step's 9 read + 9 write streams in the same "
+                                        "layout, no arithmetic"}}
     cpu = cpu_baseline(rho0) if world == 1 else None
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "spinodal-%dx%d-fp32-vdw-Tr0.8" % (n, n), "lattice": [n, n], "eos": "vdw",
                        "Tr": TR, "storage": "fp32 (deviation from w_i rho_ref)", "variant": "fused",
+                       "layout": {"planes": "f[9][ny][nx]", "rows": "f[ny][9][nx]"}[args.layout],
                        "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
                        "parallelism": "independent lattice per GPU" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
@@ -588,6 +594,8 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=20000, help="steps of the precision study")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batch and calibration runs")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the 256-lattice batch run")
+    ap.add_argument("--layout", choices=["planes", "rows"], default="rows",
+                    help="population layout of the timed lattice (the other one is timed as a variant)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -21,10 +21,12 @@
  *
  * Memory.  The caller owns every buffer: the library never allocates device
  * memory for the lattice and never frees caller memory.  Populations are stored
- * structure-of-arrays, f[i][y][x], i = 0..8 in the velocity order of
- * supplement Eq. 3 (rest, +x, +y, -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1)),
- * x fastest, no padding, as the deviation fbar_i - w_i rho_ref from the rest
- * state (w = 4/9, 1/9 x4, 1/36 x4; rho_ref = 0 stores plain populations).
+ * structure-of-arrays, f[i][y][x] (LB_LAYOUT_PLANES, the default) or with a
+ * row's nine population rows side by side, f[y][i][x] (LB_LAYOUT_ROWS), i = 0..8
+ * in the velocity order of supplement Eq. 3 (rest, +x, +y, -x, -y, (+1,+1),
+ * (-1,+1), (-1,-1), (+1,-1)), x fastest, no padding, as the deviation
+ * fbar_i - w_i rho_ref from the rest state (w = 4/9, 1/9 x4, 1/36 x4;
+ * rho_ref = 0 stores plain populations).
  * Element type: double (LB_FP64), float (LB_FP32) or IEEE half (LB_FP16S).
  * The stored state is always post-collision (after the last completed step).
  *
@@ -57,6 +59,11 @@ enum lb_precision { LB_FP64 = 0, LB_FP32 = 1, LB_FP16S = 2 };
 enum lb_eos_kind { LB_EOS_VDW = 0, LB_EOS_CS = 1 };
 enum lb_variant { LB_AUTO = 0, LB_FUSED = 1, LB_TWO_PASS = 2 };
 enum lb_rounding { LB_ROUND_STOCHASTIC = 0, LB_ROUND_NEAREST = 1 };
+/* Population layout of the state buffers (the arithmetic is the same in both;
+ * results are bit-identical).  PLANES: f[9][ny][nx]; ROWS: f[ny][9][nx], one
+ * lattice row's nine population rows contiguous, so that a step reads and writes
+ * one region per row instead of nine planes far apart. */
+enum lb_layout { LB_LAYOUT_PLANES = 0, LB_LAYOUT_ROWS = 1 };
 
 /* Problem statement (main text Eqs. 6, 7, 16, 20-22; supplement Sec. V). */
 typedef struct lb_params {
@@ -84,6 +91,10 @@ typedef struct lb_params {
                              (Eq. 16), s_eps = s_e; otherwise in (0, 2) */
   double s_0, s_j;        /* rates of the conserved moments (act on zero); <= 0 selects 1 */
   double rho_ref;         /* storage shift: populations stored as fbar_i - w_i rho_ref */
+  int32_t layout;         /* enum lb_layout.  LB_LAYOUT_ROWS: forward step, moments, pressure,
+                             reductions; the adjoint calls and the batched solver take
+                             LB_LAYOUT_PLANES only (LB_ENOTSUP) */
+  int32_t reserved1;      /* must be 0 */
 } lb_params;
 
 /* Derived lattice-unit quantities (all FP64, computed on the host). */
@@ -293,7 +304,7 @@ int lb_uses_tma(const lb_handle* h);
  * reading and writing every population in place (nine read and nine write
  * streams, as the step).  The state is unchanged (the copy is exact and becomes
  * the current buffer).  Asynchronous on the handle's stream; the pass's bandwidth
- * is the ceiling the step's SoA access pattern allows. */
+ * is the ceiling the step's access pattern allows, in the handle's layout. */
 int lb_stream_copy(lb_handle* h);
 
 /* Grid of that persistent kernel (each block steps tiles b, b + blocks, ...):

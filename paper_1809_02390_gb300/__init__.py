@@ -19,6 +19,8 @@ from .capi import LB_FP16S, LB_FP32, LB_FP64, LB_FUSED, LB_TWO_PASS, LBError  # 
 PRECISIONS = {"fp64": capi.LB_FP64, "fp32": capi.LB_FP32, "fp16s": capi.LB_FP16S}
 VARIANTS = {"fused": capi.LB_FUSED, "two_pass": capi.LB_TWO_PASS}
 EOS = {"vdw": capi.LB_EOS_VDW, "cs": capi.LB_EOS_CS}
+# Population layouts of the state buffers: f[9][ny][nx], or f[ny][9][nx].
+LAYOUTS = {"planes": capi.LB_LAYOUT_PLANES, "rows": capi.LB_LAYOUT_ROWS}
 # Rest-state weights w_i of the storage shift, in the velocity order of the ABI.
 W_REST = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 
@@ -38,9 +40,9 @@ def derive(nx: int = 64, ny: int = 64, **kw) -> dict:
 
 
 def params(nx: int, ny: int, precision: str = "fp32", eos: str = "vdw", variant: str = "fused",
-           **kw) -> capi.lb_params:
+           layout: str = "planes", **kw) -> capi.lb_params:
     return capi.make_params(nx, ny, precision=PRECISIONS[precision], eos=EOS[eos], variant=VARIANTS[variant],
-                            **kw)
+                            layout=LAYOUTS[layout], **kw)
 
 
 class Lattice:
@@ -49,10 +51,12 @@ class Lattice:
     rho0: initial density [ny, nx] (numpy array on the host, or a float64 CUDA
     tensor).  Keyword arguments are the fields of ``lb_params`` (Tr, K_int,
     s_p, rho_ref, ...).  ``rho_ref=None`` stores deviations from the rest state
-    at the mean initial density for reduced-precision storage."""
+    at the mean initial density for reduced-precision storage.  ``layout``:
+    "planes" stores f[9][ny][nx], "rows" f[ny][9][nx] (same results; the adjoint
+    and the batched solver take "planes")."""
 
     def __init__(self, rho0, precision: str = "fp32", eos: str = "vdw", variant: str = "fused",
-                 rho_ref: float | None = None, stream=None, **kw):
+                 rho_ref: float | None = None, stream=None, layout: str = "planes", **kw):
         torch = _torch()
         if isinstance(rho0, np.ndarray):
             rho_host = np.ascontiguousarray(rho0, dtype=np.float64)
@@ -69,15 +73,17 @@ class Lattice:
             rho_ref = 0.0 if precision == "fp64" else float(rho_t.double().mean())
         if precision != "fp64":
             rho_ref = float(np.float32(rho_ref))  # the library stores the shift in float
-        self.p = params(nx, ny, precision=precision, eos=eos, variant=variant, rho_ref=rho_ref, **kw)
-        self.nx, self.ny, self.precision = nx, ny, precision
+        self.p = params(nx, ny, precision=precision, eos=eos, variant=variant, rho_ref=rho_ref, layout=layout,
+                        **kw)
+        self.nx, self.ny, self.precision, self.layout = nx, ny, precision, layout
         self.rho_ref = rho_ref
         self.dtype = {"fp64": torch.float64, "fp32": torch.float32, "fp16s": torch.float16}[precision]
         self.real = torch.float64 if precision == "fp64" else torch.float32
         dev = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.f_a = torch.empty((9, ny, nx), dtype=self.dtype, device=dev)
-        self.f_b = torch.empty((9, ny, nx), dtype=self.dtype, device=dev)
+        shape = (9, ny, nx) if layout == "planes" else (ny, 9, nx)
+        self.f_a = torch.empty(shape, dtype=self.dtype, device=dev)
+        self.f_b = torch.empty(shape, dtype=self.dtype, device=dev)
         nscr = capi.lb_scratch_bytes(self.p)
         self.scratch = torch.empty(nscr, dtype=torch.uint8, device=dev)
         self._rho0_keep = rho_t
@@ -92,9 +98,15 @@ class Lattice:
     def steps_done(self) -> int:
         return capi.lb_steps_done(self.h)
 
-    def state(self):
-        """The current (post-collision) state buffer, stored as deviations f_i - w_i rho_ref."""
+    def buffer(self):
+        """The current (post-collision) state buffer in its storage layout."""
         return self.f_a if capi.lb_state(self.h) == self.f_a.data_ptr() else self.f_b
+
+    def state(self):
+        """The current state as a [9, ny, nx] view of the buffer (a permuted view in
+        the rows layout), stored as deviations f_i - w_i rho_ref."""
+        b = self.buffer()
+        return b if self.layout == "planes" else b.permute(1, 0, 2)
 
     def populations(self):
         """Post-collision populations in FP64 (storage shift added back)."""

@@ -17,6 +17,7 @@ LB_OK, LB_EINVAL, LB_ECUDA, LB_ENOMEM, LB_ENONFINITE, LB_ETIMEOUT, LB_ENOTSUP = 
 LB_FP64, LB_FP32, LB_FP16S = 0, 1, 2
 LB_EOS_VDW, LB_EOS_CS = 0, 1
 LB_AUTO, LB_FUSED, LB_TWO_PASS = 0, 1, 2
+LB_LAYOUT_PLANES, LB_LAYOUT_ROWS = 0, 1
 
 
 class lb_params(ctypes.Structure):
@@ -27,7 +28,7 @@ class lb_params(ctypes.Structure):
                 ("G2", ctypes.c_double), ("lam", ctypes.c_double), ("varpi", ctypes.c_double),
                 ("s_p", ctypes.c_double), ("s_q", ctypes.c_double), ("s_e", ctypes.c_double),
                 ("s_eps", ctypes.c_double), ("s_0", ctypes.c_double), ("s_j", ctypes.c_double),
-                ("rho_ref", ctypes.c_double)]
+                ("rho_ref", ctypes.c_double), ("layout", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class lb_derived(ctypes.Structure):
@@ -124,10 +125,10 @@ def make_params(nx: int, ny: int, precision: int = LB_FP32, eos: int = LB_EOS_VD
                 K_eos: float = 1.0, K_int: float = 1.0, G2: float = 0.0, lam: float = 0.0,
                 varpi: float = 1.0 / 6.0, s_p: float = 1.0, s_q: float = 0.0, s_e: float = 0.0,
                 s_eps: float = 0.0, s_0: float = 0.0, s_j: float = 0.0, rho_ref: float = 0.0,
-                rounding: int = 0) -> lb_params:
+                rounding: int = 0, layout: int = LB_LAYOUT_PLANES) -> lb_params:
     return lb_params(nx=nx, ny=ny, precision=precision, eos=eos, variant=variant, rounding=rounding, eos_a=eos_a,
                      eos_b=eos_b, R_gas=R_gas, Tr=Tr, K_eos=K_eos, K_int=K_int, G2=G2, lam=lam, varpi=varpi,
-                     s_p=s_p, s_q=s_q, s_e=s_e, s_eps=s_eps, s_0=s_0, s_j=s_j, rho_ref=rho_ref)
+                     s_p=s_p, s_q=s_q, s_e=s_e, s_eps=s_eps, s_0=s_0, s_j=s_j, rho_ref=rho_ref, layout=layout)
 
 
 def lb_derive(p: lb_params) -> dict:

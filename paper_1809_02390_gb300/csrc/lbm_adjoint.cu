@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     if (stage_state) {  // uniform over the grid
       extern __shared__ __align__(128) unsigned char dyn[];
       float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
-      issue_window_async(win, s, nx, ny, nx, x0, y0);
+      issue_window_async(win, s, nx, ny, planes_strides(nx, ny), x0, y0);
       cp_async_wait_all();
       __syncthreads();
       window_tile(win, f, rs);
@@ -489,6 +489,10 @@ int lb_adjoint_step(lb_handle* h, const void* f_state, const void* lam_in, void*
     std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step: null or aliased buffers");
     return LB_EINVAL;
   }
+  if (h->p.layout != LB_LAYOUT_PLANES) {
+    std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step: the adjoint takes the planes layout");
+    return LB_ENOTSUP;
+  }
   const size_t need = lb_adjoint_scratch_bytes(&h->p);
   if (!scratch || scratch_bytes < need) {
     std::snprintf(h->err, sizeof(h->err), "lb_adjoint_step needs %zu bytes of scratch, got %zu", need,
@@ -515,6 +519,10 @@ int lb_adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, 
   if (!states || k < 1 || !lam) {
     std::snprintf(h->err, sizeof(h->err), "lb_adjoint_steps: need k >= 1 states and a cotangent buffer");
     return LB_EINVAL;
+  }
+  if (h->p.layout != LB_LAYOUT_PLANES) {
+    std::snprintf(h->err, sizeof(h->err), "lb_adjoint_steps: the adjoint takes the planes layout");
+    return LB_ENOTSUP;
   }
   for (int j = 0; j < k; ++j)
     if (!states[j]) {

@@ -86,8 +86,9 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
   TileRec ti = tiles[t];
   int word = threadIdx.x < kCoefWords ? reinterpret_cast<const int*>(coef + ti.lat)[threadIdx.x] : 0;
   if constexpr (!PERSIST) {  // one block per tile
-    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, ti.sx, common, cs, ti.x0,
-                               ti.y0, rs, StoreCoef{&cs, word, true});
+    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny,
+                               planes_strides(ti.sx, ti.ny), common, cs, ti.x0, ti.y0, rs,
+                               StoreCoef{&cs, word, true});
     return;
   }
   int last = -1;
@@ -101,8 +102,8 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
     }
     const StoreCoef hook{&cs, word, ti.lat != last};
     last = ti.lat;
-    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny, ti.sx, common, cs, ti.x0,
-                               ti.y0, rs, hook);
+    step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny,
+                               planes_strides(ti.sx, ti.ny), common, cs, ti.x0, ti.y0, rs, hook);
     if (tn >= total_tiles) break;
     __syncthreads();  // shared densities and coefficients are reused by the next tile
     t = tn;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
         mbar_expect_tx(&bar, sizeof(LatCoef<f2>));
       bulk_load(&cs[slot], coef + r.lat, sizeof(LatCoef<f2>), &bar);
     }
-    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, r.sx, r.x0, r.y0);
+    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, planes_strides(r.sx, r.ny), r.x0, r.y0);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     }
     float f[kTileRows][9];
     if (kind == kPlainLoad)
-      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, ti.sx, ti.x0, ti.y0, f, rs[buf]);
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), ti.x0,
+                                      ti.y0, f, rs[buf]);
     else  // read even after a failed wait (in bounds; the block then returns)
       window_tile(win, f, rs[buf]);
     if (__syncthreads_or(late)) {
@@ -181,8 +183,8 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
       return;
     }
     if (tn < total_tiles) issue(rec[buf ^ 1], buf ^ 1);
-    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, ti.sx, common, cs[buf], ti.x0, ti.y0,
-                                    rs[buf]);
+    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), common,
+                                    cs[buf], ti.x0, ti.y0, rs[buf]);
     buf ^= 1;
   }
 }
@@ -365,6 +367,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   for (int i = 0; i < n; ++i) {
     char err[512] = {0};
     if (ps[i].precision != LB_FP32) return bail(LB_ENOTSUP, "lb_batch_init: the batched solver stores FP32");
+    if (ps[i].layout != LB_LAYOUT_PLANES)
+      return bail(LB_ENOTSUP, "lb_batch_init: the batched solver stores the planes layout");
     if (derive(&ps[i], &b->d[i], err, sizeof(err)) != LB_OK) {
       char m[600];
       std::snprintf(m, sizeof(m), "lattice %d: %s", i, err);
@@ -472,8 +476,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const size_t N = size_t(ps[i].nx) * ps[i].ny;
     k_init_rest<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
-        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny, b->desc[0][i].sx,
-        h_coefd[i]);
+        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny,
+        planes_strides(b->desc[0][i].sx, ps[i].ny), h_coefd[i]);
     e = cudaGetLastError();
     node_off += N;
   }

@@ -162,16 +162,16 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
     if constexpr (sizeof(store_t) <= 4 && std::is_same<V, f2>::value) {
       if (h->use_tma) {
         k_step_tma<V, store_t, false><<<h->tma_grid, kFusedThreads, Win<store_t>::smem, h->stream>>>(
-            h->tmap[h->cur], fin, fout, nx, ny, cv, h->wait_error, rnd);
+            h->tmap[h->cur], fin, fout, nx, ny, h->st, cv, h->wait_error, rnd);
         return;
       }
     }
-    k_step_fused<V, store_t><<<grd, kFusedThreads, 0, h->stream>>>(fin, fout, nx, ny, cv, rnd);
+    k_step_fused<V, store_t><<<grd, kFusedThreads, 0, h->stream>>>(fin, fout, nx, ny, h->st, cv, rnd);
   } else {
     real* rho = static_cast<real*>(h->scratch);
     const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
-    k_density<real, store_t><<<grd, blk, 0, h->stream>>>(fin, rho, nx, ny);
-    k_collide_rho<real, store_t><<<grd, blk, 0, h->stream>>>(fin, fout, rho, nx, ny, c, rnd);
+    k_density<real, store_t><<<grd, blk, 0, h->stream>>>(fin, rho, nx, ny, h->st);
+    k_collide_rho<real, store_t><<<grd, blk, 0, h->stream>>>(fin, fout, rho, nx, ny, h->st, c, rnd);
   }
 }
 
@@ -194,9 +194,11 @@ namespace lbm {
 
 // 3-D map of one FP32 (elem_bytes 4) or FP16 (2) population buffer: x (nx), y (ny,
 // row stride sx), plane (9); box of one plane window (40 x 18 floats or 48 x 18
-// halves).  False if the layout does not allow it (base not 16-byte aligned, row
-// stride not a multiple of 16 bytes).
-bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes) {
+// halves).  Rows layout: x (nx), plane (9, stride nx), y (ny, stride 9 nx), box
+// (cols, 1, 18), which lands in shared memory as the same 18 x cols window.  False
+// if the layout does not allow it (base not 16-byte aligned, row stride not a
+// multiple of 16 bytes).
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes, bool rows) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -210,10 +212,10 @@ bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx,
   const size_t eb = size_t(elem_bytes);
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(sx) * eb) % 16 != 0 || sx < nx) return false;
   const int cols = elem_bytes == 4 ? Win<float>::cols : Win<__half>::cols;
-  if (nx < cols || ny < kTmaRows) return false;
-  const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), 9};
-  const cuuint64_t strides[2] = {cuuint64_t(sx) * eb, cuuint64_t(sx) * ny * eb};
-  const cuuint32_t box[3] = {cuuint32_t(cols), cuuint32_t(kTmaRows), 1};
+  if (nx < cols || ny < kTmaRows || (rows && sx != nx)) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(rows ? 9 : ny), cuuint64_t(rows ? ny : 9)};
+  const cuuint64_t strides[2] = {cuuint64_t(sx) * eb, cuuint64_t(sx) * (rows ? 9 : ny) * eb};
+  const cuuint32_t box[3] = {cuuint32_t(cols), rows ? 1u : cuuint32_t(kTmaRows), rows ? cuuint32_t(kTmaRows) : 1u};
   const cuuint32_t estride[3] = {1, 1, 1};
   const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   return fn(map, dt, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -244,6 +246,31 @@ __global__ void k_stream_soa(const T* __restrict__ in, T* __restrict__ out, long
   }
 }
 
+// The same for the rows layout f[y][i][x]: node (x, y)'s nine populations at
+// 9 nx y + nx i + x (nine row segments, each coalesced, next to one another).
+template <typename T>
+__global__ void k_stream_rows(const T* __restrict__ in, T* __restrict__ out, int nx, int ny) {
+  const unsigned N = unsigned(nx) * unsigned(ny), stride = gridDim.x * blockDim.x;
+  for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += stride) {
+    const unsigned y = n / unsigned(nx), o = n + 8u * unsigned(nx) * y;  // 9 nx y + x
+    T v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = in[o + i * nx];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[o + i * nx] = v[i];
+  }
+}
+
+template <typename T>
+void launch_stream_copy(const lb_handle* h, const void* in, void* out, unsigned grid) {
+  const T* src = static_cast<const T*>(in);
+  T* dst = static_cast<T*>(out);
+  if (h->p.layout == LB_LAYOUT_ROWS)
+    k_stream_rows<<<grid, 256, 0, h->stream>>>(src, dst, h->p.nx, h->p.ny);
+  else
+    k_stream_soa<<<grid, 256, 0, h->stream>>>(src, dst, (long long)h->p.nx * h->p.ny);
+}
+
 // A bounded wait that cannot succeed: the mbarrier's single arrival comes with 16
 // expected bytes that no copy delivers, so its phase never completes.  Every thread
 // polls it `polls` times, the block agrees through the barrier that the wait gave
@@ -266,11 +293,12 @@ int configure(lb_handle* h) {
   // bytes and a lattice holding at least one interior tile; otherwise the plain
   // fused kernel runs.
   const bool fp32 = h->p.precision == LB_FP32, fp16 = h->p.precision == LB_FP16S;
+  const bool rows = h->p.layout == LB_LAYOUT_ROWS;
   const int eb = fp32 ? 4 : 2, cols = fp32 ? Win<float>::cols : Win<__half>::cols;
   h->use_tma = (fp32 || fp16) && h->variant == LB_FUSED && (h->p.nx * eb) % 16 == 0 &&
                h->p.nx >= 2 * kTileX + cols && h->p.ny >= 2 * kTileY + kTmaRows &&
-               encode_population_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny, h->p.nx, eb) &&
-               encode_population_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny, h->p.nx, eb);
+               encode_population_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny, h->p.nx, eb, rows) &&
+               encode_population_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny, h->p.nx, eb, rows);
   if (h->use_tma) {
     void* w = nullptr;
     LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_error));
@@ -297,10 +325,10 @@ void launch_moments(lb_handle* h, real* rho, real* ux, real* uy, real rho_ref, r
   const store_t* f = static_cast<const store_t*>(h->f[h->cur]);
   const int nx = h->p.nx, ny = h->p.ny;
   const size_t N = size_t(nx) * ny;
-  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, rho_ref);
+  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, h->st, rho_ref);
   if (ux || uy) {
     const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
-    k_velocity<real, store_t><<<grd, blk, 0, h->stream>>>(f, rho, ux, uy, nx, ny, G2);
+    k_velocity<real, store_t><<<grd, blk, 0, h->stream>>>(f, rho, ux, uy, nx, ny, h->st, G2);
   }
 }
 
@@ -313,10 +341,10 @@ int run_reduce(lb_handle* h, double out[8]) {
   double* dout = partial + size_t(kMaxReduceBlocks) * kReduceSlots;
   const store_t* f = static_cast<const store_t*>(h->f[h->cur]);
   const real rho_ref = real(h->p.rho_ref);
-  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, rho_ref);
+  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, h->st, rho_ref);
   const double rho_mid = 0.5 * (h->d.rho_g + h->d.rho_l);
   k_reduce_partial<real, store_t><<<h->reduce_blocks, kReduceThreads, 0, h->stream>>>(
-      f, rho, nx, ny, real(h->d.G2), std::isfinite(rho_mid) ? rho_mid : 1e300, partial);
+      f, rho, nx, ny, h->st, real(h->d.G2), std::isfinite(rho_mid) ? rho_mid : 1e300, partial);
   k_reduce_final<<<1, 32, 0, h->stream>>>(partial, h->reduce_blocks, dout);
   double res[kReduceSlots];
   real probe[2];
@@ -349,7 +377,7 @@ int run_reduce(lb_handle* h, double out[8]) {
 
 extern "C" {
 
-int lb_abi_version(void) { return 1; }
+int lb_abi_version(void) { return 2; }
 
 int lb_derive(const lb_params* p, lb_derived* out) {
   if (!out) return fail(nullptr, LB_EINVAL, "null output");
@@ -409,6 +437,7 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   h->stream = static_cast<cudaStream_t>(stream);
   h->steps = 0;
   h->variant = variant;
+  h->st = p->layout == LB_LAYOUT_ROWS ? rows_strides(p->nx) : planes_strides(p->nx, p->ny);
   h->cf = make_vcoef<float>(h->p, d);
   h->c2 = make_vcoef<f2>(h->p, d);
   h->cd = make_vcoef<double>(h->p, d);
@@ -433,9 +462,18 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   }
   const unsigned blocks = unsigned((N + 255) / 256);
   switch (p->precision) {
-    case LB_FP64: k_init_rest<double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny, p->nx, h->cd); break;
-    case LB_FP32: k_init_rest<float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, p->nx, h->cd); break;
-    default: k_init_rest<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny, p->nx, h->cd); break;
+    case LB_FP64:
+      k_init_rest<double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny, h->st,
+                                                        h->cd);
+      break;
+    case LB_FP32:
+      k_init_rest<float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, h->st,
+                                                       h->cd);
+      break;
+    default:
+      k_init_rest<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny, h->st,
+                                                        h->cd);
+      break;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return bail(e, "init kernel launch");
@@ -491,13 +529,13 @@ int lb_pressure(lb_handle* h, void* p) {
   const void* f = h->f[h->cur];
   if (h->p.precision == LB_FP64)
     k_pressure<double, double><<<blocks, 256, 0, h->stream>>>(static_cast<const double*>(f), static_cast<double*>(p),
-                                                              h->p.nx, h->p.ny, h->cd);
+                                                              h->p.nx, h->p.ny, h->st, h->cd);
   else if (h->p.precision == LB_FP32)
     k_pressure<float, float><<<blocks, 256, 0, h->stream>>>(static_cast<const float*>(f), static_cast<float*>(p),
-                                                            h->p.nx, h->p.ny, h->cf);
+                                                            h->p.nx, h->p.ny, h->st, h->cf);
   else
     k_pressure<float, __half><<<blocks, 256, 0, h->stream>>>(static_cast<const __half*>(f), static_cast<float*>(p),
-                                                             h->p.nx, h->p.ny, h->cf);
+                                                             h->p.nx, h->p.ny, h->st, h->cf);
   LB_CUDA(h, cudaGetLastError());
   return LB_OK;
 }
@@ -555,7 +593,6 @@ int lb_wait_selftest(lb_handle* h, long long polls) {
 
 int lb_stream_copy(lb_handle* h) {
   if (!h) return fail(nullptr, LB_EINVAL, "null handle");
-  const long long N = (long long)h->p.nx * h->p.ny;
   int dev = 0, sms = 0;
   LB_CUDA(h, cudaGetDevice(&dev));
   LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -563,14 +600,9 @@ int lb_stream_copy(lb_handle* h) {
   void* out = h->f[1 - h->cur];
   const unsigned grid = unsigned(sms * 8);
   switch (h->p.precision) {
-    case LB_FP64:
-      k_stream_soa<<<grid, 256, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), N);
-      break;
-    case LB_FP32:
-      k_stream_soa<<<grid, 256, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), N);
-      break;
-    default:
-      k_stream_soa<<<grid, 256, 0, h->stream>>>(static_cast<const __half*>(in), static_cast<__half*>(out), N);
+    case LB_FP64: launch_stream_copy<double>(h, in, out, grid); break;
+    case LB_FP32: launch_stream_copy<float>(h, in, out, grid); break;
+    default: launch_stream_copy<__half>(h, in, out, grid);
   }
   LB_CUDA(h, cudaGetLastError());
   h->cur = 1 - h->cur;  // same data in the other buffer: the state is unchanged

@@ -17,10 +17,11 @@ struct lb_handle {
   int64_t steps;
   int variant;  // LB_FUSED or LB_TWO_PASS
   int reduce_blocks;
+  lbm::Strides st;        // population layout (planes or rows)
   bool use_tma;           // FP32 fused step with tensor-copy staging (interior tiles)
   int tma_grid;           // persistent grid of that kernel
   int tma_grid_auto;      // its default: resident capacity, at most the tile count
-  CUtensorMap tmap[2];    // 3-D maps (x, y, plane) of f[0] and f[1]
+  CUtensorMap tmap[2];    // 3-D maps of f[0] and f[1]: (x, y, plane), rows layout (x, plane, y)
   int* wait_error;        // device word set by a bounded wait that gave up
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
   lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
@@ -29,8 +30,10 @@ struct lb_handle {
 };
 
 namespace lbm {
-// 3-D tensor map (x, y, plane) of an FP32 (elem_bytes 4) or FP16 (2) population
-// buffer with row stride sx, box = one plane window of the tensor-copy step; false
-// if the layout does not allow one (lbm_capi.cu).
-bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes = 4);
+// 3-D tensor map of an FP32 (elem_bytes 4) or FP16 (2) population buffer, box =
+// one plane window of the tensor-copy step: dimensions (x, y, plane) with row
+// stride sx, or (x, plane, y) for the rows layout (sx = nx); false if the layout
+// does not allow one (lbm_capi.cu).
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes = 4,
+                           bool rows = false);
 }  // namespace lbm

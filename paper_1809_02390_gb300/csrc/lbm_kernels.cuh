@@ -11,6 +11,17 @@ constexpr int kFusedThreads = 256;  // 8 warps; each warp owns a 32-column strip
 constexpr int kReduceThreads = 256;
 constexpr int kReduceSlots = 8;     // doubles per block partial
 
+// Where population i of node (x, y) lives: f[i * ps + y * rs + x].  Planes layout
+// f[9][ny][sx] (sx = nx, or the batched pools' padded row stride): ps = sx ny,
+// rs = sx; rows layout f[ny][9][nx] (a row's nine planes side by side): ps = nx,
+// rs = 9 nx.  32-bit offsets: the library limits 9 nx ny to below 2^31.
+struct Strides {
+  int ps, rs;
+  __host__ __device__ int at(int i, int x, int y) const { return i * ps + y * rs + x; }
+};
+__host__ __device__ inline Strides planes_strides(int sx, int ny) { return Strides{sx * ny, sx}; }
+__host__ __device__ inline Strides rows_strides(int nx) { return Strides{nx, 9 * nx}; }
+
 __host__ __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -20,9 +31,9 @@ __host__ __device__ __forceinline__ int wrap(int v, int n) {
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // Pulls the nine populations of row r at columns (cm, cc, cp) = (x-1, x, x+1):
-// f_i(x, r) = fbar_i(x - e_i, r - e_i) (supplement Eq. 2), periodic.  sx: row
-// stride in elements (nx, or nx rounded up in the batched pools).  32-bit
-// offsets: the library limits 9 sx ny to below 2^31.
+// f_i(x, r) = fbar_i(x - e_i, r - e_i) (supplement Eq. 2), periodic.  plane, sx:
+// the population and row strides in elements (Strides ps, rs).  32-bit offsets:
+// the library limits the buffer to below 2^31 elements.
 template <typename real, typename store_t>
 __device__ __forceinline__ void pull_row(const store_t* __restrict__ fin, int plane, int sx, int ny, int r, int cm,
                                          int cc, int cp, real (&f)[9]) {
@@ -77,14 +88,13 @@ struct TileShape {
 // densities, collision (one packed FP32x2 evaluation for V = f2), store.
 template <typename V, typename store_t, int TY>
 __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
-                                             store_t* __restrict__ fout, int nx, int ny, int sx, const VCoef<V>& c,
+                                             store_t* __restrict__ fout, int nx, int ny, Strides st, const VCoef<V>& c,
                                              const LatCoef<V>& l, int x0, int y0,
                                              const typename LaneType<V>::type (*rs)[kTileX + 2],
                                              Rounding rnd = Rounding{0u, 0}) {
   using real = typename LaneType<V>::type;
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int plane = sx * ny;
   const int gx = x0 + tx;
   real out[kTileRows][9];
   if constexpr (Lanes<V>::n == 2) {
@@ -122,8 +132,8 @@ __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&
   for (int k = 0; k < kTileRows; ++k) {
     const int gy = y0 + ty + k * Shape::stride;
     if (gx < nx && gy < ny) {
-      const int off = gy * sx + gx;
-      store9(fout + off, plane, out[k], unsigned(off), rnd);
+      const int off = gy * st.rs + gx;
+      store9(fout + off, st.ps, out[k], unsigned(gy * nx + gx), rnd);
     }
   }
 }
@@ -134,14 +144,13 @@ struct NoHook {
 
 // Phase 1 of a tile with plain loads: pulls the populations of the thread's two
 // nodes into f and writes the densities of tile + ring to rs (shared array of
-// (TY + 2) x (TX + 2) densities).  (x0, y0): tile origin; sx: row stride.
+// (TY + 2) x (TX + 2) densities).  (x0, y0): tile origin; st: the layout.
 // Periodic wrap.
 template <typename real, typename store_t, int TY>
-__device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int nx, int ny, int sx, int x0, int y0,
-                                          real (&f)[kTileRows][9], real (*rs)[kTileX + 2]) {
+__device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int nx, int ny, Strides st, int x0,
+                                          int y0, real (&f)[kTileRows][9], real (*rs)[kTileX + 2]) {
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int plane = sx * ny;
   const bool small = nx <= kTileX || ny <= TY;  // tiles may wrap more than once
   const int gx = x0 + tx;
   const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
@@ -149,7 +158,7 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
     const int gy = y0 + ty + k * Shape::stride;
-    pull_row(fin, plane, sx, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
+    pull_row(fin, st.ps, st.rs, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
   }
   // Ring: the row above, the row below, then the left and right columns.
   const int t = threadIdx.x;
@@ -168,7 +177,7 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
     }
     const int hx = small ? wrap(x0 - 1 + wx, nx) : wrap1(x0 - 1 + wx, nx);
     const int hy = small ? wrap(y0 - 1 + wy, ny) : wrap1(y0 - 1 + wy, ny);
-    pull_row(fin, plane, sx, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
+    pull_row(fin, st.ps, st.rs, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
   }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
@@ -180,47 +189,47 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
 // barrier (the batched kernel stores its lattice coefficients there).
 template <typename V, typename store_t, int TY, typename Hook = NoHook>
 __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
-                                          int ny, int sx, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
+                                          int ny, Strides st, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
                                           typename LaneType<V>::type (*rs)[kTileX + 2],
                                           const Hook& before_sync = Hook(), Rounding rnd = Rounding{0u, 0}) {
   using real = typename LaneType<V>::type;
   real f[kTileRows][9];
-  load_tile<real, store_t, TY>(fin, nx, ny, sx, x0, y0, f, rs);
+  load_tile<real, store_t, TY>(fin, nx, ny, st, x0, y0, f, rs);
   before_sync();
   __syncthreads();
-  collide_tile<V, store_t, TY>(f, fout, nx, ny, sx, c, l, x0, y0, rs, rnd);
+  collide_tile<V, store_t, TY>(f, fout, nx, ny, st, c, l, x0, y0, rs, rnd);
 }
 
 template <typename V, typename store_t>
 __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
-    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, VCoef<V> c,
-                 Rounding rnd) {
+    k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, Strides st,
+                 VCoef<V> c, Rounding rnd) {
   __shared__ typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
-  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, nx, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
+  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, st, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
                                 rs, NoHook(), rnd);
 }
 
 // Two-pass variant, pass 1: density plane rho_dev(x) = sum_i fbar_i(x - e_i).
 template <typename real, typename store_t>
-__global__ void k_density(const store_t* __restrict__ fin, real* __restrict__ rho, int nx, int ny) {
+__global__ void k_density(const store_t* __restrict__ fin, real* __restrict__ rho, int nx, int ny, Strides st) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   real f[9];
-  pull_row(fin, nx * ny, nx, ny, y, x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1, f);
+  pull_row(fin, st.ps, st.rs, ny, y, x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1, f);
   rho[y * nx + x] = sum9(f);
 }
 
 // Two-pass variant, pass 2: pull, force stencil from the density plane, collide.
 template <typename real, typename store_t>
 __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restrict__ fout,
-                              const real* __restrict__ rho, int nx, int ny, VCoef<real> c, Rounding rnd) {
+                              const real* __restrict__ rho, int nx, int ny, Strides st, VCoef<real> c,
+                              Rounding rnd) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const int plane = nx * ny;
   real f[9];
-  pull_row(fin, plane, nx, ny, y, xm, x, xp, f);
+  pull_row(fin, st.ps, st.rs, ny, y, xm, x, xp, f);
   const real* rm = rho + ym * nx;
   const real* rc = rho + y * nx;
   const real* rpp = rho + yp * nx;
@@ -229,19 +238,18 @@ __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restri
           __ldg(rpp + x), __ldg(rpp + xp), Sx, Sy);
   real o[9];
   collide(c, f, Sx, Sy, o);
-  const int off = y * nx + x;
-  store9(fout + off, plane, o, unsigned(off), rnd);
+  store9(fout + st.at(0, x, y), st.ps, o, unsigned(y * nx + x), rnd);
 }
 
 // Rest equilibrium from an initial density (computed in FP64, rounded once):
 // m_eq(rho, u = 0) = (rho, -2 rho + 2 eta, rho + beta_2 eta, 0, ...), minus rho_ref M w.
 template <typename store_t>
-__global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny, int sx,
+__global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny, Strides st,
                             VCoef<double> c) {
   const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= size_t(nx) * ny) return;
-  const size_t N = size_t(sx) * ny;                            // plane stride
-  const size_t n = (k / nx) * size_t(sx) + k % nx;             // node (x, y) at row stride sx
+  const size_t N = size_t(st.ps);                                    // plane stride
+  const size_t n = size_t(st.at(0, int(k % nx), int(k / nx)));        // node (x, y)
   const double rho = rho0[k];
   double pe, dpe;
   eos(c, rho, pe, dpe);
@@ -263,25 +271,27 @@ __global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict
 
 // rho = sum_i fbar_i + rho_ref at every node (no pull: the stored state is post-collision).
 template <typename real, typename store_t>
-__global__ void k_rho_local(const store_t* __restrict__ f, real* __restrict__ rho, int nx, int ny, real rho_ref) {
+__global__ void k_rho_local(const store_t* __restrict__ f, real* __restrict__ rho, int nx, int ny, Strides st,
+                            real rho_ref) {
   const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const size_t N = size_t(nx) * ny;
-  if (n >= N) return;
+  if (n >= size_t(nx) * ny) return;
+  const int y = int(n / nx), o = st.at(0, int(n - size_t(y) * nx), y);
   real s = 0;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) s += ld_st(f + i * N + n);
+  for (int i = 0; i < 9; ++i) s += ld_st(f + (o + i * st.ps));
   rho[n] = s + rho_ref;
 }
 
 // p_EOS / c^2 at every node from rho = sum_i fbar_i + rho_ref (Eq. 20 or vdW, times K_EOS).
 template <typename real, typename store_t>
-__global__ void k_pressure(const store_t* __restrict__ f, real* __restrict__ p, int nx, int ny, VCoef<real> c) {
+__global__ void k_pressure(const store_t* __restrict__ f, real* __restrict__ p, int nx, int ny, Strides st,
+                           VCoef<real> c) {
   const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const size_t N = size_t(nx) * ny;
-  if (n >= N) return;
+  if (n >= size_t(nx) * ny) return;
+  const int y = int(n / nx), o = st.at(0, int(n - size_t(y) * nx), y);
   real s = 0;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) s += ld_st(f + i * N + n);
+  for (int i = 0; i < 9; ++i) s += ld_st(f + (o + i * st.ps));
   real pe, dpe;
   eos(c, s + c.rho_ref, pe, dpe);
   p[n] = pe;
@@ -290,15 +300,15 @@ __global__ void k_pressure(const store_t* __restrict__ f, real* __restrict__ p, 
 // rho u = sum_i e_i fbar_i - F/2 with F from the density plane.
 template <typename real, typename store_t>
 __global__ void k_velocity(const store_t* __restrict__ f, const real* __restrict__ rho, real* __restrict__ ux,
-                           real* __restrict__ uy, int nx, int ny, real G2) {
+                           real* __restrict__ uy, int nx, int ny, Strides st, real G2) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const size_t N = size_t(nx) * ny, n = size_t(y) * nx + x;
+  const size_t n = size_t(y) * nx + x;
   real d[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) d[i] = ld_st(f + i * N + n);
+  for (int i = 0; i < 9; ++i) d[i] = ld_st(f + st.at(i, x, y));
   real Sx, Sy;
   stencil(rho[size_t(ym) * nx + xm], rho[size_t(ym) * nx + x], rho[size_t(ym) * nx + xp], rho[n - x + xm],
           rho[n - x + xp], rho[size_t(yp) * nx + xm], rho[size_t(yp) * nx + x], rho[size_t(yp) * nx + xp], Sx,
@@ -330,8 +340,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // non-finite count.  rho: density plane (full density).
 template <typename real, typename store_t>
 __global__ void __launch_bounds__(kReduceThreads)
-    k_reduce_partial(const store_t* __restrict__ f, const real* __restrict__ rho, int nx, int ny, real G2,
-                     double rho_mid, double* __restrict__ partial) {
+    k_reduce_partial(const store_t* __restrict__ f, const real* __restrict__ rho, int nx, int ny, Strides st,
+                     real G2, double rho_mid, double* __restrict__ partial) {
   const size_t N = size_t(nx) * ny;
   double acc[kReduceSlots] = {0, 0, 0, 0, 1e300, -1e300, 0, 0};
   for (size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += size_t(gridDim.x) * blockDim.x) {
@@ -340,7 +350,7 @@ __global__ void __launch_bounds__(kReduceThreads)
     const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
     real d[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) d[i] = ld_st(f + i * N + n);
+    for (int i = 0; i < 9; ++i) d[i] = ld_st(f + st.at(i, x, y));
     real Sx, Sy;
     stencil(rho[size_t(ym) * nx + xm], rho[size_t(ym) * nx + x], rho[size_t(ym) * nx + xp], rho[n - x + xm],
             rho[n - x + xp], rho[size_t(yp) * nx + xm], rho[size_t(yp) * nx + x], rho[size_t(yp) * nx + xp],

@@ -73,10 +73,11 @@ int reduce_static(lb_handle* h, unsigned char* base, double out[8]) {
   double* dout = reinterpret_cast<double*>(base + kPlaneBytes + kPartialBytes);
   const store_t* f = static_cast<const store_t*>(h->f[h->cur]);
   const int blocks = h->reduce_blocks < kStaticBlocks ? h->reduce_blocks : kStaticBlocks;
-  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, real(h->p.rho_ref));
+  k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, h->st,
+                                                                                real(h->p.rho_ref));
   const double rho_mid = 0.5 * (h->d.rho_g + h->d.rho_l);
   k_reduce_partial<real, store_t><<<blocks, kReduceThreads, 0, h->stream>>>(
-      f, rho, nx, ny, real(h->d.G2), rho_mid == rho_mid ? rho_mid : 1e300, partial);
+      f, rho, nx, ny, h->st, real(h->d.G2), rho_mid == rho_mid ? rho_mid : 1e300, partial);
   k_reduce_final<<<1, 32, 0, h->stream>>>(partial, blocks, dout);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(h, LB_ECUDA, "reduce kernels", e);

@@ -192,6 +192,8 @@ int derive(const lb_params* p, lb_derived* d, char* err, size_t errlen) {
   if (9 * (int64_t)p->nx * p->ny >= ((int64_t)1 << 31)) return fail("lattice too large: 9 nx ny must be below 2^31");
   if (p->precision < LB_FP64 || p->precision > LB_FP16S) return fail("unknown precision");
   if (p->rounding != LB_ROUND_STOCHASTIC && p->rounding != LB_ROUND_NEAREST) return fail("unknown rounding");
+  if (p->layout != LB_LAYOUT_PLANES && p->layout != LB_LAYOUT_ROWS) return fail("unknown layout");
+  if (p->reserved1 != 0) return fail("reserved field must be 0");
   if (p->eos != LB_EOS_VDW && p->eos != LB_EOS_CS) return fail("unknown eos");
   if (p->variant < LB_AUTO || p->variant > LB_TWO_PASS) return fail("unknown variant");
   if (!(p->eos_a > 0) || !(p->eos_b > 0) || !(p->R_gas > 0)) return fail("eos_a, eos_b, R_gas must be > 0");

@@ -11,7 +11,8 @@
 // requires) and covers the columns x0 - 2 .. x0 + 33 that any direction reads.
 // FP16 storage uses 48 x 18 windows from x0 - 8 (16 bytes of halves).  Tiles
 // whose window would leave the lattice (the periodic wrap) take the plain loads
-// of load_tile.
+// of load_tile.  Rows layout (f[y][i][x]): the map's dimensions are (x, plane, y)
+// and the same windows arrive in the same shared-memory arrangement.
 #pragma once
 
 #include <cuda.h>
@@ -175,25 +176,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // All threads: the window of the (wrapping) tile at (x0, y0) of a lattice with
-// populations at fin (row stride sx) into win.  Plane i's window row r holds
+// populations at fin (layout st) into win.  Plane i's window row r holds
 // lattice row y0 - 1 - e_iy + r, window column c lattice column x0 - 4 + c.
 __device__ __forceinline__ void issue_window_async(float* win, const float* __restrict__ fin, int nx, int ny,
-                                                   int sx, int x0, int y0) {
+                                                   Strides st, int x0, int y0) {
   const int j = threadIdx.x;
   if (j < kAsyncThreads) {
     const int c = j % kTmaCols, r0 = j / kTmaCols;
     const int gx = wrap1(x0 - 4 + c, nx);
-    const int plane = sx * ny;
-    int src[kTmaRows / 6][3];  // [pass][e_iy + 1]: offset of the source cell within a plane
+    int src[kTmaRows / 6][3];  // [pass][e_iy + 1]: offset of the source cell of population 0
 #pragma unroll
     for (int q = 0; q < kTmaRows / 6; ++q)
 #pragma unroll
-      for (int e = 0; e < 3; ++e) src[q][e] = wrap1(y0 - e + r0 + 6 * q, ny) * sx + gx;
+      for (int e = 0; e < 3; ++e) src[q][e] = wrap1(y0 - e + r0 + 6 * q, ny) * st.rs + gx;
 #pragma unroll
     for (int i = 0; i < 9; ++i)
 #pragma unroll
       for (int q = 0; q < kTmaRows / 6; ++q)
-        cp_async4(win + i * kTmaPlane + (r0 + 6 * q) * kTmaCols + c, fin + (i * plane + src[q][ey_of(i) + 1]));
+        cp_async4(win + i * kTmaPlane + (r0 + 6 * q) * kTmaCols + c, fin + (i * st.ps + src[q][ey_of(i) + 1]));
   }
   cp_async_commit();
 }
@@ -231,14 +231,17 @@ __device__ __forceinline__ void window_tile(const S* __restrict__ win, float (&f
 }
 
 // The nine copies of the interior tile at (x0, y0) into win, completing on bar
-// (one thread).
+// (one thread).  rows: the map's dimensions are (x, plane, y) instead of (x, y, plane).
 template <typename S>
 __device__ __forceinline__ void issue_windows(S* win, const CUtensorMap* map, int x0, int y0,
-                                              unsigned long long* bar, unsigned extra_bytes = 0) {
+                                              unsigned long long* bar, unsigned extra_bytes = 0, bool rows = false) {
   using W = Win<S>;
   mbar_expect_tx(bar, W::bytes + extra_bytes);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) tma_load_3d(win + i * W::plane, map, x0 - W::xoff, y0 - 1 - ey_of(i), i, bar);
+  for (int i = 0; i < 9; ++i) {
+    const int wy = y0 - 1 - ey_of(i);
+    tma_load_3d(win + i * W::plane, map, x0 - W::xoff, rows ? i : wy, rows ? wy : i, bar);
+  }
 }
 
 // How a tile's window is staged: by tensor copies (interior), by per-thread
@@ -269,7 +272,7 @@ __device__ __forceinline__ int tile_kind(int x0, int y0, int nx, int ny) {
 template <typename V, typename S, bool ASYNC_EDGES>
 __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     k_step_tma(const __grid_constant__ CUtensorMap tin, const S* __restrict__ fin, S* __restrict__ fout, int nx,
-               int ny, VCoef<V> c, int* __restrict__ err, Rounding rnd) {
+               int ny, Strides st, VCoef<V> c, int* __restrict__ err, Rounding rnd) {
   static_assert(!ASYNC_EDGES || sizeof(S) == 4, "asynchronous edge windows exist for FP32 storage only");
   using real = float;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -278,6 +281,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   __shared__ __align__(8) unsigned long long bar;
   const int tiles_x = (nx + kTileX - 1) / kTileX;
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
+  const bool rows = st.ps == nx;  // rows layout (the planes one has ps = nx ny, ny >= 50 here)
   // Tile t sits at column t mod tiles_x, row t / tiles_x; the walk t -> t + G
   // advances the origin by a fixed step (two divisions per block, none per tile).
   const int step_r = gridDim.x / tiles_x, step_c = gridDim.x - step_r * tiles_x;
@@ -296,9 +300,9 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     const int kind = tile_kind<ASYNC_EDGES, S>(x0, y0, nx, ny);
     if (kind == kTensorCopy && threadIdx.x == 0) {
       fence_proxy_async();
-      issue_windows(win, &tin, x0, y0, &bar);
+      issue_windows(win, &tin, x0, y0, &bar, 0, rows);
     } else if (kind == kAsyncCopy) {
-      if constexpr (ASYNC_EDGES) issue_window_async(win, fin, nx, ny, nx, x0, y0);
+      if constexpr (ASYNC_EDGES) issue_window_async(win, fin, nx, ny, st, x0, y0);
     }
   };
   if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -320,7 +324,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       __syncthreads();
     }
     if (kind == kPlainLoad)
-      load_tile<real, S, kTileY>(fin, nx, ny, nx, x0, y0, f, rs[buf]);
+      load_tile<real, S, kTileY>(fin, nx, ny, st, x0, y0, f, rs[buf]);
     else  // read even after a failed wait (in bounds; the block then returns)
       window_tile(win, f, rs[buf]);
     // The window is consumed and the densities are in place.  A wait that gave up
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     }
     advance(tc, tr);
     if (t + gridDim.x < total) issue(tc, tr);
-    collide_tile<V, S, kTileY>(f, fout, nx, ny, nx, c, lattice_part(c), x0, y0, rs[buf], rnd);
+    collide_tile<V, S, kTileY>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[buf], rnd);
     buf ^= 1;
   }
 }

@@ -44,9 +44,10 @@ def test_library_exports_every_declared_symbol(capi):
 
 
 def test_abi_struct_sizes(capi):
-    assert ctypes.sizeof(capi.lb_params) == 6 * 4 + 16 * 8
+    assert ctypes.sizeof(capi.lb_params) == 8 * 4 + 16 * 8
+    assert capi.lb_params.layout.offset == 6 * 4 + 16 * 8
     assert ctypes.sizeof(capi.lb_derived) == 20 * 8
-    assert capi.lib().lb_abi_version() == 1
+    assert capi.lib().lb_abi_version() == 2
 
 
 @pytest.mark.parametrize("eos,a,b,Tr,K_int", [("vdw", 9 / 49, 2 / 21, 0.85, 1.0), ("vdw", 9 / 49, 2 / 21, 0.7, 1.7),
@@ -69,7 +70,7 @@ def test_derived_parameters_match_oracle(capi, eos, a, b, Tr, K_int):
 @pytest.mark.parametrize("field,value,needle", [
     ("nx", 2, "nx and ny"), ("varpi", 1.0, "varpi"), ("varpi", 1 / 3, "varpi"), ("s_p", 2.0, "s_p"),
     ("s_p", 0.0, "s_p"), ("eos", 7, "eos"), ("precision", 5, "precision"), ("Tr", 1.2, "coexistence"),
-    ("eos_b", -1.0, "eos_a"), ("s_q", 2.5, "rates")])
+    ("eos_b", -1.0, "eos_a"), ("s_q", 2.5, "rates"), ("layout", 2, "layout"), ("reserved1", 1, "reserved")])
 def test_invalid_parameters_are_rejected(capi, field, value, needle):
     p = capi.make_params(64, 64)
     setattr(p, field, value)
@@ -103,3 +104,16 @@ def test_sizes(capi):
     p.precision = capi.LB_FP64
     assert capi.lb_state_bytes(p) == 9 * 100 * 30 * 8
     assert capi.lb_scratch_bytes(p) >= 100 * 30 * 8
+
+
+def test_batch_rejects_rows_layout_before_any_gpu_work(capi):
+    """The batched solver stores the planes layout: a lattice in the rows layout is
+    refused with LB_ENOTSUP on the host (the buffers are never touched)."""
+    import numpy as np
+
+    ps = (capi.lb_params * 2)(capi.make_params(64, 64), capi.make_params(64, 64, layout=capi.LB_LAYOUT_ROWS))
+    rho = np.full(2 * 64 * 64, 2.0)
+    b = ctypes.c_void_p()
+    meta = capi.lib().lb_batch_meta_bytes(ps, 2)
+    rc = capi.lib().lb_batch_init(ctypes.byref(b), ps, 2, 1 << 40, 2 << 40, 3 << 40, meta, rho.ctypes.data, 0, None)
+    assert rc == capi.LB_ENOTSUP and "planes layout" in capi.lb_last_error(None)
