@@ -183,8 +183,48 @@ def cpu_baseline(rho0, seconds: float = 12.0) -> dict:
         f = oracle.step(p, f, 10)
         steps += 10
     dt = time.perf_counter() - t0
-    return {"value": round(256 * 256 * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of the FP64 oracle on a 256x256 periodic crop of the workload" % steps}
+    out = {"value": round(256 * 256 * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": "%d steps of the FP64 oracle on a 256x256 periodic crop of the workload" % steps}
+    out["all_cores"] = cpu_baseline_all_cores(rho0, seconds=0.75 * seconds)
+    return out
+
+
+def _oracle_rate(job):
+    """One oracle process: steps its crop for about `seconds`; returns
+    (node updates, seconds).  Module-level so that spawned workers can import it."""
+    crop, seconds = job
+    import oracle
+    from oracle import params as op
+
+    p = op.from_physical(Tr=TR)
+    f = oracle.init_feq(p, crop)
+    f = oracle.step(p, f, 2)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        f = oracle.step(p, f, 10)
+        steps += 10
+    return crop.size * steps, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(rho0, seconds: float = 9.0) -> dict:
+    """The same oracle on every host core at once: one process per core (spawned:
+    CUDA is initialised in this process), each on its own 256 x 256 crop of the
+    workload; the throughput is the sum of the processes' rates over overlapping
+    windows of about `seconds`."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    gy, gx = max(1, rho0.shape[0] // 256), max(1, rho0.shape[1] // 256)
+    crops = [np.ascontiguousarray(rho0[256 * ((k // gx) % gy):][:256, 256 * (k % gx):][:, :256]) for k in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map_async(_oracle_rate, [(c, seconds) for c in crops]).get(timeout=120 + 4 * seconds)
+    rate = sum(u / t for u, t in res) / 1e6
+    return {"value": round(rate, 3), "unit": "MLUPS", "cores": n, "kind": "oracle",
+            "sample": "%d single-threaded oracle processes, one per core, each ~%.0f s on its own 256x256 crop"
+                      % (n, seconds)}
 
 
 def measure_adjoint(n: int, torch) -> dict:
