@@ -510,7 +510,10 @@ def run_ours(args):
 
     # --- main measurement: FP32 fused, inputs resident in HBM -----------------
     lat = Lattice(rho0, precision="fp32", variant="fused", Tr=TR, layout=args.layout)
-    kernel = "k_step_tma<f2>" if capi.lb_uses_tma(lat.h) else "k_step_fused<f2,float>"
+    if args.dispatch == "static" and capi.lb_tile_dispatch(lat.h):
+        capi.lb_set_tile_dispatch(lat.h, False)
+    kernel = ("k_step_tma_dyn<f2>" if capi.lb_tile_dispatch(lat.h) else "k_step_tma<f2>") if capi.lb_uses_tma(lat.h) \
+        else "k_step_fused<f2,float>"
     lat.step(args.warmup)
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -538,21 +541,25 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if args.only_main:
         if rank == 0:
-            print(json.dumps({"only_main": True, "size": n, "layout": args.layout, "MLUPS": round(value, 1),
-                              "ms_per_step": ms_step, "pattern_GBps": round(pattern_gbs, 1)}))
+            print(json.dumps({"only_main": True, "size": n, "layout": args.layout, "kernel": kernel,
+                              "MLUPS": round(value, 1), "ms_per_step": ms_step, "pattern_GBps": round(pattern_gbs, 1)}))
         return
 
     # --- other variants / precisions (shorter runs, same workload) -------------
     variants = {}
     other = "planes" if args.layout == "rows" else "rows"
     quarter = max(50, args.steps // 4)
-    for prec, var, lay, k in (("fp32", "fused", other, quarter), ("fp32", "two_pass", args.layout, quarter),
-                              ("fp16s", "fused", args.layout, quarter), ("fp16s", "fused", other, quarter),
-                              ("fp64", "fused", args.layout, 30)):
+    for prec, var, lay, k, static in (("fp32", "fused", other, quarter, False),
+                                      ("fp32", "fused", args.layout, quarter, True),
+                                      ("fp32", "two_pass", args.layout, quarter, False),
+                                      ("fp16s", "fused", args.layout, quarter, False),
+                                      ("fp16s", "fused", other, quarter, False), ("fp64", "fused", args.layout, 30, False)):
         lt = Lattice(rho0, precision=prec, variant=var, Tr=TR, layout=lay)
+        if static:  # the static tile walk of the tensor-copy step, for comparison
+            capi.lb_set_tile_dispatch(lt.h, False)
         lt.step(3)
         m = time_steps(lt, k, torch) / k
-        variants["%s_%s_%s" % (prec, var, lay)] = {
+        variants["%s_%s_%s%s" % (prec, var, lay, "_static_tiles" if static else "")] = {
             "MLUPS": round(nodes / (m * 1e-3) / 1e6, 1), "ms_per_step": round(m, 4),
             "algorithmic_GBps": round(BYTES_PER_LU[prec] * nodes / (m * 1e-3) / 1e9, 1)}
         lt.close()
@@ -636,6 +643,8 @@ def main():
     ap.add_argument("--precision-steps", type=int, default=20000, help="steps of the precision study")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint, batch and calibration runs")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the 256-lattice batch run")
+    ap.add_argument("--dispatch", choices=["dynamic", "static"], default="dynamic",
+                    help="tile dispatch of the tensor-copy step (tickets, or the static walk)")
     ap.add_argument("--layout", choices=["planes", "rows"], default="rows",
                     help="population layout of the timed lattice (the other one is timed as a variant)")
     args = ap.parse_args()

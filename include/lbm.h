@@ -126,8 +126,8 @@ int lb_derive(const lb_params* p, lb_derived* out);
 /* Bytes of one population buffer: 9 * nx * ny * element size. */
 size_t lb_state_bytes(const lb_params* p);
 
-/* Bytes of device scratch memory the step needs (0 for the fused variant, one
- * density plane for the two-pass variant) plus the reduction workspace. */
+/* Bytes of device scratch memory: one density plane (two-pass variant, reductions),
+ * the reduction workspace and 256 bytes of tile tickets (fused tensor-copy step). */
 size_t lb_scratch_bytes(const lb_params* p);
 
 /* Creates a handle bound to the caller's buffers and stream and initialises the
@@ -298,6 +298,16 @@ int lb_wait_selftest(lb_handle* h, long long polls);
  * FP32 storage with nx a multiple of 4 and nx >= 104, or FP16 storage with nx a
  * multiple of 8 and nx >= 112; ny >= 50.  Else 0. */
 int lb_uses_tma(const lb_handle* h);
+
+/* How the tensor-copy step hands tiles to its persistent blocks.  1 (the default
+ * when the handle has its scratch buffer): by ticket, one atomic add on a counter
+ * in the scratch buffer per tile, so the tiles in flight are always the next ones
+ * in row-major order across the grid, with two tiles' windows in flight per
+ * block; 0: each block walks tiles b, b + grid, ... with one window in flight.
+ * Results are the same bit for bit.  lb_set_tile_dispatch returns LB_ENOTSUP for
+ * 1 when the step does not use tensor copies or the handle has no scratch. */
+int lb_set_tile_dispatch(lb_handle* h, int dynamic);
+int lb_tile_dispatch(const lb_handle* h);
 
 /* Measurement aid (no counterpart in the paper): one pass with the step's memory
  * traffic and none of its arithmetic, a copy of the state into the other buffer

@@ -92,6 +92,8 @@ SIGNATURES = [
     ("lb_stream_copy", ctypes.c_int, [_V]),
     ("lb_pressure", ctypes.c_int, [_V, _V]),
     ("lb_uses_tma", ctypes.c_int, [_V]),
+    ("lb_set_tile_dispatch", ctypes.c_int, [_V, ctypes.c_int]),
+    ("lb_tile_dispatch", ctypes.c_int, [_V]),
     ("lb_set_step_blocks", ctypes.c_int, [_V, ctypes.c_int]),
     ("lb_last_error", ctypes.c_char_p, [_V]),
     ("lb_free", None, [_V]),
@@ -313,6 +315,14 @@ def lb_status(h: int) -> None:
 
 def lb_uses_tma(h: int) -> bool:
     return bool(lib().lb_uses_tma(h))
+
+
+def lb_set_tile_dispatch(h: int, dynamic: bool) -> None:
+    check(lib().lb_set_tile_dispatch(h, int(dynamic)), h)
+
+
+def lb_tile_dispatch(h: int) -> bool:
+    return bool(lib().lb_tile_dispatch(h))
 
 
 def lb_set_step_blocks(h: int, blocks: int) -> None:

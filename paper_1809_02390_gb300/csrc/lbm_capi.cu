@@ -149,6 +149,7 @@ size_t rho_plane_bytes(const lb_params* p) {
 constexpr int kMaxReduceBlocks = 1024;
 
 size_t reduce_bytes() { return size_t(kMaxReduceBlocks) * kReduceSlots * sizeof(double) + 256; }
+constexpr size_t kQueueBytes = 256;  // tile tickets of the dynamic tensor-copy step
 
 template <typename V, typename real, typename store_t>
 void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
@@ -160,6 +161,11 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
   if (h->variant == LB_FUSED) {
     const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
     if constexpr (sizeof(store_t) <= 4 && std::is_same<V, f2>::value) {
+      if (h->use_tma && h->use_dyn) {
+        k_step_tma_dyn<V, store_t><<<h->dyn_grid, kFusedThreads, Win2<store_t>::smem, h->stream>>>(
+            h->tmap[h->cur], fin, fout, nx, ny, h->st, cv, h->wait_error, rnd, h->queue);
+        return;
+      }
       if (h->use_tma) {
         k_step_tma<V, store_t, false><<<h->tma_grid, kFusedThreads, Win<store_t>::smem, h->stream>>>(
             h->tmap[h->cur], fin, fout, nx, ny, h->st, cv, h->wait_error, rnd);
@@ -317,6 +323,27 @@ int configure(lb_handle* h) {
     if (h->tma_grid_auto > tiles) h->tma_grid_auto = tiles;
     h->tma_grid = h->tma_grid_auto;
   }
+  // Dynamic tile dispatch: needs the ticket words at the end of the scratch buffer.
+  h->use_dyn = false;
+  h->queue = h->scratch ? reinterpret_cast<unsigned*>(static_cast<char*>(h->scratch) + rho_plane_bytes(&h->p) +
+                                                      reduce_bytes())
+                        : nullptr;
+  if (h->use_tma && h->queue) {
+    const void* k = fp32 ? reinterpret_cast<const void*>(k_step_tma_dyn<f2, float>)
+                         : reinterpret_cast<const void*>(k_step_tma_dyn<f2, __half>);
+    const int smem = int(fp32 ? Win2<float>::smem : Win2<__half>::smem);
+    LB_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    LB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFusedThreads, smem));
+    LB_CUDA(h, cudaGetDevice(&dev));
+    LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int tiles = ((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY);
+    h->dyn_grid_auto = per_sm < 1 ? sms : per_sm * sms;
+    if (h->dyn_grid_auto > tiles) h->dyn_grid_auto = tiles;
+    h->dyn_grid = h->dyn_grid_auto;
+    LB_CUDA(h, cudaMemsetAsync(h->queue, 0, 2 * sizeof(unsigned), h->stream));
+    h->use_dyn = true;
+  }
   return LB_OK;
 }
 
@@ -394,7 +421,7 @@ size_t lb_state_bytes(const lb_params* p) {
 
 size_t lb_scratch_bytes(const lb_params* p) {
   if (!p || p->nx < 1 || p->ny < 1) return 0;
-  return rho_plane_bytes(p) + reduce_bytes();
+  return rho_plane_bytes(p) + reduce_bytes() + kQueueBytes;
 }
 
 int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scratch, size_t scratch_bytes,
@@ -616,8 +643,19 @@ int lb_set_step_blocks(lb_handle* h, int blocks) {
   if (blocks < 0) return fail(h, LB_EINVAL, "negative block count");
   const int tiles = ((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY);
   h->tma_grid = blocks == 0 ? h->tma_grid_auto : (blocks < tiles ? blocks : tiles);
+  h->dyn_grid = blocks == 0 ? h->dyn_grid_auto : (blocks < tiles ? blocks : tiles);
   return LB_OK;
 }
+
+int lb_set_tile_dispatch(lb_handle* h, int dynamic) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (dynamic && !(h->use_tma && h->queue))
+    return fail(h, LB_ENOTSUP, "dynamic dispatch needs the tensor-copy step and the scratch buffer");
+  h->use_dyn = dynamic != 0;
+  return LB_OK;
+}
+
+int lb_tile_dispatch(const lb_handle* h) { return h && h->use_tma && h->use_dyn ? 1 : 0; }
 
 const char* lb_last_error(const lb_handle* h) { return h ? h->err : thread_error(); }
 

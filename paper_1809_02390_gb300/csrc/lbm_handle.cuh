@@ -21,6 +21,9 @@ struct lb_handle {
   bool use_tma;           // FP32 fused step with tensor-copy staging (interior tiles)
   int tma_grid;           // persistent grid of that kernel
   int tma_grid_auto;      // its default: resident capacity, at most the tile count
+  unsigned* queue;        // tile tickets of the dynamic form (end of the scratch buffer), or null
+  bool use_dyn;           // the tensor-copy step takes tiles by ticket (k_step_tma_dyn)
+  int dyn_grid, dyn_grid_auto;
   CUtensorMap tmap[2];    // 3-D maps of f[0] and f[1]: (x, y, plane), rows layout (x, plane, y)
   int* wait_error;        // device word set by a bounded wait that gave up
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
