@@ -39,7 +39,9 @@ KERNEL_SOURCES = ["paper_1809_02390_gb300/csrc/lbm_kernels.cuh", "paper_1809_023
 # DRAM bytes per launch of the timed kernel from one ncu capture, keyed by kernel,
 # layout and the hash of its sources (a changed kernel has no figure until recaptured).
 NCU_TRAFFIC = {
-    # 2048^2 capture (profiles/k_step_tma_fp32_rows_2048_full.md) scaled x4 to 4096^2.
+    # 2048^2 captures (profiles/k_step_tma_dyn_fp32_rows_2048_full.md,
+    # profiles/k_step_tma_fp32_rows_2048_full.md) scaled x4 to 4096^2.
+    ("k_step_tma_dyn<f2>", "rows", "b25542e6c56d843c"): 1025312768,
     ("k_step_tma<f2>", "rows", "2d69328c87b53d19"): 1037581312,
 }
 
@@ -609,8 +611,8 @@ def run_ours(args):
             "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
             "kernel_source_sha": src_hash,
             "pattern_ceiling": {"GBps": round(pattern_gbs, 1), "frac": round(achieved / pattern_gbs, 4),
-                                "what": "lb_stream_copy: the step's 9 read + 9 write streams in the same "
-                                        "layout, no arithmetic"}}
+                                "what": "lb_stream_copy: the step's 9 reads + 9 writes per node, same layout "
+                                        "and 32x16 tiles, one block per tile, no arithmetic"}}
     cpu = cpu_baseline(rho0) if world == 1 else None
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",

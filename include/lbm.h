@@ -260,9 +260,11 @@ int lb_batch_uses_tma(const lb_batch* b);
 /* Sets the launch form by hand: shape 0, 1, 2 = plain loads with 32 x 16 tiles at
  * 64 registers, 32 x 16 at 80, 32 x 32 at 64 (blocks_per_sm 0 = one block per tile,
  * else a persistent grid); shape 3, 4 = the persistent tensor-copy kernel at 80 and
- * 128 registers (blocks_per_sm >= 1).  LB_EINVAL outside the ranges (blocks_per_sm
- * at most the resident maximum), LB_ENOTSUP for 3 and 4 when a lattice has no
- * tensor map. */
+ * 128 registers walking the tile list statically (block b: tiles b, b + grid, ...);
+ * shape 5, 6 = the same at 80 and 128 registers taking tiles by ticket, with two
+ * tiles' windows in flight per block (blocks_per_sm >= 1 for 3 - 6).  LB_EINVAL
+ * outside the ranges (blocks_per_sm at most the resident maximum), LB_ENOTSUP for
+ * 3 - 6 when a lattice has no tensor map. */
 int lb_batch_set_config(lb_batch* b, int shape, int blocks_per_sm);
 /* Synchronous: LB_ETIMEOUT if a bounded wait of the tensor-copy kernel gave up
  * since the last call (the flag is cleared), else LB_OK. */
@@ -311,10 +313,11 @@ int lb_tile_dispatch(const lb_handle* h);
 
 /* Measurement aid (no counterpart in the paper): one pass with the step's memory
  * traffic and none of its arithmetic, a copy of the state into the other buffer
- * reading and writing every population in place (nine read and nine write
- * streams, as the step).  The state is unchanged (the copy is exact and becomes
- * the current buffer).  Asynchronous on the handle's stream; the pass's bandwidth
- * is the ceiling the step's access pattern allows, in the handle's layout. */
+ * reading and writing every population in place, tile by tile as the step (32 x 16
+ * tiles, one block per tile, the handle's layout).  The state is unchanged (the
+ * copy is exact and becomes the current buffer).  Asynchronous on the handle's
+ * stream; the pass's bandwidth is the ceiling quoted for the step's access pattern
+ * (the fastest copy of that pattern measured). */
 int lb_stream_copy(lb_handle* h);
 
 /* Grid of that persistent kernel (each block steps tiles b, b + blocks, ...):

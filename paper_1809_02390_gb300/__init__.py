@@ -185,7 +185,8 @@ class Batch:
         return capi.lb_batch_config(self.b)
 
     def set_config(self, shape: int, blocks_per_sm: int) -> None:
-        """Launch form by hand (lb_batch_set_config): shapes 0-2 plain loads, 3-4 tensor copies."""
+        """Launch form by hand (lb_batch_set_config): shapes 0-2 plain loads, 3-4 tensor
+        copies with a static tile walk, 5-6 tensor copies with tiles taken by ticket."""
         capi.lb_batch_set_config(self.b, shape, blocks_per_sm)
 
     @property

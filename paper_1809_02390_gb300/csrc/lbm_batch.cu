@@ -42,11 +42,14 @@ __host__ __device__ constexpr int row_stride(int nx) { return (nx + 3) / 4 * 4; 
 // Launch shapes the autotuner chooses among: tile height and the register budget
 // the kernel is compiled for (resident blocks per SM it must allow), plain loads;
 // shapes 3 and 4 are the persistent tensor-copy kernel (32 x 16 tiles, the tile
-// list of shape 0) at 80 and 128 registers.
-constexpr int kShapes = 5;
+// list of shape 0) at 80 and 128 registers walking the list statically, shapes 5
+// and 6 the same taking tiles by ticket with two windows in flight.
+constexpr int kShapes = 7;
 constexpr int kShapeTMA = 3;  // first tensor-copy shape
-constexpr int kShapeTY[kShapes] = {16, 16, 32, 16, 16};
+constexpr int kShapeDyn = 5;  // first ticket-dispatch shape
+constexpr int kShapeTY[kShapes] = {16, 16, 32, 16, 16, 16, 16};
 __host__ __device__ constexpr bool is_tma(int shape) { return shape >= kShapeTMA; }
+__host__ __device__ constexpr bool is_dyn(int shape) { return shape >= kShapeDyn; }
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: the pools end where they started)
 
 // One record per tile: its lattice, origin and the lattice's size, row stride and
@@ -189,6 +192,120 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
   }
 }
 
+// Ticket form of the kernel above (the single-lattice k_step_tma_dyn over the tile
+// list): block b starts with list entries b and b + G, then takes 2G, 2G + 1, ...
+// by ticket (queue[0]; queue[1] counts finished blocks, and the last one resets
+// both).  Tile k of a block has its window in buffer k mod 2 and its record and
+// coefficients in slot k mod 3: the record of tile k + 2 is written by thread 0
+// before the barrier of tile k, and its window, coefficients (bulk copy on the
+// buffer's mbarrier) and, for a wrapping tile, the per-thread asynchronous copies
+// are issued after it.  Every staged tile commits one group of asynchronous copies
+// (empty unless it wraps), so waiting for all but the newest group completes tile
+// k's.  A wait that gives up sets *err.
+template <int MINB>
+__global__ void __launch_bounds__(kFusedThreads, MINB)
+    k_step_batch_tma_dyn(const float* __restrict__ pool_in, float* __restrict__ pool_out,
+                         const TileRec* __restrict__ tiles, const LatCoef<f2>* __restrict__ coef,
+                         const CUtensorMap* __restrict__ maps, int total_tiles, VCoef<f2> common,
+                         int* __restrict__ err, unsigned* __restrict__ queue) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
+  __shared__ float rs[2][kTileY + 2][kTileX + 2];
+  __shared__ __align__(16) LatCoef<f2> cs[3];
+  __shared__ TileRec rec[3];
+  __shared__ int tq[3];
+  __shared__ __align__(8) unsigned long long bar[2];
+  const int total = total_tiles;
+  auto win = [&](int slot) { return reinterpret_cast<float*>(base + slot * Win2<float>::buffer); };
+  auto kind_of = [](const TileRec& r) { return tile_kind(r.x0, r.y0, r.nx, r.ny); };
+  const int first = 2 * int(gridDim.x);
+  bool dry = first >= total;  // thread 0: no more tickets
+  auto draw = [&]() {
+    if (dry) return total;
+    const int t = first + int(atomicAdd(queue, 1u));
+    dry = t >= total;
+    return dry ? total : t;
+  };
+  // All threads: stage tile j of the block (record in slot j mod 3).
+  auto issue = [&](int j) {
+    const int q = j % 3, slot = j & 1;
+    const TileRec& r = rec[q];
+    const bool live = tq[q] < total;
+    const int kind = live ? kind_of(r) : kPlainLoad;
+    if (live && threadIdx.x == 0) {
+      fence_proxy_async();
+      if (kind == kTensorCopy)
+        issue_windows(win(slot), maps + r.lat, r.x0, r.y0, &bar[slot], sizeof(LatCoef<f2>));
+      else
+        mbar_expect_tx(&bar[slot], sizeof(LatCoef<f2>));
+      bulk_load(&cs[q], coef + r.lat, sizeof(LatCoef<f2>), &bar[slot]);
+    }
+    if (live && kind == kAsyncCopy)
+      issue_window_async(win(slot), pool_in + r.offset, r.nx, r.ny, planes_strides(r.sx, r.ny), r.x0, r.y0);
+    else
+      cp_async_commit();
+  };
+  int pending = total;  // thread 0: the tile after the staged ones
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    const int b = int(blockIdx.x), g = int(gridDim.x);
+    tq[0] = b < total ? b : total;
+    tq[1] = b + g < total ? b + g : total;
+    if (tq[0] < total) rec[0] = tiles[tq[0]];
+    if (tq[1] < total) rec[1] = tiles[tq[1]];
+    pending = tq[1] < total ? draw() : total;
+  }
+  __syncthreads();
+  issue(0);
+  issue(1);
+  unsigned ph = 0u;  // bit s: parity of the next phase of bar[s]
+  for (int k = 0;; ++k) {
+    const int q = k % 3, slot = k & 1;
+    if (tq[q] >= total) break;  // uniform; tiles rise, so no later tile is staged
+    const TileRec ti = rec[q];
+    const int kind = kind_of(ti);
+    if (threadIdx.x == 0) {  // the record of tile k + 2 (its slot's last reader was tile k - 1)
+      const int q2 = (k + 2) % 3;
+      tq[q2] = pending;
+      if (pending < total) rec[q2] = tiles[pending];
+      pending = draw();
+    }
+    const bool late = !mbar_wait(&bar[slot], (ph >> slot) & 1u);
+    ph ^= 1u << slot;
+    if (kind == kAsyncCopy) {
+      cp_async_wait_all_but_one();
+      __syncthreads();
+    }
+    float f[kTileRows][9];
+    if (kind == kPlainLoad)
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), ti.x0,
+                                      ti.y0, f, rs[slot]);
+    else  // read even after a failed wait (in bounds; the block then stops)
+      window_tile(win(slot), f, rs[slot]);
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait(&bar[slot], ((ph >> slot) & 1u) ^ 1u);
+        if (tq[(k + 1) % 3] < total) mbar_wait(&bar[slot ^ 1], (ph >> (slot ^ 1)) & 1u);
+      }
+      cp_async_wait_all();
+      break;
+    }
+    issue(k + 2);
+    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), common,
+                                    cs[q], ti.x0, ti.y0, rs[slot]);
+  }
+  cp_async_wait_all();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+      atomicExch(queue, 0u);
+      atomicExch(queue + 1, 0u);
+    }
+  }
+}
+
 template <int TY, int MINB>
 void launch_shape(const float* in, float* out, const TileRec* tiles, const LatCoef<f2>* coef, int total, int bps,
                   int sms, const VCoef<f2>& common, cudaStream_t st) {
@@ -206,7 +323,9 @@ const void* batch_kernel(int shape) {
     case 1: return reinterpret_cast<const void*>(k_step_batch<float, 16, 3, true>);
     case 2: return reinterpret_cast<const void*>(k_step_batch<float, 32, 2, true>);
     case 3: return reinterpret_cast<const void*>(k_step_batch_tma<3>);
-    default: return reinterpret_cast<const void*>(k_step_batch_tma<2>);
+    case 4: return reinterpret_cast<const void*>(k_step_batch_tma<2>);
+    case 5: return reinterpret_cast<const void*>(k_step_batch_tma_dyn<3>);
+    default: return reinterpret_cast<const void*>(k_step_batch_tma_dyn<2>);
   }
 }
 
@@ -225,6 +344,7 @@ struct lb_batch {
   LatCoef<f2>* d_coef;
   CUtensorMap* d_maps;  // [2][n]: lattice maps in pool 0, then in pool 1
   int* d_err;           // set by a bounded wait of the tensor-copy kernel that gave up
+  unsigned* d_queue;    // tickets of the dispatch shapes (two words)
   bool tma_ok;          // every lattice large enough to have interior tiles has its maps
   VCoef<f2> common;
   cudaStream_t stream;
@@ -254,7 +374,8 @@ size_t lattice_elems(const lb_params& p) { return ((9 * size_t(row_stride(p.nx))
 int max_blocks(lb_batch* b, int shape, int* out) {
   const void* k = batch_kernel(shape);
   const int threads = kShapeTY[shape] == 16 ? TileShape<16>::threads : TileShape<32>::threads;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, threads, is_tma(shape) ? kTmaSmem : 0);
+  const int smem = is_dyn(shape) ? int(Win2<float>::smem) : (is_tma(shape) ? int(kTmaSmem) : 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, threads, smem);
   if (e != cudaSuccess) return berr(b, LB_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
   if (*out < 1) *out = 1;
   return LB_OK;
@@ -271,7 +392,13 @@ void launch_one(lb_batch* b, int from) {
   if (is_tma(s)) {
     const int grid = std::min(b->blocks_per_sm * b->sms, total);
     const CUtensorMap* maps = b->d_maps + from * b->n;
-    if (s == kShapeTMA)
+    if (s == kShapeDyn)
+      k_step_batch_tma_dyn<3><<<grid, kFusedThreads, Win2<float>::smem, b->stream>>>(
+          in, out, tiles, b->d_coef, maps, total, b->common, b->d_err, b->d_queue);
+    else if (s == kShapeDyn + 1)
+      k_step_batch_tma_dyn<2><<<grid, kFusedThreads, Win2<float>::smem, b->stream>>>(
+          in, out, tiles, b->d_coef, maps, total, b->common, b->d_err, b->d_queue);
+    else if (s == kShapeTMA)
       k_step_batch_tma<3><<<grid, kFusedThreads, kTmaSmem, b->stream>>>(in, out, tiles, b->d_coef, maps, total,
                                                                          b->common, b->d_err);
     else
@@ -335,7 +462,7 @@ size_t lb_batch_meta_bytes(const lb_params* ps, int n) {
   size_t tiles = 0;
   for (int s = 0; s < kTileLists; ++s) tiles += total_tiles_of(ps, n, kShapeTY[s]);
   return size_t(n) * (kTileLists * sizeof(BatchLattice) + sizeof(LatCoef<f2>) + 2 * sizeof(CUtensorMap)) +
-         tiles * sizeof(TileRec) + 4096;
+         tiles * sizeof(TileRec) + 4096 + 256;
 }
 
 int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
@@ -439,6 +566,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   b->d_maps = reinterpret_cast<CUtensorMap*>(m);
   m = align(m + 2 * size_t(n) * sizeof(CUtensorMap));
   b->d_err = reinterpret_cast<int*>(m);
+  m = align(m + sizeof(int));
+  b->d_queue = reinterpret_cast<unsigned*>(m);
   // Tensor maps of every lattice in both pools.  A lattice below 40 x 18 has no
   // interior tile (those need nx >= 68, ny >= 34) and keeps a zero map it never uses.
   std::vector<CUtensorMap> h_maps(2 * size_t(n));
@@ -455,6 +584,14 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   e = cudaMemcpyAsync(b->d_maps, h_maps.data(), h_maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                       b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned), b->stream);
+  // The ticket shapes hold two window buffers (above the 48 KB default).
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_step_batch_tma_dyn<3>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Win2<float>::smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k_step_batch_tma_dyn<2>),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Win2<float>::smem));
   for (int s = 0; s < kTileLists && e == cudaSuccess; ++s) {
     e = cudaMemcpyAsync(b->d_desc[s], b->desc[s].data(), n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)

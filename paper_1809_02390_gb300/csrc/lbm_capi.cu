@@ -236,45 +236,45 @@ namespace {
 // Set by a bounded wait of the tensor-copy step that gave up (read and cleared by lb_status).
 __device__ int g_wait_error;
 
-// The step's memory traffic without its arithmetic: every node's nine populations
-// read from their nine planes and written to the same places of the other buffer
-// (grid-stride loop, coalesced per plane).  Its bandwidth is the ceiling of the
-// SoA access pattern (nine read and nine write streams at once).
+// The step's memory traffic without its arithmetic: one block per 32 x 16 tile
+// (the step's tiles), each thread moving the nine populations of its two nodes
+// (rows ty and ty + 8) to the same places of the other buffer, in the handle's
+// layout.  With one block per tile the hardware hands tiles out in order as
+// blocks finish and eight blocks per SM keep 147 KB of loads in flight: of the
+// forms of this copy measured (grid-stride loops over nodes with 4-, 8- and
+// 16-byte accesses, persistent tile walks), this one moves the most bytes, so its
+// bandwidth is the ceiling quoted for the step's access pattern.
 template <typename T>
-__global__ void k_stream_soa(const T* __restrict__ in, T* __restrict__ out, long long N) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += stride) {
-    T v[9];
+__global__ void __launch_bounds__(256) k_stream_tiles(const T* __restrict__ in, T* __restrict__ out, int nx, int ny,
+                                                      Strides st) {
+  const int tiles_x = (nx + kTileX - 1) / kTileX;
+  const int x = (blockIdx.x % tiles_x) * kTileX + (threadIdx.x & (kTileX - 1));
+  const int y0 = (blockIdx.x / tiles_x) * kTileY + threadIdx.x / kTileX;
+  if (x >= nx) return;
+  T v[kTileRows][9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = in[i * N + x];
+  for (int k = 0; k < kTileRows; ++k) {
+    const int y = y0 + k * kRowStride;
+    if (y < ny) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) out[i * N + x] = v[i];
+      for (int i = 0; i < 9; ++i) v[k][i] = in[st.at(i, x, y)];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int y = y0 + k * kRowStride;
+    if (y < ny) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) out[st.at(i, x, y)] = v[k][i];
+    }
   }
 }
 
-// The same for the rows layout f[y][i][x]: node (x, y)'s nine populations at
-// 9 nx y + nx i + x (nine row segments, each coalesced, next to one another).
 template <typename T>
-__global__ void k_stream_rows(const T* __restrict__ in, T* __restrict__ out, int nx, int ny) {
-  const unsigned N = unsigned(nx) * unsigned(ny), stride = gridDim.x * blockDim.x;
-  for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += stride) {
-    const unsigned y = n / unsigned(nx), o = n + 8u * unsigned(nx) * y;  // 9 nx y + x
-    T v[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[i] = in[o + i * nx];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) out[o + i * nx] = v[i];
-  }
-}
-
-template <typename T>
-void launch_stream_copy(const lb_handle* h, const void* in, void* out, unsigned grid) {
-  const T* src = static_cast<const T*>(in);
-  T* dst = static_cast<T*>(out);
-  if (h->p.layout == LB_LAYOUT_ROWS)
-    k_stream_rows<<<grid, 256, 0, h->stream>>>(src, dst, h->p.nx, h->p.ny);
-  else
-    k_stream_soa<<<grid, 256, 0, h->stream>>>(src, dst, (long long)h->p.nx * h->p.ny);
+void launch_stream_copy(const lb_handle* h, const void* in, void* out) {
+  const unsigned tiles = unsigned(((h->p.nx + kTileX - 1) / kTileX) * ((h->p.ny + kTileY - 1) / kTileY));
+  k_stream_tiles<<<tiles, kFusedThreads, 0, h->stream>>>(static_cast<const T*>(in), static_cast<T*>(out), h->p.nx,
+                                                         h->p.ny, h->st);
 }
 
 // A bounded wait that cannot succeed: the mbarrier's single arrival comes with 16
@@ -620,16 +620,12 @@ int lb_wait_selftest(lb_handle* h, long long polls) {
 
 int lb_stream_copy(lb_handle* h) {
   if (!h) return fail(nullptr, LB_EINVAL, "null handle");
-  int dev = 0, sms = 0;
-  LB_CUDA(h, cudaGetDevice(&dev));
-  LB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const void* in = h->f[h->cur];
   void* out = h->f[1 - h->cur];
-  const unsigned grid = unsigned(sms * 8);
   switch (h->p.precision) {
-    case LB_FP64: launch_stream_copy<double>(h, in, out, grid); break;
-    case LB_FP32: launch_stream_copy<float>(h, in, out, grid); break;
-    default: launch_stream_copy<__half>(h, in, out, grid);
+    case LB_FP64: launch_stream_copy<double>(h, in, out); break;
+    case LB_FP32: launch_stream_copy<float>(h, in, out); break;
+    default: launch_stream_copy<__half>(h, in, out);
   }
   LB_CUDA(h, cudaGetLastError());
   h->cur = 1 - h->cur;  // same data in the other buffer: the state is unchanged

@@ -174,6 +174,8 @@ __device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// All but the newest committed group of this thread have completed.
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // All threads: the window of the (wrapping) tile at (x0, y0) of a lattice with
 // populations at fin (layout st) into win.  Plane i's window row r holds
@@ -344,11 +346,13 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   }
 }
 
-// Dynamic form: the blocks take tiles from a ticket counter (one atomic add per
-// tile by thread 0, drawn two tiles ahead), so that the tiles in flight at any
-// time are the next ones in row-major order across the whole grid, and each block
-// keeps two tiles' windows in flight (two window buffers, two mbarriers): while
-// tile k is collided, tiles k + 1 and k + 2 are being copied.  With the static
+// Dynamic form: block b starts with tiles b and b + G (G = gridDim.x); from then on
+// the blocks take tiles 2G, 2G + 1, ... from a ticket counter (one atomic add per
+// tile by thread 0, drawn two tiles ahead, off the critical path), so that the
+// tiles in flight at any time are the next ones in row-major order across the
+// whole grid, and each block keeps two tiles' windows in flight (two window
+// buffers, two mbarriers): while tile k is collided, tiles k + 1 and k + 2 are
+// being copied.  With the static
 // walk above the tiles in flight drift apart as blocks run at different speeds;
 // copies of the same tiles measured 7.0 TB/s with one block per tile or dynamic
 // dispatch at 8 blocks per SM, against 5.9 - 6.2 TB/s for static walks.
@@ -376,12 +380,13 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
   const bool rows = st.ps == nx;  // rows layout (the planes one has ps = nx ny, ny >= 50 here)
   auto win = [&](int slot) { return reinterpret_cast<S*>(base + slot * Win2<S>::buffer); };
-  // Thread 0: tickets in increasing order; after the first one past the last tile
-  // no more are drawn.
-  bool dry = false;
+  // Thread 0: tiles 2G + ticket in increasing order; after the first one past the
+  // last tile no more tickets are drawn.
+  const int first = 2 * int(gridDim.x);
+  bool dry = first >= total;
   auto draw = [&]() {
     if (dry) return total;
-    const int t = int(atomicAdd(queue, 1u));
+    const int t = first + int(atomicAdd(queue, 1u));
     dry = t >= total;
     return dry ? total : t;
   };
@@ -396,11 +401,12 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    tq[0] = draw();
-    tq[1] = draw();
+    const int b = int(blockIdx.x), g = int(gridDim.x);
+    tq[0] = b < total ? b : total;
+    tq[1] = b + g < total ? b + g : total;
     issue(tq[0], 0);
     issue(tq[1], 1);
-    pending = draw();
+    pending = tq[1] < total ? draw() : total;
   }
   __syncthreads();
   unsigned ph = 0u;  // bit s: parity of the next phase of bar[s]

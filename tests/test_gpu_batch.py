@@ -93,10 +93,13 @@ def test_batch_lattice_matches_oracle(orc):
     b.close()
 
 
-@pytest.mark.parametrize("shape,bps", [(0, 0), (0, 2), (1, 1), (2, 0), (3, 1), (3, 3), (4, 1), (4, 2)])
+@pytest.mark.parametrize("shape,bps", [(0, 0), (0, 2), (1, 1), (2, 0), (3, 1), (3, 3), (4, 1), (4, 2), (5, 1), (5, 3),
+                                       (6, 1), (6, 2)])
 def test_every_launch_form_equals_single_lattices(shape, bps):
     """Each launch form by hand (plain loads one block per tile or persistent,
-    tensor copies persistent at both register budgets), with a 512 x 256 lattice
+    tensor copies persistent at both register budgets, walking the tile list
+    statically or taking tiles by ticket; the ticket counter must be reset between
+    launches for the replayed steps to match), with a 512 x 256 lattice
     added so that persistent blocks walk several tiles (mixed interior and wrapping
     tiles, lattices with and without a padded row stride), in graph replay and
     single launches: bit-identical to the single-lattice step; no wait gave up."""
@@ -122,7 +125,7 @@ def test_set_config_rejects_bad_forms():
 
     rhos, kws = _inputs()
     b = Batch(rhos, [dict(k) for k in kws])
-    for shape, bps in [(5, 1), (-1, 0), (3, 0), (0, 1000)]:
+    for shape, bps in [(7, 1), (-1, 0), (3, 0), (5, 0), (0, 1000)]:
         with pytest.raises(capi.LBError):
             b.set_config(shape, bps)
     b.close()
