@@ -191,7 +191,7 @@ template <typename real, typename store_t>
 __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
     k_adj_fused(const store_t* __restrict__ s, const real* __restrict__ mu_in, const real* __restrict__ sb_in,
                 real* __restrict__ mu, real* __restrict__ sbar, double* __restrict__ partial, int accumulate, int nx,
-                int ny, VCoef<real> c, int stage_state) {
+                int ny, VCoef<real> c) {
   __shared__ real rs[kTileY + 2][kTileX + 2];   // density of s^n on tile + ring
   __shared__ real rb[kTileY + 2][kTileX + 2];   // rhob' on tile + ring
   __shared__ real sbx[kTileY + 4][kTileX + 4];  // Sb' on tile + two-node ring
@@ -239,32 +239,14 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
   }
   cp_async_commit();
   real f[kTileRows][9];
-  // stage_state (FP32, lattices of at least 40 x 18 with several waves of tiles): the
-  // state's pull window too (the window of the forward step, in dynamic shared
-  // memory), so that every global read of the block is in flight before the first
-  // is used.
-  bool staged = false;
-  if constexpr (kStageMu) {
-    if (stage_state) {  // uniform over the grid
-      extern __shared__ __align__(128) unsigned char dyn[];
-      float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
-      issue_window_async(win, s, nx, ny, planes_strides(nx, ny), x0, y0);
-      cp_async_wait_all();
-      __syncthreads();
-      window_tile(win, f, rs);
-      staged = true;
-    }
-  }
-  if (!staged) {
 #pragma unroll
-    for (int k = 0; k < kTileRows; ++k) {
-      const int gy = y0 + ty + k * kRowStride;
-      pull_row(s, plane, nx, ny, wr(gy, ny), xm, xc, xp, f[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  for (int k = 0; k < kTileRows; ++k) {
+    const int gy = y0 + ty + k * kRowStride;
+    pull_row(s, plane, nx, ny, wr(gy, ny), xm, xc, xp, f[k]);
   }
-  for (int t = threadIdx.x; t < (staged ? 0 : 2 * (kTileX + 2) + 2 * kTileY); t += kAdjThreads) {
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) rs[ty + k * kRowStride + 1][tx + 1] = sum9(f[k]);
+  for (int t = threadIdx.x; t < 2 * (kTileX + 2) + 2 * kTileY; t += kAdjThreads) {
     int wx, wy;
     if (t < kTileX + 2) {
       wx = t, wy = 0;
@@ -366,6 +348,153 @@ __global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<real>())
   }
 }
 
+// Staging of one FP32 adjoint tile in dynamic shared memory, for lattices with
+// several waves of tiles: the state's pull window (the forward step's nine
+// 40 x 18 windows), mu'_i at the tile's nodes shifted by e_i (nine 40 x 16 windows,
+// plane i's from (x0 - 4, y0 + e_iy): node (tx, ly) reads column tx + 4 + e_ix of
+// row ly) and Sb' on the tile with its two-node ring (two 40 x 20 windows from
+// (x0 - 4, y0 - 2)).  An interior tile gets all twenty windows by tensor copies
+// issued by one thread on one mbarrier; a tile whose windows wrap gets the same
+// layout by per-thread asynchronous copies with periodic coordinates.
+constexpr int kMuCols = kTileX + 8, kMuRows = kTileY;
+constexpr int kMuPlane = kMuCols * kMuRows;  // 640 floats
+constexpr int kSbCols = kTileX + 8, kSbRows = kTileY + 4;
+constexpr int kSbPlane = kSbCols * kSbRows;  // 800 floats
+constexpr int kAdjMuOff = 9 * kTmaPlane;     // after the state window
+constexpr int kAdjSbOff = kAdjMuOff + 9 * kMuPlane;
+constexpr int kAdjStageFloats = kAdjSbOff + 2 * kSbPlane;
+constexpr unsigned kAdjStageSmem = unsigned(kAdjStageFloats) * 4 + 128;
+constexpr unsigned kAdjCotBytes = unsigned(9 * kMuPlane + 2 * kSbPlane) * 4;  // mu' and Sb' windows
+static_assert((kAdjMuOff * 4) % 128 == 0 && (kMuPlane * 4) % 128 == 0 && (kAdjSbOff * 4) % 128 == 0 &&
+                  (kSbPlane * 4) % 128 == 0,
+              "tensor-copy destinations start on 128-byte boundaries");
+
+// All threads: the staging of a wrapping tile (lattice of at least 40 x 18) by
+// per-thread asynchronous copies; commits one group.
+__device__ __forceinline__ void stage_adj_async(float* base, const float* __restrict__ s,
+                                                const float* __restrict__ mu_in, const float* __restrict__ sb_in,
+                                                int nx, int ny, int x0, int y0) {
+  const int plane = nx * ny;
+  for (int e = threadIdx.x; e < 9 * kMuPlane; e += kAdjThreads) {
+    const int i = e / kMuPlane, rc = e - i * kMuPlane, r = rc / kMuCols, cc = rc - r * kMuCols;
+    const int y = wrap1(y0 + ey_of(i) + r, ny), x = wrap1(x0 - 4 + cc, nx);
+    cp_async4(base + kAdjMuOff + e, mu_in + (i * plane + y * nx + x));
+  }
+  for (int e = threadIdx.x; e < 2 * kSbPlane; e += kAdjThreads) {
+    const int p = e / kSbPlane, rc = e - p * kSbPlane, r = rc / kSbCols, cc = rc - r * kSbCols;
+    const int y = wrap1(y0 - 2 + r, ny), x = wrap1(x0 - 4 + cc, nx);
+    cp_async4(base + kAdjSbOff + e, sb_in + (p * plane + y * nx + x));
+  }
+  issue_window_async(base, s, nx, ny, planes_strides(nx, ny), x0, y0);  // commits the group
+}
+
+// One adjoint step of an FP32 tile from the staged windows above (the staged
+// counterpart of k_adj_fused: same VJP, same sums, same outputs).  A wait for the
+// tensor copies that gives up sets *err (reported by lb_status) and ends the block.
+__global__ void __launch_bounds__(kAdjThreads, 3)
+    k_adj_tma(const __grid_constant__ CUtensorMap tstate, const __grid_constant__ CUtensorMap tmu,
+              const __grid_constant__ CUtensorMap tsb, const float* __restrict__ s, const float* __restrict__ mu_in,
+              const float* __restrict__ sb_in, float* __restrict__ mu, float* __restrict__ sbar,
+              double* __restrict__ partial, int accumulate, int nx, int ny, VCoef<float> c, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char dyn[];
+  float* const base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
+  const float* const muw = base + kAdjMuOff;
+  const float* const sbx = base + kAdjSbOff;
+  const float* const sby = sbx + kSbPlane;
+  __shared__ float rs[kTileY + 2][kTileX + 2];  // density of s^n on tile + ring
+  __shared__ float rb[kTileY + 2][kTileX + 2];  // rhob' on tile + ring
+  __shared__ float red[kAdjThreads / 32][3];
+  __shared__ __align__(8) unsigned long long bar;
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  const int plane = nx * ny;
+  const bool interior = tma_interior<float>(x0, y0, nx, ny);
+  if (interior) {
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      issue_windows(base, &tstate, x0, y0, &bar, kAdjCotBytes);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) tma_load_3d(base + kAdjMuOff + i * kMuPlane, &tmu, x0 - 4, y0 + ey_of(i), i, &bar);
+      tma_load_3d(base + kAdjSbOff, &tsb, x0 - 4, y0 - 2, 0, &bar);
+      tma_load_3d(base + kAdjSbOff + kSbPlane, &tsb, x0 - 4, y0 - 2, 1, &bar);
+    }
+    const bool late = !mbar_wait(&bar, 0);
+    if (__syncthreads_or(late)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait(&bar, 0);
+      }
+      return;
+    }
+  } else {
+    stage_adj_async(base, s, mu_in, sb_in, nx, ny, x0, y0);
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  float f[kTileRows][9];
+  window_tile(base, f, rs);
+  // rhob'(y) = sum_j omega_j e_j . Sb'(y - e_j) on tile + ring; Sb' window column of
+  // lattice column x0 - 2 + cx is cx + 2.
+  const float third = float(1.0 / 3.0), twelfth = float(1.0 / 12.0);
+  for (int t = threadIdx.x; t < (kTileY + 2) * (kTileX + 2); t += kAdjThreads) {
+    const int wy = t / (kTileX + 2), wx = t - wy * (kTileX + 2);
+    const int cy = wy + 1, cx = wx + 3;
+    auto X = [&](int yy, int xx) { return sbx[yy * kSbCols + xx]; };
+    auto Y = [&](int yy, int xx) { return sby[yy * kSbCols + xx]; };
+    const float ax = X(cy, cx - 1) - X(cy, cx + 1);
+    const float ay = Y(cy - 1, cx) - Y(cy + 1, cx);
+    const float d5 = X(cy - 1, cx - 1) + Y(cy - 1, cx - 1);
+    const float d6 = Y(cy - 1, cx + 1) - X(cy - 1, cx + 1);
+    const float d7 = -X(cy + 1, cx + 1) - Y(cy + 1, cx + 1);
+    const float d8 = X(cy + 1, cx - 1) - Y(cy + 1, cx - 1);
+    rb[wy][wx] = third * (ax + ay) + twelfth * ((d5 + d6) + (d7 + d8));
+  }
+  __syncthreads();
+  const int gx = x0 + tx;
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int ly = ty + k * kRowStride + 1, lx = tx + 1;
+    const int gy = y0 + ly - 1;
+    if (gx >= nx || gy >= ny) continue;
+    float Sx, Sy;
+    stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
+            rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx, Sy);
+    const int off = gy * nx + gx;
+    // lam_i(x) = mu'_i(x + e_i) + rhob'(x + e_i).
+    float ob[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      ob[i] = muw[i * kMuPlane + (ly - 1) * kMuCols + tx + 4 + ex_of(i)] + rb[ly + ey_of(i)][lx + ex_of(i)];
+    AdjOut<float> r;
+    collide_vjp(c, f[k], Sx, Sy, ob, r);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i * plane + off] = r.d[i];
+    sbar[off] = r.Sx;
+    sbar[plane + off] = r.Sy;
+    acc[0] += r.RT;
+    acc[1] += r.G2;
+    acc[2] += r.lam;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[w][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float v = 0.f;
+    for (int j = 0; j < kAdjThreads / 32; ++j) v += red[j][threadIdx.x];
+    double* slot = partial + (size_t(blockIdx.y) * gridDim.x + blockIdx.x) * 3 + threadIdx.x;
+    *slot = accumulate ? *slot + double(v) : double(v);
+  }
+}
+
 // Cotangent lam of a state -> (mu, Sb) representation: mu_i(y) = lam_i(y - e_i), Sb = 0.
 template <typename real>
 __global__ void k_adj_push(const real* __restrict__ lam, real* __restrict__ mu, real* __restrict__ sbar, int nx,
@@ -410,32 +539,47 @@ int adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, dou
   else
     c = &h->cf;
   const dim3 blk(32, 8), pgrd((nx + 31) / 32, (ny + 7) / 8);
-  // FP32 stages the state's pull window in dynamic shared memory (above the 48 KB
-  // default together with the static arrays, hence the opt-in) when the lattice has
-  // several waves of tiles; on small lattices (one wave) waiting for the whole
-  // window before any work measured slower (256^2: 8.7 against 7.2 us per step).
-  size_t win_smem = 0;
+  // FP32 on lattices with several waves of tiles: every input of a tile staged in
+  // shared memory (k_adj_tma; tensor copies on interior tiles), so that all of a
+  // block's reads are in flight before the first is used.  On small lattices (one
+  // wave) waiting for the whole staging before any work measured slower (256^2:
+  // 8.7 against 7.2 us per step), and k_adj_fused pulls the state directly.
+  bool staged = false;
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 0;
-  if constexpr (sizeof(real) == 4) {
-    if (async_window_ok(nx, ny) && sms > 0 && size_t(grd.x) * grd.y >= size_t(4) * 3 * sms) {
-      win_smem = kTmaSmem;
-      const cudaError_t a = cudaFuncSetAttribute(k_adj_fused<real, store_t>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(win_smem));
+  if constexpr (sizeof(real) == 4 && sizeof(store_t) == 4) {
+    if (h->wait_error && async_window_ok(nx, ny) && nx % 4 == 0 && sms > 0 &&
+        size_t(grd.x) * grd.y >= size_t(4) * 3 * sms) {
+      const cudaError_t a =
+          cudaFuncSetAttribute(k_adj_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kAdjStageSmem));
       if (a != cudaSuccess) {
         std::snprintf(h->err, sizeof(h->err), "adjoint kernels: %s", cudaGetErrorString(a));
         return LB_ECUDA;
       }
+      staged = true;
     }
   }
   k_adj_push<real><<<pgrd, blk, 0, h->stream>>>(static_cast<const real*>(lam), mu[0], sb[0], nx, ny);
   int cur = 0;
   for (int j = k - 1; j >= 0; --j) {
-    k_adj_fused<real, store_t><<<grd, kAdjThreads, win_smem, h->stream>>>(
-        static_cast<const store_t*>(states[j]), mu[cur], sb[cur], mu[1 - cur], sb[1 - cur], partial, j < k - 1, nx,
-        ny, *c, win_smem > 0 ? 1 : 0);
+    bool done = false;
+    if constexpr (sizeof(real) == 4 && sizeof(store_t) == 4) {
+      CUtensorMap ts, tm, tb;
+      if (staged && encode_population_map(&ts, const_cast<void*>(states[j]), nx, ny, nx, 4) &&
+          encode_plane_map(&tm, mu[cur], nx, ny, 9, kMuCols, kMuRows) &&
+          encode_plane_map(&tb, sb[cur], nx, ny, 2, kSbCols, kSbRows)) {
+        k_adj_tma<<<grd, kAdjThreads, kAdjStageSmem, h->stream>>>(
+            ts, tm, tb, static_cast<const float*>(states[j]), mu[cur], sb[cur], mu[1 - cur], sb[1 - cur], partial,
+            j < k - 1, nx, ny, *c, h->wait_error);
+        done = true;
+      }
+    }
+    if (!done)
+      k_adj_fused<real, store_t><<<grd, kAdjThreads, 0, h->stream>>>(
+          static_cast<const store_t*>(states[j]), mu[cur], sb[cur], mu[1 - cur], sb[1 - cur], partial, j < k - 1, nx,
+          ny, *c);
     cur = 1 - cur;
   }
   if (dtheta) k_adj_theta<<<1, 256, 0, h->stream>>>(partial, int(grd.x * grd.y), h->p.R_gas, dtheta);

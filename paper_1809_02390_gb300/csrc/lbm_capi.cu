@@ -204,16 +204,22 @@ namespace lbm {
 // (cols, 1, 18), which lands in shared memory as the same 18 x cols window.  False
 // if the layout does not allow it (base not 16-byte aligned, row stride not a
 // multiple of 16 bytes).
-bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes, bool rows) {
+static EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !p)
-      return false;
+      return nullptr;
     fn = reinterpret_cast<EncodeTiledFn>(p);
   }
+  return fn;
+}
+
+bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes, bool rows) {
+  const EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
   if (elem_bytes != 4 && elem_bytes != 2) return false;
   const size_t eb = size_t(elem_bytes);
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(sx) * eb) % 16 != 0 || sx < nx) return false;
@@ -226,6 +232,22 @@ bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx,
   const CUtensorMapDataType dt = elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   return fn(map, dt, 3, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3-D map (x, y, plane) of `planes` FP32 planes of nx x ny (row stride nx), box
+// of cols x rows x 1: one copy delivers a window of one plane.
+bool encode_plane_map(CUtensorMap* map, const void* base, int nx, int ny, int planes, int cols, int rows) {
+  const EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(nx) * 4) % 16 != 0 || nx < cols || ny < rows)
+    return false;
+  const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(planes)};
+  const cuuint64_t strides[2] = {cuuint64_t(nx) * 4, cuuint64_t(nx) * ny * 4};
+  const cuuint32_t box[3] = {cuuint32_t(cols), cuuint32_t(rows), 1};
+  const cuuint32_t estride[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -39,4 +39,7 @@ namespace lbm {
 // does not allow one (lbm_capi.cu).
 bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx, int elem_bytes = 4,
                            bool rows = false);
+// 3-D map (x, y, plane) of `planes` FP32 planes of nx x ny, box cols x rows x 1
+// (lbm_capi.cu); false if the buffer does not allow one.
+bool encode_plane_map(CUtensorMap* map, const void* base, int nx, int ny, int planes, int cols, int rows);
 }  // namespace lbm
