@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
 // list): block b starts with list entries b and b + G, then takes 2G, 2G + 1, ...
 // by ticket (queue[0]; queue[1] counts finished blocks, and the last one resets
 // both).  Tile k of a block has its window in buffer k mod 2 and its record and
-// coefficients in slot k mod 3: the record of tile k + 2 is written by thread 0
+// coefficients in slot k mod 3: the record of tile k + 2 is written by the issuer
 // before the barrier of tile k, and its window, coefficients (bulk copy on the
 // buffer's mbarrier) and, for a wrapping tile, the per-thread asynchronous copies
 // are issued after it.  Every staged tile commits one group of asynchronous copies
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
   auto win = [&](int slot) { return reinterpret_cast<float*>(base + slot * Win2<float>::buffer); };
   auto kind_of = [](const TileRec& r) { return tile_kind(r.x0, r.y0, r.nx, r.ny); };
   const int first = 2 * int(gridDim.x);
-  bool dry = first >= total;  // thread 0: no more tickets
+  bool dry = first >= total;  // the issuer: no more tickets
   auto draw = [&]() {
     if (dry) return total;
     const int t = first + int(atomicAdd(queue, 1u));
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     const TileRec& r = rec[q];
     const bool live = tq[q] < total;
     const int kind = live ? kind_of(r) : kPlainLoad;
-    if (live && threadIdx.x == 0) {
+    if (live && threadIdx.x == kIssuer) {
       fence_proxy_async();
       if (kind == kTensorCopy)
         issue_windows(win(slot), maps + r.lat, r.x0, r.y0, &bar[slot], sizeof(LatCoef<f2>));
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     else
       cp_async_commit();
   };
-  int pending = total;  // thread 0: the tile after the staged ones
-  if (threadIdx.x == 0) {
+  int pending = total;  // the issuer: the tile after the staged ones
+  if (threadIdx.x == kIssuer) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     const int b = int(blockIdx.x), g = int(gridDim.x);
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     if (tq[q] >= total) break;  // uniform; tiles rise, so no later tile is staged
     const TileRec ti = rec[q];
     const int kind = kind_of(ti);
-    if (threadIdx.x == 0) {  // the record of tile k + 2 (its slot's last reader was tile k - 1)
+    if (threadIdx.x == kIssuer) {  // the record of tile k + 2 (its slot's last reader was tile k - 1)
       const int q2 = (k + 2) % 3;
       tq[q2] = pending;
       if (pending < total) rec[q2] = tiles[pending];
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     else  // read even after a failed wait (in bounds; the block then stops)
       window_tile(win(slot), f, rs[slot]);
     if (__syncthreads_or(late)) {
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == kIssuer) {
         atomicExch(err, 1);
         mbar_wait(&bar[slot], ((ph >> slot) & 1u) ^ 1u);
         if (tq[(k + 1) % 3] < total) mbar_wait(&bar[slot ^ 1], (ph >> (slot ^ 1)) & 1u);
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
                                     cs[q], ti.x0, ti.y0, rs[slot]);
   }
   cp_async_wait_all();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == kIssuer) {
     __threadfence();
     if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
       atomicExch(queue, 0u);

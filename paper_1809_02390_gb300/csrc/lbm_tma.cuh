@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
 
 // Dynamic form: block b starts with tiles b and b + G (G = gridDim.x); from then on
 // the blocks take tiles 2G, 2G + 1, ... from a ticket counter (one atomic add per
-// tile by thread 0, drawn two tiles ahead, off the critical path), so that the
+// tile by the issuer thread, drawn two tiles ahead, off the critical path), so that the
 // tiles in flight at any time are the next ones in row-major order across the
 // whole grid, and each block keeps two tiles' windows in flight (two window
 // buffers, two mbarriers): while tile k is collided, tiles k + 1 and k + 2 are
@@ -359,6 +359,12 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
 // queue[0] is the ticket counter, queue[1] counts finished blocks; the last block
 // to finish resets both to zero for the next launch (also after a wait that gave
 // up).  Results do not depend on which block steps which tile.
+// The thread that draws tickets and issues the copies of the dynamic forms: lane 0
+// of the last warp, which has no density-ring work (threads 0 - 99 sum the ring),
+// so that the bookkeeping does not lengthen the slowest warp before each barrier
+// (1% on 4096^2 against thread 0).
+constexpr int kIssuer = kFusedThreads - 32;
+
 template <typename S>
 struct Win2 {
   static constexpr unsigned buffer = 9u * Win<S>::plane * sizeof(S);  // one window buffer (128-byte multiple)
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
   const bool rows = st.ps == nx;  // rows layout (the planes one has ps = nx ny, ny >= 50 here)
   auto win = [&](int slot) { return reinterpret_cast<S*>(base + slot * Win2<S>::buffer); };
-  // Thread 0: tiles 2G + ticket in increasing order; after the first one past the
+  // The issuer: tiles 2G + ticket in increasing order; after the first one past the
   // last tile no more tickets are drawn.
   const int first = 2 * int(gridDim.x);
   bool dry = first >= total;
@@ -391,14 +397,14 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     return dry ? total : t;
   };
   auto kind_of = [&](int t) { return tile_kind<false, S>((t % tiles_x) * kTileX, (t / tiles_x) * kTileY, nx, ny); };
-  auto issue = [&](int t, int slot) {  // thread 0
+  auto issue = [&](int t, int slot) {  // the issuer
     if (t < total && kind_of(t) == kTensorCopy) {
       fence_proxy_async();
       issue_windows(win(slot), &tin, (t % tiles_x) * kTileX, (t / tiles_x) * kTileY, &bar[slot], 0, rows);
     }
   };
-  int pending = total;  // thread 0: the ticket after the two staged tiles
-  if (threadIdx.x == 0) {
+  int pending = total;  // the issuer: the tile after the two staged ones
+  if (threadIdx.x == kIssuer) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     const int b = int(blockIdx.x), g = int(gridDim.x);
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     else  // read even after a failed wait (in bounds; the block then stops)
       window_tile(win(slot), f, rs[slot]);
     if (__syncthreads_or(late)) {
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == kIssuer) {
         atomicExch(err, 1);
         mbar_wait(&bar[slot], ((ph >> slot) & 1u) ^ 1u);
         const int to = tq[slot ^ 1];
@@ -436,14 +442,14 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       break;
     }
     // The buffer of this tile is free: stage the tile two ahead into it.
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == kIssuer) {
       tq[slot] = pending;
       issue(pending, slot);
       pending = draw();
     }
     collide_tile<V, S, kTileY>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[slot], rnd);
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == kIssuer) {
     __threadfence();
     if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
       atomicExch(queue, 0u);
