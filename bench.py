@@ -281,12 +281,12 @@ def batch_workload(n_lattices: int = 256, seed: int = 0):
     return rhos, kws, meta
 
 
-def measure_batch(torch, single_mlups: float, steps: int) -> dict:
+def measure_batch(torch, single_mlups: float, steps: int, layout: str = "rows") -> dict:
     from paper_1809_02390_gb300 import Batch
 
     rhos, kws, meta = batch_workload()
     nodes = sum(r.size for r in rhos)
-    b = Batch(rhos, kws)
+    b = Batch(rhos, [dict(k, layout=layout) for k in kws])
     b.tune(4)
     cfg = b.config()
     s = b.stream
@@ -315,7 +315,7 @@ def measure_batch(torch, single_mlups: float, steps: int) -> dict:
         curve.append([round(m["Tr"], 4), round(gas, 5), round(liq, 5), round(m["rho_g"], 5), round(m["rho_l"], 5)])
     b.close()
 
-    return {"lattices": len(rhos), "nodes": nodes, "steps": steps, "ms": round(ms, 2), "MLUPS": round(mlups, 1),
+    return {"lattices": len(rhos), "layout": layout, "nodes": nodes, "steps": steps, "ms": round(ms, 2), "MLUPS": round(mlups, 1),
             "ratio_vs_single_lattice": round(mlups / single_mlups, 4) if single_mlups else None, "tuned": cfg,
             "launch": "one multi-lattice kernel per step (blocks_per_sm 0: one block per tile, else persistent), "
                       "graph replay of 64 steps",
@@ -503,7 +503,7 @@ def run_ours(args):
         elif args.only_precision:
             part = measure_precision(torch, args.precision_steps)
         else:
-            part = measure_adjoint(n, torch) if args.only_adjoint else measure_batch(torch, None, args.batch_steps)
+            part = measure_adjoint(n, torch) if args.only_adjoint else measure_batch(torch, None, args.batch_steps, args.layout)
         print(json.dumps(part), flush=True)
         return
     rho0, d = workload_rho(n, seed=rank)
@@ -592,7 +592,7 @@ def run_ours(args):
         extras["adjoint"] = measure_adjoint(n, torch)
         extras["adjoint_256"] = measure_adjoint(256, torch)  # the calibration lattice
         torch.cuda.empty_cache()
-        extras["batch"] = measure_batch(torch, value, args.batch_steps)
+        extras["batch"] = measure_batch(torch, value, args.batch_steps, args.layout)
         torch.cuda.empty_cache()
         extras["calibration"] = measure_calibration(torch)
         extras["precision"] = measure_precision(torch, args.precision_steps)

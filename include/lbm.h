@@ -92,8 +92,9 @@ typedef struct lb_params {
   double s_0, s_j;        /* rates of the conserved moments (act on zero); <= 0 selects 1 */
   double rho_ref;         /* storage shift: populations stored as fbar_i - w_i rho_ref */
   int32_t layout;         /* enum lb_layout.  LB_LAYOUT_ROWS: forward step, moments, pressure,
-                             reductions; the adjoint calls and the batched solver take
-                             LB_LAYOUT_PLANES only (LB_ENOTSUP) */
+                             reductions, batched solver (all lattices of a batch in one
+                             layout); the adjoint calls take LB_LAYOUT_PLANES only
+                             (LB_ENOTSUP) */
   int32_t reserved1;      /* must be 0 */
 } lb_params;
 
@@ -232,9 +233,10 @@ int lb_adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, 
  * time step over a flat list of tiles of all lattices; runs of 64 steps are
  * captured into CUDA graphs and replayed.  FP32 storage only.
  * Memory (all the caller's): two population pools of lb_batch_pool_bytes (lattice
- * i at element offset lb_batch_offset(i), layout f[9][ny][sx] with the row stride
- * sx = lb_batch_row_stride(i) = nx rounded up to a multiple of 4; columns nx..sx-1
- * are padding, never read or written) and a metadata buffer of
+ * i at element offset lb_batch_offset(i), layout f[9][ny][sx], or f[ny][9][sx] when
+ * the lattices' lb_params.layout is LB_LAYOUT_ROWS (one layout per batch), with the
+ * row stride sx = lb_batch_row_stride(i) = nx rounded up to a multiple of 4;
+ * columns nx..sx-1 are padding, never read or written) and a metadata buffer of
  * lb_batch_meta_bytes (descriptors, coefficients, tensor maps; the maps hold the
  * pools' addresses, so the pools must not move while the batch lives).
  * rho0: the initial densities of all lattices concatenated ([y][x] each), host

@@ -151,14 +151,16 @@ class Batch:
     """Independent FP32 lattices advanced together (lb_batch_*).
 
     rho0s: list of initial densities [ny, nx] (numpy); kws: list of dicts of
-    lb_params fields per lattice (Tr, K_int, ...).  Runs on its own CUDA stream
-    (graphs cannot be captured on the legacy default stream)."""
+    lb_params fields per lattice (Tr, K_int, ..., and layout="rows" for pools of
+    f[ny][9][sx], the same for every lattice).  Runs on its own CUDA stream (graphs
+    cannot be captured on the legacy default stream)."""
 
     def __init__(self, rho0s, kws, stream=None):
         torch = _torch()
         n = len(rho0s)
         self.n = n
         self.shapes = [np.asarray(r).shape for r in rho0s]
+        self.layout = kws[0].get("layout", "planes")
         self.rho_refs = [float(np.float32(kw.pop("rho_ref", float(np.mean(r))))) for r, kw in zip(rho0s, kws)]
         ps = (capi.lb_params * n)(*[params(s[1], s[0], precision="fp32", rho_ref=rr, **kw)
                                     for s, rr, kw in zip(self.shapes, self.rho_refs, kws)])
@@ -195,12 +197,15 @@ class Batch:
 
     def state(self, i: int):
         """Current state of lattice i: [9, ny, nx] view of the current pool (deviations;
-        rows are strided by nx rounded up to a multiple of 4)."""
+        rows are strided by nx rounded up to a multiple of 4; a permuted view in the
+        rows layout)."""
         self.stream.synchronize()
         pool = self.pool_a if capi.lb_batch_state(self.b) == self.pool_a.data_ptr() else self.pool_b
         off = capi.lb_batch_offset(self.b, i)
         sx = capi.lb_batch_row_stride(self.b, i)
         ny, nx = self.shapes[i]
+        if self.layout == "rows":
+            return pool[off:off + 9 * sx * ny].view(ny, 9, sx)[:, :, :nx].permute(1, 0, 2)
         return pool[off:off + 9 * sx * ny].view(9, ny, sx)[:, :, :nx]
 
     def status(self) -> None:

@@ -39,6 +39,12 @@ struct BatchLattice {
 
 __host__ __device__ constexpr int row_stride(int nx) { return (nx + 3) / 4 * 4; }
 
+// Strides of a lattice in the pools: planes f[9][ny][sx], or rows f[ny][9][sx]
+// (every lattice of a batch in the same layout).
+__host__ __device__ inline Strides lat_strides(int sx, int ny, int rows) {
+  return rows ? Strides{sx, 9 * sx} : planes_strides(sx, ny);
+}
+
 // Launch shapes the autotuner chooses among: tile height and the register budget
 // the kernel is compiled for (resident blocks per SM it must allow), plain loads;
 // shapes 3 and 4 are the persistent tensor-copy kernel (32 x 16 tiles, the tile
@@ -80,7 +86,7 @@ template <typename store_t, int TY, int MINB, bool PERSIST>
 __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
     k_step_batch(const store_t* __restrict__ pool_in, store_t* __restrict__ pool_out,
                  const TileRec* __restrict__ tiles, const LatCoef<f2>* __restrict__ coef, int total_tiles,
-                 VCoef<f2> common) {
+                 VCoef<f2> common, int rows) {
   static_assert(kCoefWords <= TileShape<TY>::threads, "one coefficient word per thread");
   __shared__ float rs[TY + 2][kTileX + 2];
   __shared__ LatCoef<f2> cs;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
   int word = threadIdx.x < kCoefWords ? reinterpret_cast<const int*>(coef + ti.lat)[threadIdx.x] : 0;
   if constexpr (!PERSIST) {  // one block per tile
     step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny,
-                               planes_strides(ti.sx, ti.ny), common, cs, ti.x0, ti.y0, rs,
+                               lat_strides(ti.sx, ti.ny, rows), common, cs, ti.x0, ti.y0, rs,
                                StoreCoef{&cs, word, true});
     return;
   }
@@ -106,7 +112,7 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
     const StoreCoef hook{&cs, word, ti.lat != last};
     last = ti.lat;
     step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny,
-                               planes_strides(ti.sx, ti.ny), common, cs, ti.x0, ti.y0, rs, hook);
+                               lat_strides(ti.sx, ti.ny, rows), common, cs, ti.x0, ti.y0, rs, hook);
     if (tn >= total_tiles) break;
     __syncthreads();  // shared densities and coefficients are reused by the next tile
     t = tn;
@@ -129,7 +135,8 @@ template <int MINB>
 __global__ void __launch_bounds__(kFusedThreads, MINB)
     k_step_batch_tma(const float* __restrict__ pool_in, float* __restrict__ pool_out,
                      const TileRec* __restrict__ tiles, const LatCoef<f2>* __restrict__ coef,
-                     const CUtensorMap* __restrict__ maps, int total_tiles, VCoef<f2> common, int* __restrict__ err) {
+                     const CUtensorMap* __restrict__ maps, int total_tiles, VCoef<f2> common, int* __restrict__ err,
+                     int rows) {
   extern __shared__ __align__(128) unsigned char dyn[];
   float* win = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
   __shared__ float rs[2][kTileY + 2][kTileX + 2];
@@ -144,12 +151,12 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     if (threadIdx.x == 0) {
       fence_proxy_async();
       if (kind == kTensorCopy)
-        issue_windows(win, maps + r.lat, r.x0, r.y0, &bar, sizeof(LatCoef<f2>));
+        issue_windows(win, maps + r.lat, r.x0, r.y0, &bar, sizeof(LatCoef<f2>), rows != 0);
       else
         mbar_expect_tx(&bar, sizeof(LatCoef<f2>));
       bulk_load(&cs[slot], coef + r.lat, sizeof(LatCoef<f2>), &bar);
     }
-    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, planes_strides(r.sx, r.ny), r.x0, r.y0);
+    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, lat_strides(r.sx, r.ny, rows), r.x0, r.y0);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     }
     float f[kTileRows][9];
     if (kind == kPlainLoad)
-      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), ti.x0,
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), ti.x0,
                                       ti.y0, f, rs[buf]);
     else  // read even after a failed wait (in bounds; the block then returns)
       window_tile(win, f, rs[buf]);
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
       return;
     }
     if (tn < total_tiles) issue(rec[buf ^ 1], buf ^ 1);
-    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), common,
+    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), common,
                                     cs[buf], ti.x0, ti.y0, rs[buf]);
     buf ^= 1;
   }
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     k_step_batch_tma_dyn(const float* __restrict__ pool_in, float* __restrict__ pool_out,
                          const TileRec* __restrict__ tiles, const LatCoef<f2>* __restrict__ coef,
                          const CUtensorMap* __restrict__ maps, int total_tiles, VCoef<f2> common,
-                         int* __restrict__ err, unsigned* __restrict__ queue) {
+                         int* __restrict__ err, unsigned* __restrict__ queue, int rows) {
   extern __shared__ __align__(128) unsigned char dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
   __shared__ float rs[2][kTileY + 2][kTileX + 2];
@@ -235,13 +242,13 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     if (live && threadIdx.x == kIssuer) {
       fence_proxy_async();
       if (kind == kTensorCopy)
-        issue_windows(win(slot), maps + r.lat, r.x0, r.y0, &bar[slot], sizeof(LatCoef<f2>));
+        issue_windows(win(slot), maps + r.lat, r.x0, r.y0, &bar[slot], sizeof(LatCoef<f2>), rows != 0);
       else
         mbar_expect_tx(&bar[slot], sizeof(LatCoef<f2>));
       bulk_load(&cs[q], coef + r.lat, sizeof(LatCoef<f2>), &bar[slot]);
     }
     if (live && kind == kAsyncCopy)
-      issue_window_async(win(slot), pool_in + r.offset, r.nx, r.ny, planes_strides(r.sx, r.ny), r.x0, r.y0);
+      issue_window_async(win(slot), pool_in + r.offset, r.nx, r.ny, lat_strides(r.sx, r.ny, rows), r.x0, r.y0);
     else
       cp_async_commit();
   };
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     }
     float f[kTileRows][9];
     if (kind == kPlainLoad)
-      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), ti.x0,
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), ti.x0,
                                       ti.y0, f, rs[slot]);
     else  // read even after a failed wait (in bounds; the block then stops)
       window_tile(win(slot), f, rs[slot]);
@@ -293,7 +300,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
       break;
     }
     issue(k + 2);
-    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, planes_strides(ti.sx, ti.ny), common,
+    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), common,
                                     cs[q], ti.x0, ti.y0, rs[slot]);
   }
   cp_async_wait_all();
@@ -308,13 +315,13 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
 
 template <int TY, int MINB>
 void launch_shape(const float* in, float* out, const TileRec* tiles, const LatCoef<f2>* coef, int total, int bps,
-                  int sms, const VCoef<f2>& common, cudaStream_t st) {
+                  int sms, const VCoef<f2>& common, cudaStream_t st, int rows) {
   if (bps > 0)
     k_step_batch<float, TY, MINB, true><<<bps * sms, TileShape<TY>::threads, 0, st>>>(in, out, tiles, coef, total,
-                                                                                        common);
+                                                                                        common, rows);
   else
     k_step_batch<float, TY, MINB, false><<<total, TileShape<TY>::threads, 0, st>>>(in, out, tiles, coef, total,
-                                                                                     common);
+                                                                                     common, rows);
 }
 
 const void* batch_kernel(int shape) {
@@ -346,6 +353,7 @@ struct lb_batch {
   int* d_err;           // set by a bounded wait of the tensor-copy kernel that gave up
   unsigned* d_queue;    // tickets of the dispatch shapes (two words)
   bool tma_ok;          // every lattice large enough to have interior tiles has its maps
+  int rows;             // pools in the rows layout f[ny][9][sx] (else planes f[9][ny][sx])
   VCoef<f2> common;
   cudaStream_t stream;
   int sms;
@@ -394,22 +402,22 @@ void launch_one(lb_batch* b, int from) {
     const CUtensorMap* maps = b->d_maps + from * b->n;
     if (s == kShapeDyn)
       k_step_batch_tma_dyn<3><<<grid, kFusedThreads, Win2<float>::smem, b->stream>>>(
-          in, out, tiles, b->d_coef, maps, total, b->common, b->d_err, b->d_queue);
+          in, out, tiles, b->d_coef, maps, total, b->common, b->d_err, b->d_queue, b->rows);
     else if (s == kShapeDyn + 1)
       k_step_batch_tma_dyn<2><<<grid, kFusedThreads, Win2<float>::smem, b->stream>>>(
-          in, out, tiles, b->d_coef, maps, total, b->common, b->d_err, b->d_queue);
+          in, out, tiles, b->d_coef, maps, total, b->common, b->d_err, b->d_queue, b->rows);
     else if (s == kShapeTMA)
       k_step_batch_tma<3><<<grid, kFusedThreads, kTmaSmem, b->stream>>>(in, out, tiles, b->d_coef, maps, total,
-                                                                         b->common, b->d_err);
+                                                                         b->common, b->d_err, b->rows);
     else
       k_step_batch_tma<2><<<grid, kFusedThreads, kTmaSmem, b->stream>>>(in, out, tiles, b->d_coef, maps, total,
-                                                                         b->common, b->d_err);
+                                                                         b->common, b->d_err, b->rows);
   } else if (s == 0)
-    launch_shape<16, 4>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
+    launch_shape<16, 4>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream, b->rows);
   else if (s == 1)
-    launch_shape<16, 3>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
+    launch_shape<16, 3>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream, b->rows);
   else
-    launch_shape<32, 2>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream);
+    launch_shape<32, 2>(in, out, tiles, b->d_coef, total, b->blocks_per_sm, b->sms, b->common, b->stream, b->rows);
 }
 
 int config_id(const lb_batch* b) { return b->shape * 64 + b->blocks_per_sm; }
@@ -475,6 +483,7 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   lb_batch* b = new (std::nothrow) lb_batch();
   if (!b) return berr(nullptr, LB_EINVAL, "out of host memory%s");
   b->n = n;
+  b->rows = ps[0].layout == LB_LAYOUT_ROWS ? 1 : 0;
   b->p.assign(ps, ps + n);
   b->d.resize(n);
   b->stream = static_cast<cudaStream_t>(stream);
@@ -494,8 +503,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   for (int i = 0; i < n; ++i) {
     char err[512] = {0};
     if (ps[i].precision != LB_FP32) return bail(LB_ENOTSUP, "lb_batch_init: the batched solver stores FP32");
-    if (ps[i].layout != LB_LAYOUT_PLANES)
-      return bail(LB_ENOTSUP, "lb_batch_init: the batched solver stores the planes layout");
+    if (ps[i].layout != ps[0].layout)
+      return bail(LB_ENOTSUP, "lb_batch_init: the lattices of one batch share the layout");
     if (derive(&ps[i], &b->d[i], err, sizeof(err)) != LB_OK) {
       char m[600];
       std::snprintf(m, sizeof(m), "lattice %d: %s", i, err);
@@ -578,7 +587,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
       const BatchLattice& L = b->desc[0][i];
       if (L.nx < kTmaCols || L.ny < kTmaRows) continue;
       float* base = static_cast<float*>(side ? pool_b : pool_a) + L.offset;
-      if (!encode_population_map(&h_maps[side * size_t(n) + i], base, L.nx, L.ny, L.sx)) b->tma_ok = false;
+      if (!encode_population_map(&h_maps[side * size_t(n) + i], base, L.nx, L.ny, L.sx, 4, b->rows != 0))
+        b->tma_ok = false;
     }
   cudaError_t e = cudaSuccess;
   e = cudaMemcpyAsync(b->d_maps, h_maps.data(), h_maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
@@ -614,7 +624,7 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     const size_t N = size_t(ps[i].nx) * ps[i].ny;
     k_init_rest<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
         rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny,
-        planes_strides(b->desc[0][i].sx, ps[i].ny), h_coefd[i]);
+        lat_strides(b->desc[0][i].sx, ps[i].ny, b->rows), h_coefd[i]);
     e = cudaGetLastError();
     node_off += N;
   }

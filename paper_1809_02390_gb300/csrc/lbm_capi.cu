@@ -200,7 +200,7 @@ namespace lbm {
 
 // 3-D map of one FP32 (elem_bytes 4) or FP16 (2) population buffer: x (nx), y (ny,
 // row stride sx), plane (9); box of one plane window (40 x 18 floats or 48 x 18
-// halves).  Rows layout: x (nx), plane (9, stride nx), y (ny, stride 9 nx), box
+// halves).  Rows layout: x (nx), plane (9, stride sx), y (ny, stride 9 sx), box
 // (cols, 1, 18), which lands in shared memory as the same 18 x cols window.  False
 // if the layout does not allow it (base not 16-byte aligned, row stride not a
 // multiple of 16 bytes).
@@ -224,7 +224,7 @@ bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx,
   const size_t eb = size_t(elem_bytes);
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (size_t(sx) * eb) % 16 != 0 || sx < nx) return false;
   const int cols = elem_bytes == 4 ? Win<float>::cols : Win<__half>::cols;
-  if (nx < cols || ny < kTmaRows || (rows && sx != nx)) return false;
+  if (nx < cols || ny < kTmaRows) return false;
   const cuuint64_t dims[3] = {cuuint64_t(nx), cuuint64_t(rows ? 9 : ny), cuuint64_t(rows ? ny : 9)};
   const cuuint64_t strides[2] = {cuuint64_t(sx) * eb, cuuint64_t(sx) * (rows ? 9 : ny) * eb};
   const cuuint32_t box[3] = {cuuint32_t(cols), rows ? 1u : cuuint32_t(kTmaRows), rows ? cuuint32_t(kTmaRows) : 1u};

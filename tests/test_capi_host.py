@@ -106,9 +106,9 @@ def test_sizes(capi):
     assert capi.lb_scratch_bytes(p) >= 100 * 30 * 8
 
 
-def test_batch_rejects_rows_layout_before_any_gpu_work(capi):
-    """The batched solver stores the planes layout: a lattice in the rows layout is
-    refused with LB_ENOTSUP on the host (the buffers are never touched)."""
+def test_batch_rejects_mixed_layouts_before_any_gpu_work(capi):
+    """The lattices of one batch share the layout of its pools: a batch mixing planes
+    and rows is refused with LB_ENOTSUP on the host (the buffers are never touched)."""
     import numpy as np
 
     ps = (capi.lb_params * 2)(capi.make_params(64, 64), capi.make_params(64, 64, layout=capi.LB_LAYOUT_ROWS))
@@ -116,4 +116,4 @@ def test_batch_rejects_rows_layout_before_any_gpu_work(capi):
     b = ctypes.c_void_p()
     meta = capi.lib().lb_batch_meta_bytes(ps, 2)
     rc = capi.lib().lb_batch_init(ctypes.byref(b), ps, 2, 1 << 40, 2 << 40, 3 << 40, meta, rho.ctypes.data, 0, None)
-    assert rc == capi.LB_ENOTSUP and "planes layout" in capi.lb_last_error(None)
+    assert rc == capi.LB_ENOTSUP and "share the layout" in capi.lb_last_error(None)

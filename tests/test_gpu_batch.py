@@ -129,3 +129,25 @@ def test_set_config_rejects_bad_forms():
         with pytest.raises(capi.LBError):
             b.set_config(shape, bps)
     b.close()
+
+
+@pytest.mark.parametrize("shape,bps", [(0, 0), (1, 1), (3, 1), (5, 1), (6, 2)])
+def test_rows_layout_batch_equals_single_lattices(shape, bps):
+    """Pools in the rows layout f[ny][9][sx] (padded rows; tensor maps with dimensions
+    (x, plane, y)): every launch form gives each lattice the single-lattice
+    trajectory bit for bit (the layouts share the arithmetic), in graph replay and
+    single launches."""
+    from paper_1809_02390_gb300 import Batch, derive
+
+    rhos, kws = _inputs()
+    d = derive(512, 256, Tr=0.8)
+    rhos.append(inputs.spinodal(512, 256, 0.5 * (d["rho_g"] + d["rho_l"]), 0.01, 3))
+    kws.append(dict(Tr=0.8))
+    b = Batch(rhos, [dict(k, layout="rows") for k in kws])
+    b.set_config(shape, bps)
+    b.run(64 + 7)
+    b.status()
+    ref = _singles(rhos, kws, 64 + 7)
+    for i in range(len(rhos)):
+        assert torch.equal(b.state(i), ref[i]), i
+    b.close()
