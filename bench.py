@@ -395,6 +395,18 @@ def measure_oscillation(torch, steps: int = 60000) -> dict:
     return {k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()}
 
 
+def measure_translation(torch) -> dict:
+    """Galilean check: a droplet restarted with a uniform velocity U against the same
+    droplet at rest, compared in the co-moving frame after 2,000 steps (FP32)."""
+    from paper_1809_02390_gb300.validation import translating_droplet
+
+    t0 = time.perf_counter()
+    rows = [translating_droplet(U=u, steps=2000) for u in (0.025, 0.05, 0.1)]
+    out = {"rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()} for r in rows],
+           "seconds": round(time.perf_counter() - t0, 1)}
+    return out
+
+
 def measure_sweeps(torch) -> dict:
     """Interface thickness and surface tension against K_INT (CS EOS, a = 1, b = 4),
     fitted slopes next to the simulated and analytic slopes printed in supplement
@@ -499,7 +511,8 @@ def run_ours(args):
     n = args.size
     if args.only_adjoint or args.only_batch or args.only_precision or args.only_validation:  # one measurement
         if args.only_validation:
-            part = {"oscillation": measure_oscillation(torch), "interface_sweeps": measure_sweeps(torch)}
+            part = {"oscillation": measure_oscillation(torch), "translation": measure_translation(torch),
+                    "interface_sweeps": measure_sweeps(torch)}
         elif args.only_precision:
             part = measure_precision(torch, args.precision_steps)
         else:
@@ -597,6 +610,7 @@ def run_ours(args):
         extras["calibration"] = measure_calibration(torch)
         extras["precision"] = measure_precision(torch, args.precision_steps)
         extras["oscillation"] = measure_oscillation(torch)
+        extras["translation"] = measure_translation(torch)
         extras["interface_sweeps"] = measure_sweeps(torch)
 
     if rank != 0:

@@ -280,6 +280,16 @@ int lb_batch_derived(const lb_batch* b, int i, lb_derived* out);
 const char* lb_batch_last_error(const lb_batch* b);
 void lb_batch_free(lb_batch* b);
 
+/* Sets the current state to the equilibrium of a density and velocity field, in
+ * place of a caller-made state (no counterpart in the paper; lb_init's rest state is
+ * the case u = 0): fbar_i = (M^-1 m_eq(rho, u))_i - w_i rho_ref, with m_eq of Eq. 3
+ * (self-tuning eta from the EOS at rho; alpha_1 = -1, beta_1 = 1, alpha_2 = 1) and
+ * momentum rho u, so u is the velocity before the half-force shift of Eq. 5 (the
+ * first step's velocity is u + F/(2 rho)).  rho, ux, uy: nx*ny doubles each, [y][x],
+ * on the device; ux or uy NULL means 0.  Asynchronous on the handle's stream; the
+ * step count is unchanged. */
+int lb_set_equilibrium(lb_handle* h, const double* rho, const double* ux, const double* uy);
+
 /* Copies the current state to / from a caller device buffer of lb_state_bytes(). */
 int lb_get_state(lb_handle* h, void* dst);
 int lb_set_state(lb_handle* h, const void* src);

@@ -98,6 +98,24 @@ class Lattice:
     def steps_done(self) -> int:
         return capi.lb_steps_done(self.h)
 
+    def set_equilibrium(self, rho, ux=None, uy=None) -> None:
+        """Sets the state to the equilibrium of a density and velocity field ([ny, nx]
+        arrays or tensors; ux, uy default 0; u is the velocity before the half-force
+        shift), through lb_set_equilibrium."""
+        torch = _torch()
+        dev = self.f_a.device
+
+        def dev64(a):
+            t = torch.as_tensor(a, dtype=torch.float64).to(dev).contiguous()
+            if tuple(t.shape) != (self.ny, self.nx):
+                raise ValueError("fields must be [ny, nx]")
+            return t
+
+        keep = [dev64(rho)] + [dev64(a) if a is not None else None for a in (ux, uy)]
+        capi.lb_set_equilibrium(self.h, keep[0].data_ptr(), *[t.data_ptr() if t is not None else None
+                                                               for t in keep[1:]])
+        self.stream.synchronize()
+
     def buffer(self):
         """The current (post-collision) state buffer in its storage layout."""
         return self.f_a if capi.lb_state(self.h) == self.f_a.data_ptr() else self.f_b

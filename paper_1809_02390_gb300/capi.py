@@ -92,6 +92,7 @@ SIGNATURES = [
     ("lb_stream_copy", ctypes.c_int, [_V]),
     ("lb_pressure", ctypes.c_int, [_V, _V]),
     ("lb_uses_tma", ctypes.c_int, [_V]),
+    ("lb_set_equilibrium", ctypes.c_int, [_V, _V, _V, _V]),
     ("lb_set_tile_dispatch", ctypes.c_int, [_V, ctypes.c_int]),
     ("lb_tile_dispatch", ctypes.c_int, [_V]),
     ("lb_set_step_blocks", ctypes.c_int, [_V, ctypes.c_int]),
@@ -315,6 +316,10 @@ def lb_status(h: int) -> None:
 
 def lb_uses_tma(h: int) -> bool:
     return bool(lib().lb_uses_tma(h))
+
+
+def lb_set_equilibrium(h: int, rho: int, ux: int | None, uy: int | None) -> None:
+    check(lib().lb_set_equilibrium(h, rho, ux, uy), h)
 
 
 def lb_set_tile_dispatch(h: int, dynamic: bool) -> None:

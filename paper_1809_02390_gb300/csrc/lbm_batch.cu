@@ -622,8 +622,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   size_t node_off = 0;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const size_t N = size_t(ps[i].nx) * ps[i].ny;
-    k_init_rest<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
-        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny,
+    k_init_eq<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
+        rd + node_off, nullptr, nullptr, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny,
         lat_strides(b->desc[0][i].sx, ps[i].ny, b->rows), h_coefd[i]);
     e = cudaGetLastError();
     node_off += N;

@@ -512,15 +512,15 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   const unsigned blocks = unsigned((N + 255) / 256);
   switch (p->precision) {
     case LB_FP64:
-      k_init_rest<double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny, h->st,
+      k_init_eq<double><<<blocks, 256, 0, h->stream>>>(rho_dev, nullptr, nullptr, static_cast<double*>(f_a), p->nx, p->ny, h->st,
                                                         h->cd);
       break;
     case LB_FP32:
-      k_init_rest<float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, h->st,
+      k_init_eq<float><<<blocks, 256, 0, h->stream>>>(rho_dev, nullptr, nullptr, static_cast<float*>(f_a), p->nx, p->ny, h->st,
                                                        h->cd);
       break;
     default:
-      k_init_rest<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny, h->st,
+      k_init_eq<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, nullptr, nullptr, static_cast<__half*>(f_a), p->nx, p->ny, h->st,
                                                         h->cd);
       break;
   }
@@ -598,6 +598,27 @@ int lb_reduce(lb_handle* h, double out[8]) {
     case LB_FP32: return run_reduce<float, float>(h, out);
     default: return run_reduce<float, __half>(h, out);
   }
+}
+
+int lb_set_equilibrium(lb_handle* h, const double* rho, const double* ux, const double* uy) {
+  if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+  if (!rho) return fail(h, LB_EINVAL, "rho is required");
+  const size_t N = size_t(h->p.nx) * h->p.ny;
+  const unsigned blocks = unsigned((N + 255) / 256);
+  void* f = h->f[h->cur];
+  const int nx = h->p.nx, ny = h->p.ny;
+  switch (h->p.precision) {
+    case LB_FP64:
+      k_init_eq<double><<<blocks, 256, 0, h->stream>>>(rho, ux, uy, static_cast<double*>(f), nx, ny, h->st, h->cd);
+      break;
+    case LB_FP32:
+      k_init_eq<float><<<blocks, 256, 0, h->stream>>>(rho, ux, uy, static_cast<float*>(f), nx, ny, h->st, h->cd);
+      break;
+    default:
+      k_init_eq<__half><<<blocks, 256, 0, h->stream>>>(rho, ux, uy, static_cast<__half*>(f), nx, ny, h->st, h->cd);
+  }
+  LB_CUDA(h, cudaGetLastError());
+  return LB_OK;
 }
 
 int lb_get_state(lb_handle* h, void* dst) {

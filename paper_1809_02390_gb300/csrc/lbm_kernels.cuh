@@ -241,31 +241,51 @@ __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restri
   store9(fout + st.at(0, x, y), st.ps, o, unsigned(y * nx + x), rnd);
 }
 
-// Rest equilibrium from an initial density (computed in FP64, rounded once):
-// m_eq(rho, u = 0) = (rho, -2 rho + 2 eta, rho + beta_2 eta, 0, ...), minus rho_ref M w.
+// Equilibrium state from a density and a velocity field (computed in FP64, rounded
+// once): m_eq(rho, u) of Eq. 3 with the self-tuning eta (alpha_1 = -1, beta_1 = 1,
+// alpha_2 = 1), momentum rho u (c = 1), minus rho_ref M w, then the inverse
+// transform M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+// ux = uy = null: the rest state (u = 0).
 template <typename store_t>
-__global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny, Strides st,
-                            VCoef<double> c) {
+__global__ void k_init_eq(const double* __restrict__ rho0, const double* __restrict__ ux0,
+                          const double* __restrict__ uy0, store_t* __restrict__ f, int nx, int ny, Strides st,
+                          VCoef<double> c) {
   const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= size_t(nx) * ny) return;
   const size_t N = size_t(st.ps);                                    // plane stride
   const size_t n = size_t(st.at(0, int(k % nx), int(k / nx)));        // node (x, y)
   const double rho = rho0[k];
+  const double ux = ux0 ? ux0[k] : 0.0, uy = uy0 ? uy0[k] : 0.0;
   double pe, dpe;
   eos(c, rho, pe, dpe);
   const double eta = 3.0 * (pe + 0.5 * c.G2 * rho * rho) - rho;
+  const double x2 = ux * ux, y2 = uy * uy, r3u2 = 3.0 * rho * (x2 + y2);
+  const double m1 = 2.0 * (eta - rho) + r3u2;
+  const double m2 = 9.0 * rho * x2 * y2 + (c.beta2 * eta + rho) - r3u2;
   const double n0 = (rho - c.rho_ref) / 9.0;
-  const double n1 = (-2.0 * rho + 2.0 * eta + 2.0 * c.rho_ref) / 36.0;
-  const double n2 = (rho + c.beta2 * eta - c.rho_ref) / 36.0;
+  const double n1 = (m1 + 2.0 * c.rho_ref) / 36.0;
+  const double n2 = (m2 - c.rho_ref) / 36.0;
+  const double n3 = rho * ux / 6.0, n5 = rho * uy / 6.0;
+  const double n4 = rho * ux * (3.0 * y2 - 1.0) / 12.0, n6 = rho * uy * (3.0 * x2 - 1.0) / 12.0;
+  const double n7 = rho * (x2 - y2) / 4.0, n8 = rho * ux * uy / 4.0;
   const double axis = n0 - n1 - 2.0 * n2, diag = n0 + 2.0 * n1 + n2;
-  if constexpr (sizeof(store_t) == 8) {
-    f[n] = n0 - 4.0 * n1 + 4.0 * n2;
-    for (int i = 1; i <= 4; ++i) f[i * N + n] = axis;
-    for (int i = 5; i <= 8; ++i) f[i * N + n] = diag;
-  } else {
-    st_st(f + n, float(n0 - 4.0 * n1 + 4.0 * n2));
-    for (int i = 1; i <= 4; ++i) st_st(f + i * N + n, float(axis));
-    for (int i = 5; i <= 8; ++i) st_st(f + i * N + n, float(diag));
+  const double px = n3 - 2.0 * n4, py = n5 - 2.0 * n6, qx = n3 + n4, qy = n5 + n6;
+  double o[9];
+  o[0] = n0 - 4.0 * n1 + 4.0 * n2;
+  o[1] = axis + n7 + px;
+  o[2] = axis - n7 + py;
+  o[3] = axis + n7 - px;
+  o[4] = axis - n7 - py;
+  o[5] = diag + n8 + (qx + qy);
+  o[6] = diag - n8 + (qy - qx);
+  o[7] = diag + n8 - (qx + qy);
+  o[8] = diag - n8 + (qx - qy);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    if constexpr (sizeof(store_t) == 8)
+      f[i * N + n] = o[i];
+    else
+      st_st(f + i * N + n, float(o[i]));
   }
 }
 

@@ -211,3 +211,55 @@ def sigma_slopes(trs=tuple(SIGMA_SWEEP), n: int = 512, radius: float = 128.0, st
         s, b = slope(SIGMA_SWEEP[Tr], [r["sigma"] for r in runs])
         out[Tr] = {"slope": s, "intercept": b, "sigma": [r["sigma"] for r in runs], "K_int": list(SIGMA_SWEEP[Tr])}
     return out
+
+
+# ---------------------------------------------------------------------------
+# Galilean invariance: a translating droplet (the test the paper's R, T, X
+# corrections are for; main text after Eq. 10, supplement Eqs. 33-40).
+
+def translating_droplet(U: float = 0.05, steps: int = 2000, relax: int = 4000, nx: int = 256, ny: int = 128,
+                        radius: float = 24.0, width: float = 5.0, precision: str = "fp32", Tr: float = 0.85) -> dict:
+    """A droplet relaxed at rest, then restarted twice from the equilibrium of its
+    relaxed density: at rest, and with a uniform velocity U along x.  After `steps`
+    steps (U * steps a whole number of nodes) the moving droplet, shifted back by
+    U * steps, is compared with the resting one: in a Galilean-invariant model the
+    two density fields are the same.  Returns the largest density difference
+    relative to rho_l - rho_g, the difference of the liquid densities at the
+    droplet centres, and the drift of the droplet's centre (periodic centroid of
+    rho - rho_mid along x) from U * steps."""
+    import torch
+
+    from . import Lattice, derive, inputs
+
+    shift = U * steps
+    if abs(shift - round(shift)) > 1e-9:
+        raise ValueError("U * steps must be a whole number of nodes")
+    shift = int(round(shift))
+    d = derive(nx, ny, Tr=Tr)
+    rg, rl = d["rho_g"], d["rho_l"]
+    rho0 = inputs.droplet(nx, ny, radius, width, rg, rl)
+    base = Lattice(rho0, precision=precision, Tr=Tr)
+    base.step(relax)
+    rho_r = base.moments(velocity=False).double()
+    base.close()
+    runs = {}
+    for u in (0.0, U):
+        lat = Lattice(rho0, precision=precision, Tr=Tr)
+        lat.set_equilibrium(rho_r, torch.full_like(rho_r, u), None)
+        lat.step(steps)
+        runs[u] = lat.moments(velocity=False).double()
+        lat.close()
+    rest, moving = runs[0.0], torch.roll(runs[U], shifts=-shift, dims=1)
+    level = 0.5 * (rg + rl)
+
+    def centre_x(r):
+        w = (r - level).clamp(min=0).sum(dim=0)
+        ang = 2 * math.pi * torch.arange(nx, dtype=torch.float64, device=r.device) / nx
+        return float(torch.atan2((w * torch.sin(ang)).sum(), (w * torch.cos(ang)).sum())) * nx / (2 * math.pi)
+
+    drift = (centre_x(runs[U]) - centre_x(rest) - shift + nx / 2) % nx - nx / 2
+    cy, cx = ny // 2, nx // 2
+    return {"U": U, "steps": steps, "shift": shift, "precision": precision, "Tr": Tr,
+            "max_drho_rel": float((moving - rest).abs().max() / (rl - rg)),
+            "rho_centre_rel": float((moving[cy, cx] - rest[cy, cx]) / rest[cy, cx]),
+            "centre_drift": float(drift), "finite": bool(torch.isfinite(runs[U]).all())}

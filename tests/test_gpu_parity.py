@@ -289,3 +289,28 @@ def test_stream_copy_leaves_the_state(precision):
     a.step(5)
     b.step(5)
     assert torch.equal(a.state(), b.state())
+
+
+@pytest.mark.parametrize("layout", ["planes", "rows"])
+def test_set_equilibrium_matches_oracle(orc, layout):
+    """lb_set_equilibrium (equilibrium of Eq. 3 for a density and velocity field)
+    against the oracle's equilibrium, then 100 FP64 steps from it; the FP32 state
+    is the FP64 one rounded once."""
+    import torch
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    nx, ny = 70, 45
+    rng = np.random.default_rng(11)
+    rho = inputs.droplet(nx, ny, 12, 6, p.rho_g, p.rho_l) * (1 + 0.01 * rng.uniform(-1, 1, (ny, nx)))
+    ux, uy = 0.05 * rng.uniform(-1, 1, (ny, nx)), 0.05 * rng.uniform(-1, 1, (ny, nx))
+    f0 = orc.init_eq(p, rho, ux, uy)
+    lat = lattice(rho, "fp64", layout=layout, Tr=0.85, K_int=1.0)
+    lat.set_equilibrium(rho, ux, uy)
+    assert rel_inf(gpu_populations(lat), f0) <= 1e-15
+    lat.step(100)
+    torch.cuda.synchronize()
+    assert rel_inf(gpu_populations(lat), orc.step(p, f0, 100)) <= 1e-12
+    l32 = lattice(rho, "fp32", layout=layout, Tr=0.85, K_int=1.0)
+    l32.set_equilibrium(rho, ux, None)
+    ref = orc.init_eq(p, rho, ux, None)
+    assert rel_inf(gpu_populations(l32), ref) <= 2e-7
