@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "lbm_handle.cuh"
+#include "lbm_fields.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "lbm_handle.cuh"
+#include "lbm_fields.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {

@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "lbm_handle.cuh"
+#include "lbm_fields.cuh"
 
 namespace {
 
