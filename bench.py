@@ -622,6 +622,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "kernel": kernel, "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
+            "traffic_GBps": round(traffic / (ms_step * 1e-3) / 1e9, 1) if traffic else None,
             "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
             "kernel_source_sha": src_hash,
             "pattern_ceiling": {"GBps": round(pattern_gbs, 1), "frac": round(achieved / pattern_gbs, 4),
