@@ -135,8 +135,10 @@ size_t lb_scratch_bytes(const lb_params* p);
  * lattice at rest: fbar_i = (M^-1 m_eq(rho0, u = 0))_i - w_i rho_ref, with eta
  * from the EOS at rho0 (the stated initial condition; the paper does not give
  * one).  f_a, f_b: device buffers of lb_state_bytes() each (ping-pong; f_a holds
- * the state after init).  scratch: device buffer of lb_scratch_bytes() bytes,
- * or NULL when that is 0.  rho0: nx*ny doubles, row-major [y][x], on the host
+ * the state after init).  scratch: device buffer of lb_scratch_bytes() bytes, or
+ * NULL (the fused step then walks its tiles statically, and lb_reduce and the
+ * two-pass variant are unavailable); it holds the tile tickets of the fused step,
+ * so handles that step concurrently need scratch buffers of their own.  rho0: nx*ny doubles, row-major [y][x], on the host
  * (rho0_on_device = 0; copied through f_b, synchronously) or the device (1).
  * The handle keeps the pointers; the caller keeps ownership and must keep the
  * buffers alive until lb_free.  Fails with LB_EINVAL for bad parameters or
