@@ -117,3 +117,25 @@ def test_batch_rejects_mixed_layouts_before_any_gpu_work(capi):
     meta = capi.lib().lb_batch_meta_bytes(ps, 2)
     rc = capi.lib().lb_batch_init(ctypes.byref(b), ps, 2, 1 << 40, 2 << 40, 3 << 40, meta, rho.ctypes.data, 0, None)
     assert rc == capi.LB_ENOTSUP and "share the layout" in capi.lb_last_error(None)
+
+
+def test_new_entry_points_reject_null_handles(capi):
+    """The equilibrium, dispatch and tuning calls check their handle
+    before any GPU work."""
+    lib = capi.lib()
+    assert lib.lb_set_equilibrium(None, None, None, None) == capi.LB_EINVAL
+    assert lib.lb_set_tile_dispatch(None, 1) == capi.LB_EINVAL
+    assert lib.lb_tile_dispatch(None) == 0
+    assert lib.lb_set_step_blocks(None, 0) == capi.LB_EINVAL
+    assert lib.lb_uses_tma(None) == 0
+
+
+def test_scratch_holds_the_tile_tickets(capi):
+    """Scratch = one density plane (rounded to 256 bytes) + the reduction workspace
+    + 256 bytes of tile tickets; FP16 and FP32 planes are float, FP64 double."""
+    p = capi.make_params(100, 30, precision=capi.LB_FP32)
+    q = capi.make_params(100, 30, precision=capi.LB_FP64)
+    plane32 = (100 * 30 * 4 + 255) // 256 * 256
+    plane64 = (100 * 30 * 8 + 255) // 256 * 256
+    assert capi.lb_scratch_bytes(q) - capi.lb_scratch_bytes(p) == plane64 - plane32
+    assert capi.lb_scratch_bytes(p) >= plane32 + 256
