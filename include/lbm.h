@@ -334,10 +334,11 @@ int lb_tile_dispatch(const lb_handle* h);
  * (the fastest copy of that pattern measured). */
 int lb_stream_copy(lb_handle* h);
 
-/* Grid of that persistent kernel (each block steps tiles b, b + blocks, ...):
- * blocks > 0 fixes it (at most the tile count), 0 restores the default (as many
- * blocks as can be resident).  LB_EINVAL if blocks < 0.  Results do not depend
- * on it; it exists for tuning and for tests of the per-block tile loop. */
+/* Grid of the persistent tensor-copy step, in either tile dispatch (static walk:
+ * each block steps tiles b, b + blocks, ...; tickets: tiles b and b + blocks, then
+ * by ticket): blocks > 0 fixes it (at most the tile count), 0 restores the default
+ * (as many blocks as can be resident).  LB_EINVAL if blocks < 0.  Results do not
+ * depend on it; it exists for tuning and for tests of the per-block tile loop. */
 int lb_set_step_blocks(lb_handle* h, int blocks);
 
 /* Derived parameters in use by the handle. */
