@@ -188,7 +188,27 @@ def cpu_baseline(rho0, seconds: float = 12.0) -> dict:
     out = {"value": round(256 * 256 * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
            "sample": "%d steps of the FP64 oracle on a 256x256 periodic crop of the workload" % steps}
     out["all_cores"] = cpu_baseline_all_cores(rho0, seconds=0.75 * seconds)
+    out["host"] = {"cpu": host_cpu(), "nproc": os.cpu_count()}
     return out
+
+
+def host_cpu() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def _oracle_rate(job):
