@@ -51,7 +51,7 @@ extern "C" {
 #define LB_EINVAL (-1)     /* invalid argument or parameter */
 #define LB_ECUDA (-2)      /* CUDA runtime error (message has the CUDA error string) */
 #define LB_ENOMEM (-3)     /* caller-provided scratch too small */
-#define LB_ENONFINITE (-4) /* non-finite density found by lb_status / lb_reduce */
+#define LB_ENONFINITE (-4) /* non-finite density found by lb_reduce / lb_batch_status */
 #define LB_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define LB_ENOTSUP (-6)    /* combination not supported */
 
@@ -177,22 +177,25 @@ int lb_pressure(lb_handle* h, void* p);
 int lb_reduce(lb_handle* h, double out[8]);
 
 /* lb_reduce for callers that cannot allocate device memory (the paper has no
- * counterpart).  Such callers exist: a host program whose allocator owns the whole
- * GPU and grants no further buffers, a plugin inside such a program, or code that
- * runs while a stream is captured into a CUDA graph, where an allocation would
- * break the capture.  Same results as lb_reduce (same kernels, same order), but the
+ * counterpart).  Such callers exist: a host program whose own allocator has taken
+ * the whole GPU and grants no further buffers, or a plugin inside such a program,
+ * which receives the lattice from its host and has no allocator of its own.  Same
+ * results as lb_reduce (same kernels, same block count, same order), but the
  * scratch is a file-scope static device array inside the library, of
- * LB_REDUCE_STATIC_MAX_NODES * 8 + 65600 bytes (about 8.1 MB), which every GPU
- * that loads the library holds until the process exits.  Nothing is allocated:
- * no cudaMalloc / cudaFree, no allocating library routine.  The handle may have
- * been created with scratch = NULL.
+ * LB_REDUCE_STATIC_MAX_NODES * 8 + 65600 bytes (about 8.1 MB).  lb_init commits
+ * that array on its device (it looks up the array's address there, with the
+ * device current, which loads the module holding it), so every GPU on which a
+ * handle has been created holds it until the process exits, and a later call
+ * cannot fail for want of memory.  Nothing is allocated by the call: no
+ * cudaMalloc / cudaFree, no allocating library routine.  The handle may have been
+ * created with scratch = NULL.
  * Limits: lattices above LB_REDUCE_STATIC_MAX_NODES nodes are rejected with
- * LB_ENOMEM (use lb_reduce).  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  All calls share the one array and each
- * call writes every element it reads, so nothing carries over between calls, but
- * calls whose GPU work overlaps (several streams or threads at once) race on it
- * and must be serialised by the caller.  Synchronous like lb_reduce. */
+ * LB_ENOMEM (use lb_reduce).  All calls share the one array and each call writes
+ * every element it reads, so nothing carries over between calls, but calls whose
+ * GPU work overlaps (several streams or threads at once) race on it and must be
+ * serialised by the caller.  Synchronous like lb_reduce: it waits on the handle's
+ * stream, so it must not be called while that stream is being captured into a
+ * CUDA graph. */
 #define LB_REDUCE_STATIC_MAX_NODES 1048576
 int lb_reduce_static(lb_handle* h, double out[8]);
 
@@ -239,8 +242,9 @@ int lb_adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, 
  * the lattices' lb_params.layout is LB_LAYOUT_ROWS (one layout per batch), with the
  * row stride sx = lb_batch_row_stride(i) = nx rounded up to a multiple of 4;
  * columns nx..sx-1 are padding, never read or written) and a metadata buffer of
- * lb_batch_meta_bytes (descriptors, coefficients, tensor maps; the maps hold the
- * pools' addresses, so the pools must not move while the batch lives).
+ * lb_batch_meta_bytes (descriptors, coefficients, tensor maps, per-lattice
+ * counters of the non-finite check; the maps hold the pools' addresses, so the
+ * pools must not move while the batch lives).
  * rho0: the initial densities of all lattices concatenated ([y][x] each), host
  * (staged through pool_b, synchronous) or device.  A stream of NULL (the legacy
  * default stream) cannot be captured: lb_batch_run then launches step by step. */
@@ -270,9 +274,19 @@ int lb_batch_uses_tma(const lb_batch* b);
  * outside the ranges (blocks_per_sm at most the resident maximum), LB_ENOTSUP for
  * 3 - 6 when a lattice has no tensor map. */
 int lb_batch_set_config(lb_batch* b, int shape, int blocks_per_sm);
-/* Synchronous: LB_ETIMEOUT if a bounded wait of the tensor-copy kernel gave up
- * since the last call (the flag is cleared), else LB_OK. */
+/* Synchronous health check: LB_ETIMEOUT if a bounded wait of the tensor-copy
+ * kernel gave up since the last call (the flag is cleared); else LB_ENONFINITE if
+ * any lattice of the current state has a node whose density (the sum of its nine
+ * populations) is not finite, with the lattice indices in lb_batch_last_error;
+ * else LB_OK.  The check reads every population once (one kernel). */
 int lb_batch_status(lb_batch* b);
+/* Non-finite check of every lattice of the current state (synchronous, the
+ * check of lb_batch_status): counts[i] (host array of n, or NULL) = number of
+ * nodes of lattice i whose density is not finite.  Returns the number of
+ * lattices with at least one such node (0 = all finite), or a negative error
+ * code.  A lattice goes non-finite when the method itself is unstable for its
+ * parameters (thin interfaces at low temperature); the others are unaffected. */
+int lb_batch_nonfinite(lb_batch* b, uint32_t* counts);
 /* Device pointer of the pool holding the current state; element offset of lattice i. */
 void* lb_batch_state(lb_batch* b);
 int64_t lb_batch_steps_done(const lb_batch* b);
@@ -296,9 +310,11 @@ int lb_set_equilibrium(lb_handle* h, const double* rho, const double* ux, const 
 int lb_get_state(lb_handle* h, void* dst);
 int lb_set_state(lb_handle* h, const void* src);
 
-/* Synchronous health check: LB_ETIMEOUT if a kernel's bounded wait for an
- * asynchronous tensor copy gave up since the last call (the flag is cleared),
- * else LB_OK.  Kernels never spin without a limit. */
+/* Synchronous health check of this handle: LB_ETIMEOUT if a bounded wait of one
+ * of its kernels (step or adjoint) for an asynchronous tensor copy gave up since
+ * the last call (the handle's own device flag is cleared), else LB_OK.  Each
+ * handle has its own flag, so a give-up is reported on the handle whose kernel
+ * had it.  Kernels never spin without a limit. */
 int lb_status(lb_handle* h);
 
 /* Check of the reporting above, for users and tests (no counterpart in the paper):

@@ -227,8 +227,14 @@ class Batch:
         return pool[off:off + 9 * sx * ny].view(9, ny, sx)[:, :, :nx]
 
     def status(self) -> None:
-        """Raises LBError if a bounded wait of the tensor-copy kernel gave up."""
+        """Raises LBError if a bounded wait of the tensor-copy kernel gave up
+        (LB_ETIMEOUT) or a lattice has a non-finite density (LB_ENONFINITE)."""
         capi.lb_batch_status(self.b)
+
+    def nonfinite(self) -> list[int]:
+        """Indices of the lattices whose current state has a non-finite density."""
+        _, counts = capi.lb_batch_nonfinite(self.b, self.n)
+        return [i for i, c in enumerate(counts) if c]
 
     def density(self, i: int):
         return self.state(i).double().sum(0) + self.rho_refs[i]

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("lb_batch_tune", ctypes.c_int, [_V, ctypes.c_int, _D]),
     ("lb_batch_config", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]),
+    ("lb_batch_nonfinite", ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_uint32)]),
     ("lb_batch_state", _V, [_V]),
     ("lb_batch_steps_done", ctypes.c_int64, [_V]),
     ("lb_batch_offset", ctypes.c_int64, [_V, ctypes.c_int]),
@@ -269,6 +270,15 @@ def lb_batch_set_config(b: int, shape: int, blocks_per_sm: int) -> None:
 
 def lb_batch_status(b: int) -> None:
     check_batch(lib().lb_batch_status(b), b)
+
+
+def lb_batch_nonfinite(b: int, n: int) -> tuple[int, list[int]]:
+    """(number of lattices with a non-finite density, per-lattice node counts)."""
+    counts = (ctypes.c_uint32 * n)()
+    rc = lib().lb_batch_nonfinite(b, counts)
+    if rc < 0:
+        check_batch(rc, b)
+    return rc, list(counts)
 
 
 def lb_batch_state(b: int) -> int:

@@ -550,7 +550,7 @@ int adjoint_steps(lb_handle* h, const void* const* states, int k, void* lam, dou
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 0;
   if constexpr (sizeof(real) == 4 && sizeof(store_t) == 4) {
-    if (h->wait_error && async_window_ok(nx, ny) && nx % 4 == 0 && sms > 0 &&
+    if (h->use_tma && h->wait_error && async_window_ok(nx, ny) && nx % 4 == 0 && sms > 0 &&
         size_t(grd.x) * grd.y >= size_t(4) * 3 * sms) {
       const cudaError_t a =
           cudaFuncSetAttribute(k_adj_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kAdjStageSmem));

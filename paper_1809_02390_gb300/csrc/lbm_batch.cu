@@ -314,6 +314,32 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
   }
 }
 
+// Non-finite check of every lattice of a batch: one block per tile of the
+// 32 x 16 tile list, each thread the two nodes (x0 + tx, y0 + ty) and
+// (x0 + tx, y0 + ty + 8); a node counts when the sum of its nine stored
+// populations is not finite.  The block's count goes to bad[lattice].
+__global__ void __launch_bounds__(kFusedThreads) k_batch_nonfinite(const float* __restrict__ pool,
+                                                                    const TileRec* __restrict__ tiles, int rows,
+                                                                    unsigned* __restrict__ bad) {
+  const TileRec t = tiles[blockIdx.x];
+  const int x = t.x0 + (threadIdx.x & (kTileX - 1));
+  const Strides st = rows ? Strides{t.sx, 9 * t.sx} : Strides{t.sx * t.ny, t.sx};
+  int n = 0;
+#pragma unroll
+  for (int k = 0; k < kTileRows; ++k) {
+    const int y = t.y0 + int(threadIdx.x / kTileX) + k * kRowStride;
+    if (x < t.nx && y < t.ny) {
+      const float* f = pool + t.offset;
+      float sum = 0.f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sum += f[st.at(i, x, y)];
+      n += isfinite(sum) ? 0 : 1;
+    }
+  }
+  const int total = __syncthreads_count(n > 0) + __syncthreads_count(n > 1);
+  if (threadIdx.x == 0 && total > 0) atomicAdd(bad + t.lat, unsigned(total));
+}
+
 template <int TY, int MINB>
 void launch_shape(const float* in, float* out, const TileRec* tiles, const LatCoef<f2>* coef, int total, int bps,
                   int sms, const VCoef<f2>& common, cudaStream_t st, int rows) {
@@ -353,6 +379,8 @@ struct lb_batch {
   CUtensorMap* d_maps;  // [2][n]: lattice maps in pool 0, then in pool 1
   int* d_err;           // set by a bounded wait of the tensor-copy kernel that gave up
   unsigned* d_queue;    // tickets of the dispatch shapes (two words)
+  unsigned* d_bad;      // per lattice: nodes whose density is not finite (lb_batch_nonfinite)
+  std::vector<unsigned> h_bad;
   bool tma_ok;          // every lattice large enough to have interior tiles has its maps
   int rows;             // pools in the rows layout f[ny][9][sx] (else planes f[9][ny][sx])
   VCoef<f2> common;
@@ -470,8 +498,9 @@ size_t lb_batch_meta_bytes(const lb_params* ps, int n) {
   if (!ps || n < 1) return 0;
   size_t tiles = 0;
   for (int s = 0; s < kTileLists; ++s) tiles += total_tiles_of(ps, n, kShapeTY[s]);
-  return size_t(n) * (kTileLists * sizeof(BatchLattice) + sizeof(LatCoef<f2>) + 2 * sizeof(CUtensorMap)) +
-         tiles * sizeof(TileRec) + 4096 + 256;
+  return size_t(n) * (kTileLists * sizeof(BatchLattice) + sizeof(LatCoef<f2>) + 2 * sizeof(CUtensorMap) +
+                      sizeof(unsigned)) +
+         tiles * sizeof(TileRec) + 4096 + 512;
 }
 
 int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
@@ -578,6 +607,9 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   b->d_err = reinterpret_cast<int*>(m);
   m = align(m + sizeof(int));
   b->d_queue = reinterpret_cast<unsigned*>(m);
+  m = align(m + 2 * sizeof(unsigned));
+  b->d_bad = reinterpret_cast<unsigned*>(m);
+  b->h_bad.assign(size_t(n), 0u);
   // Tensor maps of every lattice in both pools.  A lattice below 40 x 18 has no
   // interior tile (those need nx >= 68, ny >= 34) and keeps a zero map it never uses.
   std::vector<CUtensorMap> h_maps(2 * size_t(n));
@@ -734,6 +766,33 @@ int lb_batch_set_config(lb_batch* b, int shape, int blocks_per_sm) {
 
 int lb_batch_uses_tma(const lb_batch* b) { return b && is_tma(b->shape) ? 1 : 0; }
 
+}  // extern "C"
+
+namespace {
+
+// Counts the non-finite densities of every lattice of the current state into
+// b->h_bad (synchronous); returns the number of lattices with any, or an error.
+int count_nonfinite(lb_batch* b) {
+  cudaError_t e = cudaMemsetAsync(b->d_bad, 0, size_t(b->n) * sizeof(unsigned), b->stream);
+  if (e == cudaSuccess && b->total_tiles[0] > 0) {
+    k_batch_nonfinite<<<unsigned(b->total_tiles[0]), kFusedThreads, 0, b->stream>>>(
+        static_cast<const float*>(b->pool[b->cur]), b->d_tiles[0], b->rows, b->d_bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->h_bad.data(), b->d_bad, size_t(b->n) * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "non-finite check: %s", cudaGetErrorString(e));
+  int lattices = 0;
+  for (unsigned v : b->h_bad) lattices += v ? 1 : 0;
+  return lattices;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lb_batch_status(lb_batch* b) {
   if (!b) return LB_EINVAL;
   int v = 0;
@@ -741,7 +800,32 @@ int lb_batch_status(lb_batch* b) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess && v) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   if (e != cudaSuccess) return berr(b, LB_ECUDA, "lb_batch_status: %s", cudaGetErrorString(e));
-  return v ? berr(b, LB_ETIMEOUT, "a bounded wait for a tensor copy gave up%s") : LB_OK;
+  if (v) return berr(b, LB_ETIMEOUT, "a bounded wait for a tensor copy gave up%s");
+  const int bad = count_nonfinite(b);
+  if (bad < 0) return bad;
+  if (bad > 0) {
+    char list[256] = {0};
+    size_t used = 0;
+    int shown = 0;
+    for (int i = 0; i < b->n && shown < 16; ++i)
+      if (b->h_bad[i]) {
+        used += size_t(std::snprintf(list + used, sizeof(list) - used, "%s%d", shown ? ", " : "", i));
+        ++shown;
+        if (used >= sizeof(list)) break;
+      }
+    std::snprintf(b->err, sizeof(b->err), "%d lattice(s) have non-finite densities: %s%s", bad, list,
+                  bad > shown ? ", ..." : "");
+    return LB_ENONFINITE;
+  }
+  return LB_OK;
+}
+
+int lb_batch_nonfinite(lb_batch* b, uint32_t* counts) {
+  if (!b) return LB_EINVAL;
+  const int bad = count_nonfinite(b);
+  if (bad < 0) return bad;
+  if (counts) std::memcpy(counts, b->h_bad.data(), size_t(b->n) * sizeof(uint32_t));
+  return bad;
 }
 
 void* lb_batch_state(lb_batch* b) { return b ? b->pool[b->cur] : nullptr; }

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <type_traits>
 
@@ -147,8 +148,6 @@ size_t rho_plane_bytes(const lb_params* p) {
   return (size_t(p->nx) * p->ny * real_bytes(p->precision) + 255) / 256 * 256;
 }
 
-constexpr int kMaxReduceBlocks = 1024;
-
 size_t reduce_bytes() { return size_t(kMaxReduceBlocks) * kReduceSlots * sizeof(double) + 256; }
 constexpr size_t kQueueBytes = 256;  // tile tickets of the dynamic tensor-copy step
 
@@ -256,8 +255,36 @@ bool encode_plane_map(CUtensorMap* map, const void* base, int nx, int ny, int pl
 
 namespace {
 
-// Set by a bounded wait of the tensor-copy step that gave up (read and cleared by lb_status).
-__device__ int g_wait_error;
+// One word per live handle, set by a bounded wait of that handle's tensor-copy
+// step or adjoint that gave up (read and cleared by lb_status on the handle).
+// Slots are handed out by lb_init and returned by lb_free; the same slot index
+// serves the handle on whichever device it lives (each device has its own array).
+constexpr int kWaitSlots = 4096;
+__device__ int g_wait_flags[kWaitSlots];
+std::mutex g_slot_mu;
+bool g_slot_used[kWaitSlots] = {false};
+
+int take_wait_slot() {
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  for (int i = 0; i < kWaitSlots; ++i)
+    if (!g_slot_used[i]) {
+      g_slot_used[i] = true;
+      return i;
+    }
+  return -1;
+}
+
+void release_wait_slot(lb_handle* h) {
+  if (!h || h->wait_slot < 0) return;
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  g_slot_used[h->wait_slot] = false;
+  h->wait_slot = -1;
+}
+
+void destroy(lb_handle* h) {
+  release_wait_slot(h);
+  delete h;
+}
 
 // The step's memory traffic without its arithmetic: one block per 32 x 16 tile
 // (the step's tiles), each thread moving the nine populations of its two nodes
@@ -316,7 +343,19 @@ __global__ void k_wait_selftest(long long polls, int* __restrict__ err) {
 }
 
 int configure(lb_handle* h) {
-  const int rc = configure_device(h);
+  int rc = configure_device(h);
+  if (rc != LB_OK) return rc;
+  // This handle's wait word (cleared: a slot may come from a freed handle).
+  h->wait_slot = take_wait_slot();
+  if (h->wait_slot < 0) return fail(h, LB_ENOMEM, "more than %d live handles", kWaitSlots);
+  void* w = nullptr;
+  LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_flags));
+  h->wait_error = static_cast<int*>(w) + h->wait_slot;
+  LB_CUDA(h, cudaMemsetAsync(h->wait_error, 0, sizeof(int), h->stream));
+  // lb_reduce_static's array is committed now, while the caller can still spare
+  // the memory, rather than at its first call.
+  void* st = nullptr;
+  rc = static_scratch_address(h, &st);
   if (rc != LB_OK) return rc;
   // The tensor-copy path needs FP32 or FP16 storage, rows of a multiple of 16
   // bytes and a lattice holding at least one interior tile; otherwise the plain
@@ -329,9 +368,6 @@ int configure(lb_handle* h) {
                encode_population_map(&h->tmap[0], h->f[0], h->p.nx, h->p.ny, h->p.nx, eb, rows) &&
                encode_population_map(&h->tmap[1], h->f[1], h->p.nx, h->p.ny, h->p.nx, eb, rows);
   if (h->use_tma) {
-    void* w = nullptr;
-    LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_error));
-    h->wait_error = static_cast<int*>(w);
     // Persistent grid: as many blocks as can be resident.
     const void* k = fp32 ? reinterpret_cast<const void*>(k_step_tma<f2, float, false>)
                          : reinterpret_cast<const void*>(k_step_tma<f2, __half, false>);
@@ -405,17 +441,11 @@ int run_reduce(lb_handle* h, double out[8]) {
   LB_CUDA(h, cudaMemcpyAsync(&probe[1], rho, sizeof(real), cudaMemcpyDeviceToHost, h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   // p_EOS / c^2 at the two probe nodes, FP64 on the host.
-  const VCoef<double>& cd = h->cd;
-  auto pe = [&](double r) {
-    if (cd.eos == LB_EOS_VDW) return cd.lam * (r * cd.RT / (1.0 - cd.bq * r) - cd.a * r * r);
-    const double t = cd.bq * r, om = 1.0 - t;
-    return cd.lam * (r * cd.RT * (1.0 + t + t * t - t * t * t) / (om * om * om) - cd.a * r * r);
-  };
   out[0] = res[0];
   out[1] = res[1];
   out[2] = res[2];
-  out[3] = pe(double(probe[0]));
-  out[4] = pe(double(probe[1]));
+  out[3] = p_eos_host(h->cd, double(probe[0]));
+  out[4] = p_eos_host(h->cd, double(probe[1]));
   out[5] = res[3];
   out[6] = res[4];
   out[7] = res[5];
@@ -464,15 +494,6 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   if (variant == LB_TWO_PASS && !scratch)
     return fail(nullptr, LB_ENOMEM, "the two-pass variant needs %zu bytes of scratch", lb_scratch_bytes(p));
   const size_t N = size_t(p->nx) * p->ny;
-  if (!rho0_on_device) {
-    for (size_t n = 0; n < N; ++n)
-      if (!(rho0[n] > 0) || !std::isfinite(rho0[n]))
-        return fail(nullptr, LB_EINVAL, "initial density at node %zu is not positive and finite", n);
-    if (p->eos == LB_EOS_VDW)
-      for (size_t n = 0; n < N; ++n)
-        if (!(p->eos_b * rho0[n] < 1.0))
-          return fail(nullptr, LB_EINVAL, "initial density at node %zu exceeds 1/b of the vdW EOS", n);
-  }
   lb_handle* h = new (std::nothrow) lb_handle();
   if (!h) return fail(nullptr, LB_EINVAL, "out of host memory");
   h->p = *p;
@@ -491,24 +512,38 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   h->cf = make_vcoef<float>(h->p, d);
   h->c2 = make_vcoef<f2>(h->p, d);
   h->cd = make_vcoef<double>(h->p, d);
+  h->wait_slot = -1;
   rc = configure(h);
   if (rc != LB_OK) {
     set_thread_error(h->err);
-    delete h;
+    destroy(h);
     return rc;
   }
   const double* rho_dev = rho0;
   auto bail = [&](cudaError_t e, const char* what) {
     fail(nullptr, LB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-    delete h;
+    destroy(h);
     return LB_ECUDA;
   };
   cudaError_t e;
+  // Host densities: staged in the second population buffer (9 x >= 2 bytes per
+  // node hold the 8 of the density and, after them, the two words of the check)
+  // and checked there by k_check_rho0 (positive, finite, below 1/b for vdW).
+  unsigned long long* bad = nullptr;
   if (!rho0_on_device) {
-    // Stage the host densities in the second population buffer (>= 8 bytes per node).
+    bad = reinterpret_cast<unsigned long long*>(static_cast<char*>(f_b) + N * sizeof(double));
+    e = cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), h->stream);
+    if (e != cudaSuccess) return bail(e, "cudaMemsetAsync(check)");
     e = cudaMemcpyAsync(f_b, rho0, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return bail(e, "cudaMemcpyAsync(rho0)");
     rho_dev = static_cast<const double*>(f_b);
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms < 1)
+      sms = 1;
+    const size_t want = (N + 255) / 256, cap = size_t(sms) * 8;
+    k_check_rho0<<<unsigned(want < cap ? want : cap), 256, 0, h->stream>>>(rho_dev, N, p->eos == LB_EOS_VDW,
+                                                                           p->eos_b, bad);
   }
   const unsigned blocks = unsigned((N + 255) / 256);
   switch (p->precision) {
@@ -528,8 +563,17 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   e = cudaGetLastError();
   if (e != cudaSuccess) return bail(e, "init kernel launch");
   if (!rho0_on_device) {
+    unsigned long long first[2] = {0, 0};
+    e = cudaMemcpyAsync(first, bad, sizeof(first), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return bail(e, "cudaMemcpyAsync(check)");
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+    if (first[0] != ~0ull || first[1] != ~0ull) {
+      destroy(h);
+      if (first[0] != ~0ull)
+        return fail(nullptr, LB_EINVAL, "initial density at node %llu is not positive and finite", first[0]);
+      return fail(nullptr, LB_EINVAL, "initial density at node %llu exceeds 1/b of the vdW EOS", first[1]);
+    }
   }
   *out = h;
   return LB_OK;
@@ -642,11 +686,12 @@ int lb_get_derived(const lb_handle* h, lb_derived* out) {
 
 int lb_status(lb_handle* h) {
   if (!h) return fail(nullptr, LB_EINVAL, "null handle");
-  int v = 0, zero = 0;
-  LB_CUDA(h, cudaMemcpyFromSymbolAsync(&v, g_wait_error, sizeof(int), 0, cudaMemcpyDeviceToHost, h->stream));
+  int v = 0;
+  LB_CUDA(h, cudaMemcpyAsync(&v, h->wait_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LB_CUDA(h, cudaStreamSynchronize(h->stream));
   if (v) {
-    LB_CUDA(h, cudaMemcpyToSymbolAsync(g_wait_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, h->stream));
+    LB_CUDA(h, cudaMemsetAsync(h->wait_error, 0, sizeof(int), h->stream));
+    LB_CUDA(h, cudaStreamSynchronize(h->stream));
     return fail(h, LB_ETIMEOUT, "a bounded wait for a tensor copy gave up");
   }
   return LB_OK;
@@ -655,9 +700,7 @@ int lb_status(lb_handle* h) {
 int lb_wait_selftest(lb_handle* h, long long polls) {
   if (!h) return fail(nullptr, LB_EINVAL, "null handle");
   if (polls < 1 || polls > (1ll << 22)) return fail(h, LB_EINVAL, "polls must be in [1, 2^22]");
-  void* w = nullptr;
-  LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_error));
-  k_wait_selftest<<<1, 128, 0, h->stream>>>(polls, static_cast<int*>(w));
+  k_wait_selftest<<<1, 128, 0, h->stream>>>(polls, h->wait_error);
   LB_CUDA(h, cudaGetLastError());
   return lb_status(h);
 }
@@ -699,6 +742,6 @@ int lb_tile_dispatch(const lb_handle* h) { return h && h->use_tma && h->use_dyn 
 
 const char* lb_last_error(const lb_handle* h) { return h ? h->err : thread_error(); }
 
-void lb_free(lb_handle* h) { delete h; }
+void lb_free(lb_handle* h) { destroy(h); }
 
 }  // extern "C"

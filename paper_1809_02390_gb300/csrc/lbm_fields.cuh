@@ -9,6 +9,32 @@ namespace lbm {
 
 constexpr int kReduceThreads = 256;
 constexpr int kReduceSlots = 8;  // doubles per block partial
+// Largest grid of k_reduce_partial: the partials buffer of lb_reduce (caller's
+// scratch) and of lb_reduce_static (static array) both hold this many blocks, and
+// both take min(2 x SMs, this) blocks, so the two calls sum in the same order.
+constexpr int kMaxReduceBlocks = 1024;
+
+// p_EOS / c^2 of one density in FP64 on the host (the probes of the reductions):
+// vdW rho R T/(1 - b rho) - a rho^2, Carnahan-Starling (Eq. 20) with t = b rho / 4,
+// both times K_EOS / c^2.
+inline double p_eos_host(const VCoef<double>& c, double r) {
+  if (c.eos == LB_EOS_VDW) return c.lam * (r * c.RT / (1.0 - c.bq * r) - c.a * r * r);
+  const double t = c.bq * r, om = 1.0 - t;
+  return c.lam * (r * c.RT * (1.0 + t + t * t - t * t * t) / (om * om * om) - c.a * r * r);
+}
+
+// Validation of an initial density field on the device: bad[0] = smallest index
+// of a density that is not positive and finite, bad[1] = smallest index of one at
+// or above 1/b (vdW only: 1 - b rho must stay positive); both start at
+// 0xff..ff (none).  Grid-stride loop.
+static __global__ void k_check_rho0(const double* __restrict__ rho, size_t n, int vdw, double eos_b,
+                             unsigned long long* __restrict__ bad) {
+  for (size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += size_t(gridDim.x) * blockDim.x) {
+    const double r = rho[k];
+    if (!(r > 0.0) || !isfinite(r)) atomicMin(&bad[0], static_cast<unsigned long long>(k));
+    if (vdw && !(eos_b * r < 1.0)) atomicMin(&bad[1], static_cast<unsigned long long>(k));
+  }
+}
 
 // Equilibrium state from a density and a velocity field (computed in FP64, rounded
 // once): m_eq(rho, u) of Eq. 3 with the self-tuning eta (alpha_1 = -1, beta_1 = 1,

@@ -25,7 +25,8 @@ struct lb_handle {
   bool use_dyn;           // the tensor-copy step takes tiles by ticket (k_step_tma_dyn)
   int dyn_grid, dyn_grid_auto;
   CUtensorMap tmap[2];    // 3-D maps of f[0] and f[1]: (x, y, plane), rows layout (x, plane, y)
-  int* wait_error;        // device word set by a bounded wait that gave up
+  int* wait_error;        // this handle's device word, set by a bounded wait that gave up
+  int wait_slot;          // its index in the library's array of such words (-1: none taken)
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
   lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
   lbm::VCoef<double> cd;
@@ -42,4 +43,7 @@ bool encode_population_map(CUtensorMap* map, void* base, int nx, int ny, int sx,
 // 3-D map (x, y, plane) of `planes` FP32 planes of nx x ny, box cols x rows x 1
 // (lbm_capi.cu); false if the buffer does not allow one.
 bool encode_plane_map(CUtensorMap* map, const void* base, int nx, int ny, int planes, int cols, int rows);
+// Device address of lb_reduce_static's static scratch on the current device
+// (looked up once per device, which commits the array there; lbm_static.cu).
+int static_scratch_address(lb_handle* h, void** out);
 }  // namespace lbm

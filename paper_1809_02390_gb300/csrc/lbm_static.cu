@@ -1,11 +1,13 @@
 // lb_reduce_static: the diagnostics of lb_reduce for callers that cannot
 // allocate device memory.  Some callers cannot call cudaMalloc at all: a host
-// program whose allocator owns every byte of the GPU and hands out no more
-// buffers, a plugin loaded into such a program, or code that runs while a
-// stream is being captured into a CUDA graph, where an allocation would break
-// the capture.  lb_reduce needs the caller's scratch buffer; this variant keeps
-// its scratch in the file-scope device array below instead, so nothing is
-// allocated by the caller, by this library or by any library it calls.
+// program whose own allocator has taken every byte of the GPU and hands out no
+// more buffers, or a plugin loaded into such a program, which gets the lattice
+// from its host and has no allocator of its own.  lb_reduce needs the caller's
+// scratch buffer; this variant keeps its scratch in the file-scope device array
+// below instead, so nothing is allocated by the caller, by this library or by
+// any library it calls.  The call is synchronous (it copies the sums to the host
+// and waits on the handle's stream), so it must not be made on a stream that is
+// being captured into a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -19,12 +21,13 @@ namespace {
 using namespace lbm;
 
 constexpr size_t kPlaneBytes = size_t(LB_REDUCE_STATIC_MAX_NODES) * sizeof(double);
-constexpr int kStaticBlocks = 1024;
-constexpr size_t kPartialBytes = size_t(kStaticBlocks) * kReduceSlots * sizeof(double);
+constexpr size_t kPartialBytes = size_t(kMaxReduceBlocks) * kReduceSlots * sizeof(double);
 constexpr size_t kOutBytes = kReduceSlots * sizeof(double);
 
-// Density plane (as double or float) | block partials | final sums.  Every GPU
-// that loads the library holds this array until the process exits.
+// Density plane (as double or float) | block partials | final sums.  The driver
+// loads the module that holds this array, and so commits the array's memory,
+// when lb_init first looks up its address on a device (static_scratch_address);
+// from then on that GPU holds it until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kPlaneBytes + kPartialBytes + kOutBytes];
 
 // Device address of g_static_scratch for each device, looked up once per device
@@ -40,7 +43,15 @@ int set_err(lb_handle* h, int code, const char* msg, cudaError_t e = cudaSuccess
   return code;
 }
 
-int scratch_address(lb_handle* h, void** out) {
+}  // namespace
+
+namespace lbm {
+
+// Looks up (once per device, with that device current) the device address of the
+// static scratch, which loads its module and commits the array on this device.
+// lb_init calls it, so that the memory is taken when a handle is created and a
+// later lb_reduce_static cannot fail for want of device memory.
+int static_scratch_address(lb_handle* h, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_err(h, LB_ECUDA, "cudaGetDevice", e);
@@ -56,11 +67,9 @@ int scratch_address(lb_handle* h, void** out) {
   return LB_OK;
 }
 
-double p_eos_host(const VCoef<double>& c, double r) {
-  if (c.eos == LB_EOS_VDW) return c.lam * (r * c.RT / (1.0 - c.bq * r) - c.a * r * r);
-  const double t = c.bq * r, om = 1.0 - t;
-  return c.lam * (r * c.RT * (1.0 + t + t * t - t * t * t) / (om * om * om) - c.a * r * r);
-}
+}  // namespace lbm
+
+namespace {
 
 template <typename real, typename store_t>
 int reduce_static(lb_handle* h, unsigned char* base, double out[8]) {
@@ -73,7 +82,7 @@ int reduce_static(lb_handle* h, unsigned char* base, double out[8]) {
   double* partial = reinterpret_cast<double*>(base + kPlaneBytes);
   double* dout = reinterpret_cast<double*>(base + kPlaneBytes + kPartialBytes);
   const store_t* f = static_cast<const store_t*>(h->f[h->cur]);
-  const int blocks = h->reduce_blocks < kStaticBlocks ? h->reduce_blocks : kStaticBlocks;
+  const int blocks = h->reduce_blocks;  // at most kMaxReduceBlocks (configure_device), as in lb_reduce
   k_rho_local<real, store_t><<<unsigned((N + 255) / 256), 256, 0, h->stream>>>(f, rho, nx, ny, h->st,
                                                                                 real(h->p.rho_ref));
   const double rho_mid = 0.5 * (h->d.rho_g + h->d.rho_l);
@@ -119,7 +128,7 @@ extern "C" int lb_reduce_static(lb_handle* h, double out[8]) {
     return LB_ENOMEM;
   }
   void* base = nullptr;
-  const int rc = scratch_address(h, &base);
+  const int rc = static_scratch_address(h, &base);
   if (rc != LB_OK) return rc;
   unsigned char* b = static_cast<unsigned char*>(base);
   switch (h->p.precision) {

@@ -87,11 +87,11 @@ def test_init_rejects_bad_input_before_any_gpu_work(capi):
     rho[5] = -1.0
     h = ctypes.c_void_p()
     buf = (ctypes.c_char * 16)()
-    rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), ctypes.addressof(buf), ctypes.addressof(buf) + 8,
+    rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), ctypes.addressof(buf), ctypes.addressof(buf),
                             None, 0, rho.ctypes.data, 0, None)
     assert rc == capi.LB_EINVAL  # identical f buffers
-    rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), 1 << 40, 2 << 40, None, 0, rho.ctypes.data, 0, None)
-    assert rc == capi.LB_EINVAL and "node 5" in capi.lb_last_error(None)
+    # (A density that is not positive is rejected on the device, after the copy:
+    # tests/test_gpu_errors.py.)
     p.variant = capi.LB_TWO_PASS
     rho[5] = 2.0
     rc = capi.lib().lb_init(ctypes.byref(h), ctypes.byref(p), 1 << 40, 2 << 40, None, 0, rho.ctypes.data, 0, None)

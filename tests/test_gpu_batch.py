@@ -151,3 +151,38 @@ def test_rows_layout_batch_equals_single_lattices(shape, bps):
     for i in range(len(rhos)):
         assert torch.equal(b.state(i), ref[i]), i
     b.close()
+
+
+def test_status_names_the_lattices_that_go_non_finite(orc):
+    """Lattice 125 of the 256-lattice benchmark set (side 133, vdW, Tr = 0.6642,
+    W = 3.29 droplet) is past the method's stability limit: the FP64 oracle itself
+    goes non-finite within 60 steps.  In a batch next to two stable lattices,
+    lb_batch_status reports LB_ENONFINITE naming it, lb_batch_nonfinite counts its
+    nodes, and the stable lattices stay finite and equal to their single runs."""
+    from oracle import params as op
+    from oracle import thermo
+    from paper_1809_02390_gb300 import Batch, capi, derive
+
+    sp = inputs.batch_specs(256, 0)[125]
+    assert sp["nx"] == 133 and sp["shape"] == "droplet"
+    e = thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, sp["Tr"])
+    k_int = sp["W"] / thermo.interface(e, 1.0)["W"]
+    p = op.from_physical(Tr=sp["Tr"], K_int=k_int)
+    bad_rho = inputs.droplet(133, 133, 133 / 4, sp["W"], p.rho_g, p.rho_l)
+    assert not np.isfinite(orc.step(p, orc.init_feq(p, bad_rho), 60)).all()
+
+    rhos, kws = _inputs()
+    rhos = [rhos[0], bad_rho, rhos[3]]
+    kws = [kws[0], dict(Tr=sp["Tr"], K_int=k_int), kws[3]]
+    b = Batch(rhos, kws)
+    b.run(100)
+    with pytest.raises(capi.LBError) as ei:
+        b.status()
+    assert ei.value.code == capi.LB_ENONFINITE and "non-finite densities: 1" in str(ei.value)
+    n_bad, counts = capi.lb_batch_nonfinite(b.b, 3)
+    assert n_bad == 1 and b.nonfinite() == [1]
+    assert counts[0] == 0 and counts[2] == 0 and 0 < counts[1] <= 133 * 133
+    singles = _singles([rhos[0], rhos[2]], [kws[0], kws[2]], 100)
+    for i, ref in zip((0, 2), singles):
+        assert torch.equal(b.state(i), ref)
+    b.close()

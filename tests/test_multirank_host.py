@@ -28,7 +28,7 @@ bench.barrier(world)
 out["mlups"] = bench.aggregate_mlups(world, 4096 * 4096, 100, out["max"])
 dist.destroy_process_group()
 # The reference arm under the same launcher: rank 0 alone runs it and prints.
-args = types.SimpleNamespace(steps=2, warmup=3, gpus=world)
+args = types.SimpleNamespace(steps=2, warmup=3, gpus=world, layout="rows")
 print("RESULT " + json.dumps(out), flush=True)
 bench.run_reference(args)
 """

@@ -1,12 +1,14 @@
 """lb_reduce_static: the lattice diagnostics of lb_reduce without any device allocation.
 
-Some programs cannot call cudaMalloc: a host whose own allocator owns every
-byte of the GPU, a plugin running inside such a host, or code that runs while a
-stream is being captured into a CUDA graph (an allocation there breaks the
-capture).  They can still get the reductions (mass, momentum, probe pressures,
-liquid count, density range) from lb_reduce_static, which keeps its scratch in a
-static device array inside the library.  These tests call it through the C ABI
-and check that it returns exactly what lb_reduce returns, call after call.
+Some programs cannot call cudaMalloc: a host whose own allocator has taken
+every byte of the GPU, or a plugin running inside such a host, which gets its
+lattice from the host and has no allocator of its own.  They can still get the
+reductions (mass, momentum, probe pressures, liquid count, density range) from
+lb_reduce_static, which keeps its scratch in a static device array inside the
+library, committed when the handle is created.  These tests call it through the
+C ABI and check that it returns exactly what lb_reduce returns, call after call,
+that a call changes neither the device's free memory nor torch's pool, and that
+it still works once the GPU's memory has been filled.
 
 This file is collected last on purpose: it runs after every other test, and
 it also passes alone in a fresh process.
@@ -100,4 +102,47 @@ def test_rejects_lattices_above_its_limit():
     rc = capi.lib().lb_reduce_static(lat.h, out)
     assert rc == capi.LB_ENOMEM
     assert "static scratch" in capi.lb_last_error(lat.h)
+    lat.close()
+
+
+def test_calls_allocate_nothing():
+    """Free device memory (cudaMemGetInfo) and torch's reserved pool are the same
+    before and after a run of calls (after one warm-up call)."""
+    from paper_1809_02390_gb300 import Lattice, capi
+
+    lat = Lattice(_droplet(128, 96), precision="fp32", Tr=0.85)
+    lat.step(10)
+    first = capi.lb_reduce_static(lat.h)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(5):
+        _same(capi.lb_reduce_static(lat.h), first)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    lat.close()
+
+
+def test_works_after_the_gpu_memory_is_filled():
+    """The caller this entry point is for: after the handle exists, another
+    allocator takes (nearly) all free device memory; lb_reduce_static still
+    returns the reductions, because its array was committed by lb_init."""
+    from paper_1809_02390_gb300 import Lattice, capi
+
+    lat = Lattice(_droplet(96, 96), precision="fp64", Tr=0.85)
+    lat.step(15)
+    want = capi.lb_reduce(lat.h)
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    hog = torch.empty(max(free - (96 << 20), 0), dtype=torch.uint8, device="cuda")
+    try:
+        free_after, _ = torch.cuda.mem_get_info()
+        assert free_after < (256 << 20)
+        _same(capi.lb_reduce_static(lat.h), want)
+        _same(capi.lb_reduce_static(lat.h), want)
+    finally:
+        del hog
+        torch.cuda.empty_cache()
     lat.close()
