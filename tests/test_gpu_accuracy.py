@@ -1,0 +1,84 @@
+"""Accuracy of the reduced-precision storage against the FP64 oracle on the
+physics the method is for: flat-interface coexistence densities and the Laplace
+pressure jump of a droplet (supplement Sec. V).  Targets for FP32 storage:
+bulk densities within 1e-4 and the pressure jump within 1% of the oracle's.
+FP16 storage is checked against looser bounds and its errors are printed
+beside the FP32 ones (pytest -s shows them)."""
+import numpy as np
+import pytest
+
+from gpu_util import oracle_params
+from paper_1809_02390_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP32_BULK = 1e-4   # relative, coexistence densities
+FP32_DP = 1e-2     # relative, Laplace pressure jump
+FP16_BULK = 5e-3   # row means (stochastic rounding differs from row to row)
+FP16_DP = 0.5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_02390_gb300 import build
+
+    build.build()
+
+
+@pytest.mark.parametrize("Tr", [0.8, 0.9])
+def test_flat_interface_densities_against_the_oracle(orc, Tr):
+    """vdW slab, K_INT = 1, 8,000 steps.  The oracle runs the 1-D problem on 128 x 4
+    nodes; the GPU runs the same profile on 128 x 64 nodes (rows layout, so the
+    FP32 and FP16 steps take the tensor-copy kernel of the benchmark): the problem
+    does not depend on y, so every FP32 row is the same and must match the
+    oracle's; FP16 stores round stochastically with a dither keyed by the node,
+    so its rows differ and their means are compared."""
+    from paper_1809_02390_gb300 import Lattice
+
+    p = oracle_params(Tr=Tr)
+    from oracle import thermo
+
+    W = thermo.interface(thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, Tr), 1.0)["W"]
+    prof = inputs.slab(128, 4, 64, W, p.rho_g, p.rho_l)
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, prof), 8000))[0][0]
+    rg, rl = ref[0], ref[64]
+    lines = []
+    for precision, tol in (("fp32", FP32_BULK), ("fp16s", FP16_BULK)):
+        lat = Lattice(np.tile(prof[:1], (64, 1)), precision=precision, Tr=Tr, layout="rows")
+        lat.step(8000)
+        rho = lat.moments(velocity=False).double().cpu().numpy()
+        lat.close()
+        if precision == "fp32":   # every row does the same arithmetic: rows are identical
+            assert np.ptp(rho, axis=0).max() == 0.0
+        eg, el = abs(rho[:, 0].mean() / rg - 1), abs(rho[:, 64].mean() / rl - 1)
+        lines.append("%s Tr=%.1f: gas %.2e liquid %.2e" % (precision, Tr, eg, el))
+        assert eg <= tol and el <= tol, lines[-1]
+    print("\n" + "\n".join(lines))
+
+
+def test_laplace_pressure_jump_against_the_oracle(orc):
+    """Droplet of radius 12 on 64 x 64 (vdW, Tr = 0.85, W = 5), 4,000 steps:
+    dp = p_EOS(centre) - p_EOS(node (0, 0)) of each storage precision against
+    the oracle's dp, and the bulk densities at both probes."""
+    from paper_1809_02390_gb300 import Lattice
+
+    p = oracle_params(Tr=0.85)
+    rho0 = inputs.droplet(64, 64, 12.0, 5.0, p.rho_g, p.rho_l)
+    ref = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), 4000))[0]
+    dp_ref = orc.eos(p, ref[32, 32])[0] - orc.eos(p, ref[0, 0])[0]
+    lines = []
+    for precision, tol_b, tol_dp in (("fp32", FP32_BULK, FP32_DP), ("fp16s", FP16_BULK, FP16_DP)):
+        lat = Lattice(rho0, precision=precision, Tr=0.85)
+        lat.step(4000)
+        rho = lat.moments(velocity=False).double().cpu().numpy()
+        lat.close()
+        dp = orc.eos(p, rho[32, 32])[0] - orc.eos(p, rho[0, 0])[0]
+        e_in, e_out = abs(rho[32, 32] / ref[32, 32] - 1), abs(rho[0, 0] / ref[0, 0] - 1)
+        e_dp = abs(dp / dp_ref - 1)
+        lines.append("%s droplet: liquid %.2e gas %.2e dp %.2e" % (precision, e_in, e_out, e_dp))
+        assert e_in <= tol_b and e_out <= tol_b and e_dp <= tol_dp, lines[-1]
+    print("\n" + "\n".join(lines))
