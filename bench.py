@@ -31,6 +31,7 @@ if ROOT not in sys.path:
 METRIC = "D2Q9 multiphase MLUPS & % of GB300 HBM peak (FP32 vs FP64); adjoint/forward cost"
 N_SIDE = 4096
 TR = 0.8
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 populations
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
 # for the kernel sources they were measured on (sha256 of the files below).
@@ -323,13 +324,15 @@ def measure_batch(torch, single_mlups: float, steps: int, layout: str = "rows") 
     import numpy as np
 
     eg, el, curve, unstable = [], [], [], []
+    bad = set(b.nonfinite())  # lb_batch_nonfinite: lattices with a non-finite density
     for i, m in enumerate(meta):
+        if i in bad:
+            unstable.append({"index": i, "side": m["nx"], "Tr": round(m["Tr"], 4), "W": round(m["W"], 3),
+                             "shape": m["shape"]})
+            continue
         rho = b.density(i).cpu().numpy()
         ny, nx = rho.shape
         liq, gas = float(rho[ny // 2, nx // 2]), float(rho[0, 0])
-        if not np.isfinite(rho).all():
-            unstable.append({"side": m["nx"], "Tr": round(m["Tr"], 4), "W": round(m["W"], 3), "shape": m["shape"]})
-            continue
         eg.append(abs(gas / m["rho_g"] - 1))
         el.append(abs(liq / m["rho_l"] - 1))
         curve.append([round(m["Tr"], 4), round(gas, 5), round(liq, 5), round(m["rho_g"], 5), round(m["rho_l"], 5)])
@@ -479,6 +482,15 @@ def measure_calibration(torch, iterations: int = 50) -> dict:
             "rel_error_start": rel(start), "rel_error_fit": rel(theta), "params": ["Tr", "G2", "K_int"]}
 
 
+def workload_config(n: int, layout: str, world: int) -> dict:
+    """The benchmark's workload description (the same dict on both arms)."""
+    return {"workload": "spinodal-%dx%d-fp32-vdw-Tr0.8" % (n, n), "lattice": [n, n], "eos": "vdw",
+            "Tr": TR, "storage": "fp32 (deviation from w_i rho_ref)", "variant": "fused",
+            "layout": {"planes": "f[9][ny][nx]", "rows": "f[ny][9][nx]"}[layout],
+            "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
+            "parallelism": "independent lattice per GPU" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores; each step is one
     oracle time step on a 128 x 128 periodic crop of the workload."""
@@ -503,10 +515,11 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "spinodal-4096x4096-vdw-Tr0.8 (128x128 periodic crop per step)",
-                       "lattice": [128, 128], "eos": "vdw", "Tr": TR},
+            "config": workload_config(N_SIDE, args.layout, world),
             "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle steps on a 128x128 crop" % args.steps},
+                             "sample": "each step: one FP64 oracle time step on a 128 x 128 periodic crop of the "
+                                       "4096 x 4096 workload's initial field (%d timed steps after %d warm-up "
+                                       "steps; rate = crop nodes x steps / time)" % (args.steps, args.warmup)},
             "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -544,11 +557,13 @@ def run_ours(args):
     pk = peaks()
 
     # --- main measurement: FP32 fused, inputs resident in HBM -----------------
-    lat = Lattice(rho0, precision="fp32", variant="fused", Tr=TR, layout=args.layout)
+    main_prec = args.main_precision if args.only_main else "fp32"
+    main_var = args.main_variant if args.only_main else "fused"
+    lat = Lattice(rho0, precision=main_prec, variant=main_var, Tr=TR, layout=args.layout)
     if args.dispatch == "static" and capi.lb_tile_dispatch(lat.h):
         capi.lb_set_tile_dispatch(lat.h, False)
     kernel = ("k_step_tma_dyn<f2>" if capi.lb_tile_dispatch(lat.h) else "k_step_tma<f2>") if capi.lb_uses_tma(lat.h) \
-        else "k_step_fused<f2,float>"
+        else ("k_step_fused<f2,float>" if main_var == "fused" else "k_density + k_collide_rho")
     lat.step(args.warmup)
     barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -556,7 +571,7 @@ def run_ours(args):
     ms = max_over_ranks(ms, torch, world)
     ms_step = ms / args.steps
     value = aggregate_mlups(world, nodes, args.steps, ms)
-    achieved = BYTES_PER_LU["fp32"] * nodes / (ms_step * 1e-3) / 1e9
+    achieved = BYTES_PER_LU[main_prec] * nodes / (ms_step * 1e-3) / 1e9
     sane = lat.reduce()
     # Ceiling of the access pattern: the same nine read and nine write streams with
     # no arithmetic (lb_stream_copy), timed like the step.
@@ -570,14 +585,16 @@ def run_ours(args):
         capi.lb_stream_copy(lat.h)
     e1.record(s_)
     torch.cuda.synchronize()
-    pattern_gbs = BYTES_PER_LU["fp32"] * nodes * 50 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    pattern_gbs = BYTES_PER_LU[main_prec] * nodes * 50 / (e0.elapsed_time(e1) * 1e-3) / 1e9
     lat.close()
     del lat
     torch.cuda.empty_cache()
     if args.only_main:
         if rank == 0:
             print(json.dumps({"only_main": True, "size": n, "layout": args.layout, "kernel": kernel,
-                              "MLUPS": round(value, 1), "ms_per_step": ms_step, "pattern_GBps": round(pattern_gbs, 1)}))
+                              "precision": main_prec, "variant": main_var, "MLUPS": round(value, 1),
+                              "ms_per_step": ms_step, "algorithmic_GBps": round(achieved, 1),
+                              "pattern_GBps": round(pattern_gbs, 1)}))
         return
 
     # --- other variants / precisions (shorter runs, same workload) -------------
@@ -604,21 +621,26 @@ def run_ours(args):
     # --- end to end through the public API with host buffers -------------------
     rho_host = torch.from_numpy(np.ascontiguousarray(rho0)).pin_memory()
     out_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
+
+    def end_to_end(steps):
+        lt = Lattice(rho_host, precision="fp32", variant="fused", Tr=TR, layout=args.layout)
+        lt.step(steps)
+        rho_dev = lt.moments(velocity=False)
+        out_host.copy_(rho_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        lt.close()
+
+    end_to_end(args.warmup)  # warm-up pass: first-use costs of the allocator and the library
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    lt = Lattice(rho_host, precision="fp32", variant="fused", Tr=TR, layout=args.layout)
-    lt.step(args.steps)
-    rho_dev = lt.moments(velocity=False)
-    out_host.copy_(rho_dev, non_blocking=True)
-    torch.cuda.synchronize()
+    end_to_end(args.steps)
     e2e_s = max_over_ranks(time.perf_counter() - t0, torch, world)
-    lt.close()
-    del lt
     e2e = {"value": round(world * nodes * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
            "h2d_bytes_per_step": round(nodes * 8 / args.steps, 1),
            "d2h_bytes_per_step": round(nodes * 4 / args.steps, 1),
-           "note": "lb_init from pinned host densities, K steps, lb_moments, density read back; bytes amortised per step"}
+           "note": "lb_init from pinned host densities (checked on the device), K steps, lb_moments, density "
+                   "read back; after one untimed pass of W steps; bytes amortised per step"}
 
     extras = {}
     if world == 1 and not args.no_extras:
@@ -641,6 +663,9 @@ def run_ours(args):
     traffic = NCU_TRAFFIC.get((kernel, args.layout, src_hash))
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
+            "frac_of_nominal": round(achieved / HBM_NOMINAL_GBS, 4),
+            "frac_note": "frac divides by the measured copy bandwidth (the roofline peak); frac_of_nominal by "
+                         "GB300's nominal HBM3e bandwidth of %.0f GB/s" % HBM_NOMINAL_GBS,
             "kernel": kernel, "algorithmic_bytes_per_launch": BYTES_PER_LU["fp32"] * nodes,
             "traffic_GBps": round(traffic / (ms_step * 1e-3) / 1e9, 1) if traffic else None,
             "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs, copy burst)",
@@ -652,11 +677,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "spinodal-%dx%d-fp32-vdw-Tr0.8" % (n, n), "lattice": [n, n], "eos": "vdw",
-                       "Tr": TR, "storage": "fp32 (deviation from w_i rho_ref)", "variant": "fused",
-                       "layout": {"planes": "f[9][ny][nx]", "rows": "f[ny][9][nx]"}[args.layout],
-                       "l2": "inputs larger than L2 (2 x 604 MB population buffers)",
-                       "parallelism": "independent lattice per GPU" if world > 1 else "single GPU"},
+            "config": workload_config(n, args.layout, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clk.summary(), "variants": variants, **extras,
             "check": {"mass": sane["mass"], "rho_min": sane["rho_min"], "rho_max": sane["rho_max"]}}
@@ -673,6 +694,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=N_SIDE, help="lattice side (profiling runs use smaller cases)")
     ap.add_argument("--only-main", action="store_true", help="time the FP32 fused step only (profiling)")
+    ap.add_argument("--main-precision", choices=["fp32", "fp16s", "fp64"], default="fp32",
+                    help="with --only-main: storage precision of the timed step (profiling)")
+    ap.add_argument("--main-variant", choices=["fused", "two_pass"], default="fused",
+                    help="with --only-main: fused step or the two-pass variant (profiling)")
     ap.add_argument("--only-adjoint", action="store_true", help="time the FP32 adjoint at --size only (profiling)")
     ap.add_argument("--only-batch", action="store_true", help="time the 256-lattice batch only (profiling)")
     ap.add_argument("--only-precision", action="store_true", help="run the FP64/FP32/FP16 study only")
