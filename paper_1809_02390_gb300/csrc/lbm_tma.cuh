@@ -381,11 +381,17 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
   __shared__ real rs[2][kTileY + 2][kTileX + 2];
   __shared__ __align__(8) unsigned long long bar[2];
-  __shared__ int tq[2];  // tile staged in each window buffer (>= total: none)
+  __shared__ int tq[2];   // tile staged in each window buffer (>= total: none)
+  __shared__ int2 tp[2];  // its origin (x0, y0), written by the issuer with tq
   const int tiles_x = (nx + kTileX - 1) / kTileX;
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
   const bool rows = st.ps == nx;  // rows layout (the planes one has ps = nx ny, ny >= 50 here)
   auto win = [&](int slot) { return reinterpret_cast<S*>(base + slot * Win2<S>::buffer); };
+  // Origin of tile t (row-major over the lattice): one division, by the issuer only.
+  auto origin = [&](int t) {
+    const int r = t / tiles_x;
+    return make_int2((t - r * tiles_x) * kTileX, r * kTileY);
+  };
   // The issuer: tiles 2G + ticket in increasing order; after the first one past the
   // last tile no more tickets are drawn.
   const int first = 2 * int(gridDim.x);
@@ -396,11 +402,11 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     dry = t >= total;
     return dry ? total : t;
   };
-  auto kind_of = [&](int t) { return tile_kind<false, S>((t % tiles_x) * kTileX, (t / tiles_x) * kTileY, nx, ny); };
-  auto issue = [&](int t, int slot) {  // the issuer
-    if (t < total && kind_of(t) == kTensorCopy) {
+  auto kind_at = [&](int2 o) { return tile_kind<false, S>(o.x, o.y, nx, ny); };
+  auto issue = [&](int t, int2 o, int slot) {  // the issuer
+    if (t < total && kind_at(o) == kTensorCopy) {
       fence_proxy_async();
-      issue_windows(win(slot), &tin, (t % tiles_x) * kTileX, (t / tiles_x) * kTileY, &bar[slot], 0, rows);
+      issue_windows(win(slot), &tin, o.x, o.y, &bar[slot], 0, rows);
     }
   };
   int pending = total;  // the issuer: the tile after the two staged ones
@@ -410,8 +416,10 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     const int b = int(blockIdx.x), g = int(gridDim.x);
     tq[0] = b < total ? b : total;
     tq[1] = b + g < total ? b + g : total;
-    issue(tq[0], 0);
-    issue(tq[1], 1);
+    tp[0] = origin(tq[0]);
+    tp[1] = origin(tq[1]);
+    issue(tq[0], tp[0], 0);
+    issue(tq[1], tp[1], 1);
     pending = tq[1] < total ? draw() : total;
   }
   __syncthreads();
@@ -420,8 +428,9 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     const int slot = k & 1;
     const int t = tq[slot];  // tickets rise, so the first past the end ends the loop
     if (t >= total) break;
-    const int x0 = (t % tiles_x) * kTileX, y0 = (t / tiles_x) * kTileY;
-    const int kind = kind_of(t);
+    const int2 o = tp[slot];
+    const int x0 = o.x, y0 = o.y;
+    const int kind = kind_at(o);
     real f[kTileRows][9];
     bool late = false;
     if (kind == kTensorCopy) {
@@ -437,14 +446,15 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
         atomicExch(err, 1);
         mbar_wait(&bar[slot], ((ph >> slot) & 1u) ^ 1u);
         const int to = tq[slot ^ 1];
-        if (to < total && kind_of(to) == kTensorCopy) mbar_wait(&bar[slot ^ 1], (ph >> (slot ^ 1)) & 1u);
+        if (to < total && kind_at(tp[slot ^ 1]) == kTensorCopy) mbar_wait(&bar[slot ^ 1], (ph >> (slot ^ 1)) & 1u);
       }
       break;
     }
     // The buffer of this tile is free: stage the tile two ahead into it.
     if (threadIdx.x == kIssuer) {
       tq[slot] = pending;
-      issue(pending, slot);
+      tp[slot] = origin(pending);
+      issue(pending, tp[slot], slot);
       pending = draw();
     }
     collide_tile<V, S, kTileY>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[slot], rnd);
