@@ -449,16 +449,22 @@ def measure_sweeps(torch) -> dict:
                "W_slope_analytic": paper[Tr][1]}
         if Tr in ss:
             row.update({"sigma_slope": round(ss[Tr]["slope"], 7), "sigma_slope_paper_sim": paper[Tr][2],
-                        "sigma_slope_analytic": paper[Tr][3]})
+                        "sigma_slope_analytic": paper[Tr][3],
+                        "sigma_slope_with_intercept": round(ss[Tr]["slope_with_intercept"], 7)})
         rows.append(row)
     return {"seconds": round(time.perf_counter() - t0, 1), "rows": rows,
             "K_int": {"W": {str(k): list(v_) for k, v_ in v.W_SWEEP.items()},
-                      "sigma": {str(k): list(v_) for k, v_ in v.SIGMA_SWEEP.items()}}}
+                      "sigma": {str(k): list(v_[0]) for k, v_ in v.SIGMA_SWEEP.items()}},
+            "sigma_setup": {str(k): {"lattice": v_[1], "radius": v_[2], "relax_steps": v_[3], "avg_steps": v_[4]}
+                            for k, v_ in v.SIGMA_SWEEP.items()}}
 
 
 def measure_calibration(torch, iterations: int = 50) -> dict:
     """256 x 256 FP32, perturbed ellipse (axis ratio 1.5, area of an R = 40 disk),
-    2,000 steps, checkpoints every 45; target made at (Tr, G2, K_int) = (0.8, G2_ref, 1)."""
+    2,000 steps, checkpoints every 45; target made at (Tr, G2, K_int) = (0.8, G2_ref, 1);
+    loss = squared L2 distance of the final density.  L-BFGS (the library's default)
+    and, for comparison, Adam, each for at most `iterations` loss-and-gradient
+    evaluations from the same perturbed start."""
     from paper_1809_02390_gb300 import inputs
     from paper_1809_02390_gb300.adjoint import RolloutSpec, calibrate, density, initial_state, rollout
 
@@ -471,15 +477,18 @@ def measure_calibration(torch, iterations: int = 50) -> dict:
     with torch.no_grad():
         target = density(rollout(ref, f0, spec, steps, 45), spec).detach()
     start = ref * torch.tensor([0.97, 1.05, 1.08], dtype=torch.float64)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    theta, losses = calibrate(spec, f0, target, start, steps, iterations=iterations, lr=0.01, checkpoint_every=45)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
     rel = lambda t: [round(float(v), 5) for v in ((t - ref) / ref)]
-    return {"lattice": [n, n], "steps_per_rollout": steps, "checkpoint_every": 45, "iterations": iterations,
-            "seconds": round(dt, 2), "loss_first": losses[0], "loss_last": losses[-1],
-            "rel_error_start": rel(start), "rel_error_fit": rel(theta), "params": ["Tr", "G2", "K_int"]}
+    out = {"lattice": [n, n], "steps_per_rollout": steps, "checkpoint_every": 45, "params": ["Tr", "G2", "K_int"],
+           "rel_error_start": rel(start)}
+    for method, lr in (("lbfgs", 1.0), ("adam", 0.01)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        theta, losses = calibrate(spec, f0, target, start, steps, iterations=iterations, lr=lr, checkpoint_every=45,
+                                  method=method)
+        torch.cuda.synchronize()
+        out[method] = {"evaluations": len(losses), "seconds": round(time.perf_counter() - t0, 2),
+                       "loss_first": losses[0], "loss_last": losses[-1], "rel_error_fit": rel(theta)}
+    return out
 
 
 def workload_config(n: int, layout: str, world: int) -> dict:

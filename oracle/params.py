@@ -7,6 +7,15 @@ The paper fixes (main text, after Eq. 20):
 and the relaxation-rate constraint tau_p tau_q = (k+1) tau_e tau_q = 1/12
 with tau = 1/s - 1/2 (Eq. 16).  The oracle runs with c = 1, so the pressure is
 carried as p/c^2: lam = K_EOS / c^2 multiplies the EOS and G2 = G^2 / c^2.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Pins: relaxation_rates by hand-worked values and by the flat-interface tests
+whose outcome depends on Eq. 16 (tests/test_oracle_physics.py).  The c^2 rule
+(Eq. 22) only sets the time unit (lam and G2 scale together, so no equilibrium
+depends on it); the one printed number that does, the analytic oscillation
+period of the elliptic droplet, is not reproduced from the stated parameters:
+parity unpinned for the time unit c^2.
 """
 from __future__ import annotations
 

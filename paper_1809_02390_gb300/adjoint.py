@@ -30,7 +30,7 @@ class RolloutSpec:
                  rho_ref: float | None = None, s_p: float = 1.0):
         from . import derive
 
-        self.nx, self.ny, self.precision = nx, ny, precision
+        self.nx, self.ny, self.precision, self.Tr_ref = nx, ny, precision, Tr_ref
         self.eos, self.eos_a, self.eos_b, self.R_gas, self.s_p = eos, eos_a, eos_b, R_gas, s_p
         d = derive(nx, ny, eos=eos, eos_a=eos_a, eos_b=eos_b, R_gas=R_gas, Tr=Tr_ref, K_int=K_int_ref, s_p=s_p)
         self.Tc = d["Tc"]
@@ -41,6 +41,17 @@ class RolloutSpec:
         # Storage shift of the populations (f_i - w_i rho_ref); the FP32 kernels carry it in float.
         r = 0.5 * (self.rho_g + self.rho_l) if rho_ref is None else float(rho_ref)
         self.rho_ref = r if precision == "fp64" else float(np.float32(r))
+
+    def moments_lattice(self):
+        """A lattice of this spec used only to evaluate densities of given states
+        through lb_moments (created on first use)."""
+        lat = getattr(self, "_moments_lat", None)
+        if lat is None:
+            lat = Lattice(np.full((self.ny, self.nx), 0.5 * (self.rho_g + self.rho_l)), precision=self.precision,
+                          rho_ref=self.rho_ref,
+                          **self.lattice_kwargs([self.Tr_ref, self.G2_ref, self.K_ref]))
+            self._moments_lat = lat
+        return lat
 
     def lattice_kwargs(self, theta) -> dict:
         Tr, G2, K = (float(v) for v in theta)
@@ -134,28 +145,105 @@ def initial_state(spec: RolloutSpec, rho0, theta):
     return f0
 
 
+class _DensityFn:
+    fn = None
+
+
+def _make_density():
+    import torch
+
+    class _Density(torch.autograd.Function):
+        """rho of a post-collision state by the library (lb_moments: rho = sum_i fbar_i,
+        Eq. 5 at the time level of the last collision); its transpose, for the
+        backward pass, spreads the cotangent of rho over the nine populations."""
+
+        @staticmethod
+        def forward(ctx, state, spec):
+            lat = spec.moments_lattice()
+            capi.lb_set_state(lat.h, state.detach().contiguous().data_ptr())
+            rho = lat.moments(velocity=False).clone()
+            ctx.shape, ctx.dtype = tuple(state.shape), state.dtype
+            return rho
+
+        @staticmethod
+        def backward(ctx, g):
+            return g.to(ctx.dtype).unsqueeze(0).expand(ctx.shape).contiguous(), None
+
+    return _Density
+
+
 def density(state, spec: RolloutSpec):
-    """rho = sum_i f_i of a state tensor (the weights of the storage shift sum to 1)."""
-    return state.sum(0) + spec.rho_ref
+    """rho of a state tensor [9, ny, nx] (deviation storage), computed by the library
+    (lb_moments) and differentiable in the state."""
+    if _DensityFn.fn is None:
+        _DensityFn.fn = _make_density()
+    return _DensityFn.fn.apply(state, spec)
+
+
+def trajectory(theta, f0, spec: RolloutSpec, nsteps: int, snapshots: int = 1,
+               checkpoint_every: int | None = None) -> list:
+    """Densities after each of ``snapshots`` equal segments of an ``nsteps``-step
+    rollout (the last one ends at ``nsteps``), differentiable in theta and f0: the
+    segments are chained rollouts, so the adjoint of each segment receives the
+    cotangents of its own snapshot and of everything after it."""
+    if snapshots < 1 or nsteps < snapshots:
+        raise ValueError("need 1 <= snapshots <= nsteps")
+    bounds = [round(nsteps * (k + 1) / snapshots) for k in range(snapshots)]
+    out, state, done = [], f0, 0
+    for b in bounds:
+        state = rollout(theta, state, spec, b - done, checkpoint_every)
+        done = b
+        out.append(density(state, spec))
+    return out
 
 
 def calibrate(spec: RolloutSpec, f0, target, theta0, nsteps: int, iterations: int = 50, lr: float = 0.02,
-              checkpoint_every: int | None = None):
-    """Fits theta = (Tr, G2, K_int) so that the density after ``nsteps`` steps from
-    ``f0`` matches ``target`` (loss = sum (rho - target)^2), with Adam on the
-    relative deviations theta = theta0 (1 + delta).  Returns (theta, losses)."""
+              checkpoint_every: int | None = None, snapshots: int = 1, method: str = "lbfgs",
+              bound: float = 0.25):
+    """Fits theta = (Tr, G2, K_int) so that the densities of a rollout of ``nsteps``
+    steps from ``f0`` match ``target`` (loss = sum over snapshots of sum (rho - target)^2),
+    optimising delta in theta = theta0 (1 + bound tanh(delta / bound)): relative
+    deviations for small delta, kept inside +-bound (25%) so that a line search
+    cannot step to a temperature at or above the critical one, or below zero.  ``target``: the
+    final density (snapshots = 1) or the list of ``snapshots`` densities of
+    ``trajectory``.  method "adam" takes ``iterations`` Adam steps of size ``lr``;
+    "lbfgs" (the default) runs L-BFGS with a strong-Wolfe line search for at most
+    ``iterations`` loss-and-gradient evaluations (each one forward rollout and its
+    adjoint).  The loss is ill-conditioned: the final density mostly fixes Tr and
+    G2 / lam (coexistence densities, interface width), lam alone acts only through
+    the dynamics.  Adam's per-parameter step normalisation follows the loss down
+    the well-determined directions and leaves the others; the quasi-Newton
+    curvature estimate resolves all three.  Snapshots along the trajectory add the
+    dynamics to the loss.  Returns (theta, losses), one loss per evaluation."""
     import torch
 
+    targets = [target] if snapshots == 1 and not isinstance(target, (list, tuple)) else list(target)
+    if len(targets) != snapshots:
+        raise ValueError("target must hold one density per snapshot")
     base = theta0.detach().clone().double()
     delta = torch.zeros(3, dtype=torch.float64, requires_grad=True)
-    opt = torch.optim.Adam([delta], lr=lr)
     losses = []
-    for _ in range(iterations):
+
+    def theta_of(d):
+        return base * (1.0 + bound * torch.tanh(d / bound))
+
+    def closure():
         opt.zero_grad()
-        theta = base * (1.0 + delta)
-        out = rollout(theta, f0, spec, nsteps, checkpoint_every)
-        loss = ((density(out, spec) - target) ** 2).sum()
+        rhos = trajectory(theta_of(delta), f0, spec, nsteps, snapshots, checkpoint_every)
+        loss = sum(((r - t) ** 2).sum() for r, t in zip(rhos, targets))
         loss.backward()
         losses.append(float(loss.detach()))
-        opt.step()
-    return (base * (1.0 + delta)).detach(), losses
+        return loss
+
+    if method == "adam":
+        opt = torch.optim.Adam([delta], lr=lr)
+        for _ in range(iterations):
+            closure()
+            opt.step()
+    elif method == "lbfgs":
+        opt = torch.optim.LBFGS([delta], lr=1.0, max_iter=iterations, max_eval=iterations, history_size=10,
+                                tolerance_grad=1e-12, tolerance_change=1e-14, line_search_fn="strong_wolfe")
+        opt.step(closure)
+    else:
+        raise ValueError("method must be 'adam' or 'lbfgs'")
+    return theta_of(delta).detach(), losses

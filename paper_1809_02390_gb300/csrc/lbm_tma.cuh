@@ -151,21 +151,31 @@ __device__ __forceinline__ void ring_cell(int t, int& wx, int& wy) {
   }
 }
 
-// Windows of tiles that wrap, by per-thread asynchronous 4-byte copies (cp.async):
-// the window of such a tile gets the cells a tensor copy would deliver, with
-// periodic source coordinates, so that every tile of a lattice of at least
-// kTmaCols x kTmaRows nodes is staged ahead (every coordinate then lies in
-// [-4, 2n) and one conditional wrap suffices).  240 threads = 6 window rows x 40
-// columns per pass, 3 passes, 9 planes: 27 copies per thread.
+// Windows of tiles that wrap, by per-thread asynchronous copies (cp.async): the
+// window of such a tile gets the cells a tensor copy would deliver, with periodic
+// source coordinates, so that every tile of a lattice of at least kTmaCols x
+// kTmaRows nodes is staged ahead (every coordinate then lies in [-4, 2n) and one
+// conditional wrap suffices).  180 threads, one per window row (18) and run of four
+// columns (10); each copies its run in all nine planes.  A run is one 16-byte copy
+// when its four source cells are contiguous and 16-byte aligned, i.e. when it does
+// not cross the lattice's right edge and its start is a multiple of 4 after the
+// wrap: always when nx is a multiple of 4, else for runs inside [0, nx); otherwise
+// four 4-byte copies.  Row strides and plane strides are multiples of 4 floats in
+// every layout that reaches here (the tensor-copy path needs them).
 __host__ __device__ __forceinline__ bool async_window_ok(int nx, int ny) {
   return nx >= kTmaCols && ny >= kTmaRows;
 }
 
-constexpr int kAsyncThreads = 6 * kTmaCols;
-static_assert(kTmaRows % 6 == 0 && kAsyncThreads <= kFusedThreads, "window rows split in passes of 6");
+constexpr int kAsyncRuns = kTmaCols / 4;                 // 10 runs of four columns per window row
+constexpr int kAsyncThreads = kTmaRows * kAsyncRuns;     // 180
+static_assert(kTmaCols % 4 == 0 && kAsyncThreads <= kFusedThreads, "window rows split in runs of four columns");
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// 16 bytes (both addresses 16-byte aligned), bypassing L1.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 // One element (4 or 8 bytes, naturally aligned) by cp.async.
 __device__ __forceinline__ void cp_async_elem(float* dst, const float* src) { cp_async4(dst, src); }
@@ -178,24 +188,32 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // All threads: the window of the (wrapping) tile at (x0, y0) of a lattice with
-// populations at fin (layout st) into win.  Plane i's window row r holds
-// lattice row y0 - 1 - e_iy + r, window column c lattice column x0 - 4 + c.
+// populations at fin (16-byte aligned; layout st) into win.  Plane i's window row r
+// holds lattice row y0 - 1 - e_iy + r, window column c lattice column x0 - 4 + c.
 __device__ __forceinline__ void issue_window_async(float* win, const float* __restrict__ fin, int nx, int ny,
                                                    Strides st, int x0, int y0) {
   const int j = threadIdx.x;
   if (j < kAsyncThreads) {
-    const int c = j % kTmaCols, r0 = j / kTmaCols;
-    const int gx = wrap1(x0 - 4 + c, nx);
-    int src[kTmaRows / 6][3];  // [pass][e_iy + 1]: offset of the source cell of population 0
+    const int r = j / kAsyncRuns, c4 = 4 * (j - r * kAsyncRuns);
+    const int col = x0 - 4 + c4;  // lattice column of the run's first cell, in [-4, 2 nx)
+    const bool whole = (nx & 3) == 0 || (col >= 0 && col + 3 < nx);
+    int row[3];  // [e_iy + 1]: element offset of lattice row y0 - 1 - e_iy + r
 #pragma unroll
-    for (int q = 0; q < kTmaRows / 6; ++q)
+    for (int e = 0; e < 3; ++e) row[e] = wrap1(y0 - e + r, ny) * st.rs;
+    float* dst = win + r * kTmaCols + c4;
+    if (whole) {
+      const int gx = wrap1(col, nx);
 #pragma unroll
-      for (int e = 0; e < 3; ++e) src[q][e] = wrap1(y0 - e + r0 + 6 * q, ny) * st.rs + gx;
+      for (int i = 0; i < 9; ++i) cp_async16(dst + i * kTmaPlane, fin + (i * st.ps + row[ey_of(i) + 1] + gx));
+    } else {
+      int gx[4];
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
+      for (int q = 0; q < 4; ++q) gx[q] = wrap1(col + q, nx);
 #pragma unroll
-      for (int q = 0; q < kTmaRows / 6; ++q)
-        cp_async4(win + i * kTmaPlane + (r0 + 6 * q) * kTmaCols + c, fin + (i * st.ps + src[q][ey_of(i) + 1]));
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cp_async4(dst + i * kTmaPlane + q, fin + (i * st.ps + row[ey_of(i) + 1] + gx[q]));
+    }
   }
   cp_async_commit();
 }

@@ -192,7 +192,10 @@ def test_fused_segment_equals_single_steps(orc, precision, tol, nx, ny):
 
 def test_calibration_recovers_parameters():
     """Gradient-based calibration through the adjoint: a target density field made at
-    reference (Tr, G2, K_int) is fitted from perturbed parameters."""
+    reference (Tr, G2, K_int) is fitted from parameters perturbed by -4%, +5%, -7%;
+    L-BFGS (the default) recovers each of the three within 2% (on the 256^2 benchmark
+    case it recovers them exactly to the printed digits, where Adam with the same
+    budget leaves K_int 19% off: the loss is ill-conditioned)."""
     from paper_1809_02390_gb300.adjoint import RolloutSpec, calibrate, density, initial_state, rollout
 
     n = 64
@@ -203,6 +206,6 @@ def test_calibration_recovers_parameters():
     with torch.no_grad():
         target = density(rollout(ref, f0, spec, 300), spec).detach()
     start = ref * torch.tensor([0.96, 1.05, 0.93], dtype=torch.float64)
-    theta, losses = calibrate(spec, f0, target, start, 300, iterations=40, lr=0.01)
-    assert losses[-1] < 0.05 * losses[0]
-    assert float(((theta - ref) / ref).abs().max()) < 0.5 * float(((start - ref) / ref).abs().max())
+    theta, losses = calibrate(spec, f0, target, start, 300, iterations=40)
+    assert losses[-1] < 1e-4 * losses[0]
+    assert float(((theta - ref) / ref).abs().max()) < 0.02
