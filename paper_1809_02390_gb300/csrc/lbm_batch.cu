@@ -59,10 +59,13 @@ __host__ __device__ constexpr bool is_tma(int shape) { return shape >= kShapeTMA
 __host__ __device__ constexpr bool is_dyn(int shape) { return shape >= kShapeDyn; }
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: the pools end where they started)
 
-// One record per tile: its lattice, origin and the lattice's size, row stride and
-// pool offset.
+// One record per tile: its lattice, origin, the lattice's size and strides (in the
+// pool's layout), how the tensor-copy kernels stage it (TileKind, from the tile's
+// position, fixed when the batch is built) and the lattice's pool offset.
 struct TileRec {
-  int lat, x0, y0, nx, ny, sx;
+  int lat, x0, y0, nx, ny;
+  int ps, rs;  // population and row strides of the lattice in its pool (Strides)
+  int kind;
   long long offset;
 };
 
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
   int word = threadIdx.x < kCoefWords ? reinterpret_cast<const int*>(coef + ti.lat)[threadIdx.x] : 0;
   if constexpr (!PERSIST) {  // one block per tile
     step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny,
-                               lat_strides(ti.sx, ti.ny, rows), common, cs, ti.x0, ti.y0, rs,
+                               Strides{ti.ps, ti.rs}, common, cs, ti.x0, ti.y0, rs,
                                StoreCoef{&cs, word, true});
     return;
   }
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(TileShape<TY>::threads, MINB)
     const StoreCoef hook{&cs, word, ti.lat != last};
     last = ti.lat;
     step_tile<f2, store_t, TY>(pool_in + ti.offset, pool_out + ti.offset, ti.nx, ti.ny,
-                               lat_strides(ti.sx, ti.ny, rows), common, cs, ti.x0, ti.y0, rs, hook);
+                               Strides{ti.ps, ti.rs}, common, cs, ti.x0, ti.y0, rs, hook);
     if (tn >= total_tiles) break;
     __syncthreads();  // shared densities and coefficients are reused by the next tile
     t = tn;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
   __shared__ TileRec rec[2];
   __shared__ __align__(8) unsigned long long bar;
   if (blockIdx.x >= total_tiles) return;
-  auto kind_of = [](const TileRec& r) { return tile_kind(r.x0, r.y0, r.nx, r.ny); };
+  auto kind_of = [](const TileRec& r) { return r.kind; };
   // All threads: stage the tile of record r, its coefficients into cs[slot].
   auto issue = [&](const TileRec& r, int slot) {
     const int kind = kind_of(r);
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
         mbar_expect_tx(&bar, sizeof(LatCoef<f2>));
       bulk_load(&cs[slot], coef + r.lat, sizeof(LatCoef<f2>), &bar);
     }
-    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, lat_strides(r.sx, r.ny, rows), r.x0, r.y0);
+    if (kind == kAsyncCopy) issue_window_async(win, pool_in + r.offset, r.nx, r.ny, Strides{r.ps, r.rs}, r.x0, r.y0);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     }
     float f[kTileRows][9];
     if (kind == kPlainLoad)
-      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), ti.x0,
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, Strides{ti.ps, ti.rs}, ti.x0,
                                       ti.y0, f, rs[buf]);
     else  // read even after a failed wait (in bounds; the block then returns)
       window_tile(win, f, rs[buf]);
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
       return;
     }
     if (tn < total_tiles) issue(rec[buf ^ 1], buf ^ 1);
-    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), common,
+    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, Strides{ti.ps, ti.rs}, common,
                                     cs[buf], ti.x0, ti.y0, rs[buf]);
     buf ^= 1;
   }
@@ -203,11 +206,14 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
 // Ticket form of the kernel above (the single-lattice k_step_tma_dyn over the tile
 // list): block b starts with list entries b and b + G, then takes 2G, 2G + 1, ...
 // by ticket (queue[0]; queue[1] counts finished blocks, and the last one resets
-// both).  Tile k of a block has its window in buffer k mod 2 and its record and
-// coefficients in slot k mod 3: the record of tile k + 2 is written by the issuer
-// before the barrier of tile k, and its window, coefficients (bulk copy on the
-// buffer's mbarrier) and, for a wrapping tile, the per-thread asynchronous copies
-// are issued after it.  Every staged tile commits one group of asynchronous copies
+// both).  Tile k of a block has its window in buffer k mod 2, its coefficients in
+// slot k mod 3 and its record in slot k mod 4: the record of tile k + 2 is written
+// by the issuer before the barrier of tile k, and its window, coefficients (bulk
+// copy on the buffer's mbarrier) and, for a wrapping tile, the per-thread
+// asynchronous copies are issued after it.  The record's fields are read from
+// shared memory where they are used (the store after the collision reads the
+// lattice's origin, size and strides), so they hold no registers during the
+// collision; the fourth record slot keeps a record until its tile is stored.  Every staged tile commits one group of asynchronous copies
 // (empty unless it wraps), so waiting for all but the newest group completes tile
 // k's.  A wait that gives up sets *err.
 template <int MINB>
@@ -220,12 +226,12 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
   __shared__ float rs[2][kTileY + 2][kTileX + 2];
   __shared__ __align__(16) LatCoef<f2> cs[3];
-  __shared__ TileRec rec[3];
-  __shared__ int tq[3];
+  __shared__ TileRec rec[4];  // tile k's record in slot k mod 4, read until its store
+  __shared__ int tq[4];
   __shared__ __align__(8) unsigned long long bar[2];
   const int total = total_tiles;
   auto win = [&](int slot) { return reinterpret_cast<float*>(base + slot * Win2<float>::buffer); };
-  auto kind_of = [](const TileRec& r) { return tile_kind(r.x0, r.y0, r.nx, r.ny); };
+  auto kind_of = [](const TileRec& r) { return r.kind; };
   const int first = 2 * int(gridDim.x);
   bool dry = first >= total;  // the issuer: no more tickets
   auto draw = [&]() {
@@ -234,11 +240,12 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     dry = t >= total;
     return dry ? total : t;
   };
-  // All threads: stage tile j of the block (record in slot j mod 3).
+  // All threads: stage tile j of the block (record in slot j mod 4, coefficients in
+  // slot j mod 3).
   auto issue = [&](int j) {
     const int q = j % 3, slot = j & 1;
-    const TileRec& r = rec[q];
-    const bool live = tq[q] < total;
+    const TileRec& r = rec[j & 3];
+    const bool live = tq[j & 3] < total;
     const int kind = live ? kind_of(r) : kPlainLoad;
     if (live && threadIdx.x == kIssuer) {
       fence_proxy_async();
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
       bulk_load(&cs[q], coef + r.lat, sizeof(LatCoef<f2>), &bar[slot]);
     }
     if (live && kind == kAsyncCopy)
-      issue_window_async(win(slot), pool_in + r.offset, r.nx, r.ny, lat_strides(r.sx, r.ny, rows), r.x0, r.y0);
+      issue_window_async(win(slot), pool_in + r.offset, r.nx, r.ny, Strides{r.ps, r.rs}, r.x0, r.y0);
     else
       cp_async_commit();
   };
@@ -269,12 +276,12 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
   issue(1);
   unsigned ph = 0u;  // bit s: parity of the next phase of bar[s]
   for (int k = 0;; ++k) {
-    const int q = k % 3, slot = k & 1;
-    if (tq[q] >= total) break;  // uniform; tiles rise, so no later tile is staged
-    const TileRec ti = rec[q];
+    const int q = k % 3, slot = k & 1, rq = k & 3;
+    if (tq[rq] >= total) break;  // uniform; tiles rise, so no later tile is staged
+    const TileRec& ti = rec[rq];  // read where used: the fields stay in shared memory
     const int kind = kind_of(ti);
-    if (threadIdx.x == kIssuer) {  // the record of tile k + 2 (its slot's last reader was tile k - 1)
-      const int q2 = (k + 2) % 3;
+    if (threadIdx.x == kIssuer) {  // the record of tile k + 2 (its slot's last reader was tile k - 2,
+      const int q2 = (k + 2) & 3;   // which every thread finished before the barrier of tile k - 1)
       tq[q2] = pending;
       if (pending < total) rec[q2] = tiles[pending];
       pending = draw();
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
     }
     float f[kTileRows][9];
     if (kind == kPlainLoad)
-      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), ti.x0,
+      load_tile<float, float, kTileY>(pool_in + ti.offset, ti.nx, ti.ny, Strides{ti.ps, ti.rs}, ti.x0,
                                       ti.y0, f, rs[slot]);
     else  // read even after a failed wait (in bounds; the block then stops)
       window_tile(win(slot), f, rs[slot]);
@@ -295,14 +302,16 @@ __global__ void __launch_bounds__(kFusedThreads, MINB)
       if (threadIdx.x == kIssuer) {
         atomicExch(err, 1);
         mbar_wait(&bar[slot], ((ph >> slot) & 1u) ^ 1u);
-        if (tq[(k + 1) % 3] < total) mbar_wait(&bar[slot ^ 1], (ph >> (slot ^ 1)) & 1u);
+        if (tq[(k + 1) & 3] < total) mbar_wait(&bar[slot ^ 1], (ph >> (slot ^ 1)) & 1u);
       }
       cp_async_wait_all();
       break;
     }
     issue(k + 2);
-    collide_tile<f2, float, kTileY>(f, pool_out + ti.offset, ti.nx, ti.ny, lat_strides(ti.sx, ti.ny, rows), common,
-                                    cs[q], ti.x0, ti.y0, rs[slot]);
+    float out[kTileRows][9];
+    collide_nodes<f2, kTileY>(f, common, cs[q], rs[slot], out);
+    store_nodes<float, float, kTileY>(out, pool_out + ti.offset, ti.nx, ti.ny, Strides{ti.ps, ti.rs}, ti.x0,
+                                      ti.y0, Rounding{0u, 0});
   }
   cp_async_wait_all();
   if (threadIdx.x == kIssuer) {
@@ -323,7 +332,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_batch_nonfinite(const float* 
                                                                     unsigned* __restrict__ bad) {
   const TileRec t = tiles[blockIdx.x];
   const int x = t.x0 + (threadIdx.x & (kTileX - 1));
-  const Strides st = rows ? Strides{t.sx, 9 * t.sx} : Strides{t.sx * t.ny, t.sx};
+  const Strides st{t.ps, t.rs};
   int n = 0;
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
@@ -583,10 +592,12 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     h_tiles[s].reserve(b->total_tiles[s]);
     for (int i = 0; i < n; ++i) {
       const BatchLattice& L = b->desc[s][i];
+      const Strides st = lat_strides(L.sx, L.ny, b->rows);
       const int tyn = (ps[i].ny + kShapeTY[s] - 1) / kShapeTY[s];
       for (int r = 0; r < tyn; ++r)
         for (int q = 0; q < L.tiles_x; ++q)
-          h_tiles[s].push_back(TileRec{i, q * kTileX, r * kShapeTY[s], L.nx, L.ny, L.sx, L.offset});
+          h_tiles[s].push_back(TileRec{i, q * kTileX, r * kShapeTY[s], L.nx, L.ny, st.ps, st.rs,
+                                       tile_kind(q * kTileX, r * kShapeTY[s], L.nx, L.ny), L.offset});
     }
   }
   uintptr_t m = align(reinterpret_cast<uintptr_t>(meta));

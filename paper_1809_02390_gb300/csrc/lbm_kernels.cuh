@@ -83,19 +83,18 @@ struct TileShape {
   static constexpr int ring = 2 * (kTileX + 2) + 2 * TY;
 };
 
-// Phase 2 of a tile: force stencil of each thread's two nodes from the shared
-// densities, collision (one packed FP32x2 evaluation for V = f2), store.
-template <typename V, typename store_t, int TY>
-__device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
-                                             store_t* __restrict__ fout, int nx, int ny, Strides st, const VCoef<V>& c,
-                                             const LatCoef<V>& l, int x0, int y0,
-                                             const typename LaneType<V>::type (*rs)[kTileX + 2],
-                                             Rounding rnd = Rounding{0u, 0}) {
+// Phase 2 of a tile, arithmetic part: force stencil of each thread's two nodes
+// from the shared densities and the collision (one packed FP32x2 evaluation for
+// V = f2); out[k] = post-collision deviations of the thread's node in row ty + k
+// stride.
+template <typename V, int TY>
+__device__ __forceinline__ void collide_nodes(const typename LaneType<V>::type (&f)[kTileRows][9], const VCoef<V>& c,
+                                              const LatCoef<V>& l,
+                                              const typename LaneType<V>::type (*rs)[kTileX + 2],
+                                              typename LaneType<V>::type (&out)[kTileRows][9]) {
   using real = typename LaneType<V>::type;
   using Shape = TileShape<TY>;
   const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int gx = x0 + tx;
-  real out[kTileRows][9];
   if constexpr (Lanes<V>::n == 2) {
     // Both nodes' stencils as one packed evaluation: lane k reads row ty + k stride.
     const int lx = tx + 1, l0 = ty + 1, l1 = ty + Shape::stride + 1;
@@ -127,14 +126,34 @@ __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&
       collide(c, l, f[k], Sx, Sy, out[k]);
     }
   }
+}
+
+// Phase 2 of a tile, store part: the thread's two nodes of the tile at (x0, y0).
+template <typename real, typename store_t, int TY>
+__device__ __forceinline__ void store_nodes(const real (&out)[kTileRows][9], store_t* __restrict__ fout, int nx,
+                                            int ny, Strides st, int x0, int y0, Rounding rnd) {
+  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  const int gx = x0 + tx;
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * Shape::stride;
+    const int gy = y0 + ty + k * TileShape<TY>::stride;
     if (gx < nx && gy < ny) {
       const int off = gy * st.rs + gx;
       store9(fout + off, st.ps, out[k], unsigned(gy * nx + gx), rnd);
     }
   }
+}
+
+// Phase 2 of a tile: collide_nodes, then store_nodes.
+template <typename V, typename store_t, int TY>
+__device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
+                                             store_t* __restrict__ fout, int nx, int ny, Strides st, const VCoef<V>& c,
+                                             const LatCoef<V>& l, int x0, int y0,
+                                             const typename LaneType<V>::type (*rs)[kTileX + 2],
+                                             Rounding rnd = Rounding{0u, 0}) {
+  typename LaneType<V>::type out[kTileRows][9];
+  collide_nodes<V, TY>(f, c, l, rs, out);
+  store_nodes<typename LaneType<V>::type, store_t, TY>(out, fout, nx, ny, st, x0, y0, rnd);
 }
 
 struct NoHook {

@@ -124,7 +124,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 
 // Whether the TMA windows of the tile at (x0, y0) lie inside the lattice.
 template <typename S = float>
-__device__ __forceinline__ bool tma_interior(int x0, int y0, int nx, int ny) {
+__host__ __device__ __forceinline__ bool tma_interior(int x0, int y0, int nx, int ny) {
   return x0 >= Win<S>::xoff && x0 + Win<S>::cols - Win<S>::xoff <= nx && y0 >= 2 && y0 + kTmaRows <= ny;
 }
 
@@ -270,7 +270,7 @@ __device__ __forceinline__ void issue_windows(S* win, const CUtensorMap* map, in
 enum TileKind { kTensorCopy = 0, kAsyncCopy = 1, kPlainLoad = 2 };
 
 template <bool ASYNC_EDGES = true, typename S = float>
-__device__ __forceinline__ int tile_kind(int x0, int y0, int nx, int ny) {
+__host__ __device__ __forceinline__ int tile_kind(int x0, int y0, int nx, int ny) {
   return tma_interior<S>(x0, y0, nx, ny) ? kTensorCopy
                                          : (ASYNC_EDGES && async_window_ok(nx, ny) ? kAsyncCopy : kPlainLoad);
 }
