@@ -134,7 +134,9 @@ size_t lb_scratch_bytes(const lb_params* p);
 /* Creates a handle bound to the caller's buffers and stream and initialises the
  * lattice at rest: fbar_i = (M^-1 m_eq(rho0, u = 0))_i - w_i rho_ref, with eta
  * from the EOS at rho0 (the stated initial condition; the paper does not give
- * one).  f_a, f_b: device buffers of lb_state_bytes() each (ping-pong; f_a holds
+ * one), computed in the step's compute type (FP64 for LB_FP64, FP32 otherwise).
+ * Host densities are checked on the device as the state is built: the first node
+ * that is not positive and finite (or, for vdW, not below 1/b) is reported.  f_a, f_b: device buffers of lb_state_bytes() each (ping-pong; f_a holds
  * the state after init).  scratch: device buffer of lb_scratch_bytes() bytes, or
  * NULL (the fused step then walks its tiles statically, and lb_reduce and the
  * two-pass variant are unavailable); it holds the tile tickets of the fused step,

@@ -537,7 +537,6 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     return code;
   };
   std::vector<LatCoef<f2>> h_coef(n);
-  std::vector<VCoef<double>> h_coefd(n);
   size_t off = 0, total_nodes = 0;
   for (int i = 0; i < n; ++i) {
     char err[512] = {0};
@@ -561,7 +560,6 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
                   "lb_batch_init: lattices of one batch must share the EOS (kind, a, b), varpi and the relaxation rates");
     h_coef[i] = LatCoef<f2>{full.G2,        full.rho_ref, full.m2rr, full.lam_RT, full.neg_lam_a,
                             full.neg_2lam_a, full.g15,     full.Q1G2, full.Q2G2,   full.Q78G2};
-    h_coefd[i] = make_vcoef<double>(b->p[i], b->d[i]);
     for (int s = 0; s < kTileLists; ++s) {
       BatchLattice L;
       L.nx = ps[i].nx;
@@ -666,9 +664,12 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   size_t node_off = 0;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     const size_t N = size_t(ps[i].nx) * ps[i].ny;
-    k_init_eq<float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
-        rd + node_off, nullptr, nullptr, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny,
-        lat_strides(b->desc[0][i].sx, ps[i].ny, b->rows), h_coefd[i]);
+    // FP32 arithmetic with the coefficients a single lattice of the same parameters
+    // gets (b->p holds the storage shift rounded to float, as lb_init does), so that
+    // every lattice starts bit-identical to its single-lattice run.
+    k_init_rest<float, float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
+        rd + node_off, static_cast<float*>(pool_a) + b->desc[0][i].offset, ps[i].nx, ps[i].ny,
+        lat_strides(b->desc[0][i].sx, ps[i].ny, b->rows), make_vcoef<float>(b->p[i], b->d[i]), nullptr, 0.0);
     e = cudaGetLastError();
     node_off += N;
   }

@@ -528,7 +528,8 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   cudaError_t e;
   // Host densities: staged in the second population buffer (9 x >= 2 bytes per
   // node hold the 8 of the density and, after them, the two words of the check)
-  // and checked there by k_check_rho0 (positive, finite, below 1/b for vdW).
+  // and checked by the init kernel as it reads them (positive, finite, below 1/b
+  // for vdW).
   unsigned long long* bad = nullptr;
   if (!rho0_on_device) {
     bad = reinterpret_cast<unsigned long long*>(static_cast<char*>(f_b) + N * sizeof(double));
@@ -537,27 +538,21 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
     e = cudaMemcpyAsync(f_b, rho0, N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return bail(e, "cudaMemcpyAsync(rho0)");
     rho_dev = static_cast<const double*>(f_b);
-    int sms = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                   cudaSuccess || sms < 1)
-      sms = 1;
-    const size_t want = (N + 255) / 256, cap = size_t(sms) * 8;
-    k_check_rho0<<<unsigned(want < cap ? want : cap), 256, 0, h->stream>>>(rho_dev, N, p->eos == LB_EOS_VDW,
-                                                                           p->eos_b, bad);
   }
   const unsigned blocks = unsigned((N + 255) / 256);
+  const double vdw_b = p->eos == LB_EOS_VDW ? p->eos_b : 0.0;
   switch (p->precision) {
     case LB_FP64:
-      k_init_eq<double><<<blocks, 256, 0, h->stream>>>(rho_dev, nullptr, nullptr, static_cast<double*>(f_a), p->nx, p->ny, h->st,
-                                                        h->cd);
+      k_init_rest<double, double><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<double*>(f_a), p->nx, p->ny,
+                                                                  h->st, h->cd, bad, vdw_b);
       break;
     case LB_FP32:
-      k_init_eq<float><<<blocks, 256, 0, h->stream>>>(rho_dev, nullptr, nullptr, static_cast<float*>(f_a), p->nx, p->ny, h->st,
-                                                       h->cd);
+      k_init_rest<float, float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<float*>(f_a), p->nx, p->ny, h->st,
+                                                                h->cf, bad, vdw_b);
       break;
     default:
-      k_init_eq<__half><<<blocks, 256, 0, h->stream>>>(rho_dev, nullptr, nullptr, static_cast<__half*>(f_a), p->nx, p->ny, h->st,
-                                                        h->cd);
+      k_init_rest<__half, float><<<blocks, 256, 0, h->stream>>>(rho_dev, static_cast<__half*>(f_a), p->nx, p->ny,
+                                                                 h->st, h->cf, bad, vdw_b);
       break;
   }
   e = cudaGetLastError();

@@ -23,17 +23,37 @@ inline double p_eos_host(const VCoef<double>& c, double r) {
   return c.lam * (r * c.RT * (1.0 + t + t * t - t * t * t) / (om * om * om) - c.a * r * r);
 }
 
-// Validation of an initial density field on the device: bad[0] = smallest index
-// of a density that is not positive and finite, bad[1] = smallest index of one at
-// or above 1/b (vdW only: 1 - b rho must stay positive); both start at
-// 0xff..ff (none).  Grid-stride loop.
-static __global__ void k_check_rho0(const double* __restrict__ rho, size_t n, int vdw, double eos_b,
-                             unsigned long long* __restrict__ bad) {
-  for (size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += size_t(gridDim.x) * blockDim.x) {
-    const double r = rho[k];
-    if (!(r > 0.0) || !isfinite(r)) atomicMin(&bad[0], static_cast<unsigned long long>(k));
-    if (vdw && !(eos_b * r < 1.0)) atomicMin(&bad[1], static_cast<unsigned long long>(k));
+// The rest state of lb_init (u = 0) from an initial density field: f_i = (M^-1
+// m_eq(rho, 0))_i - w_i rho_ref with m_eq of Eq. 3 and the self-tuning eta, in the
+// compute type `real` (FP64 for FP64 storage; FP32 for FP32 and FP16 storage, where
+// FP64 arithmetic on this GPU would cost more than the 20 steps after it), and, if
+// bad is not null, the check of the density: bad[0] = smallest index of a density
+// that is not positive and finite, bad[1] = smallest index of one at or above 1/b
+// (vdW: 1 - b rho must stay positive); both start at 0xff..ff (none), and the
+// check is done in FP64 on the given density.
+template <typename store_t, typename real>
+__global__ void k_init_rest(const double* __restrict__ rho0, store_t* __restrict__ f, int nx, int ny, Strides st,
+                            VCoef<real> c, unsigned long long* __restrict__ bad, double vdw_b) {
+  const size_t k = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= size_t(nx) * ny) return;
+  const double r64 = rho0[k];
+  if (bad) {
+    if (!(r64 > 0.0) || !isfinite(r64)) atomicMin(&bad[0], static_cast<unsigned long long>(k));
+    if (vdw_b > 0.0 && !(vdw_b * r64 < 1.0)) atomicMin(&bad[1], static_cast<unsigned long long>(k));
   }
+  const size_t N = size_t(st.ps);                              // plane stride
+  const size_t n = size_t(st.at(0, int(k % nx), int(k / nx)));  // node (x, y)
+  const real rho = real(r64);
+  real pe, dpe;
+  eos(c, rho, pe, dpe);
+  const real eta = real(3) * (pe + real(0.5) * c.G2 * rho * rho) - rho;
+  const real n0 = (rho - c.rho_ref) / real(9);
+  const real n1 = (real(-2) * rho + real(2) * eta + real(2) * c.rho_ref) / real(36);
+  const real n2 = (rho + c.beta2 * eta - c.rho_ref) / real(36);
+  const real axis = n0 - n1 - real(2) * n2, diag = n0 + real(2) * n1 + n2;
+  const real o[9] = {n0 - real(4) * n1 + real(4) * n2, axis, axis, axis, axis, diag, diag, diag, diag};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) st_st(f + (n + size_t(i) * N), o[i]);
 }
 
 // Equilibrium state from a density and a velocity field (computed in FP64, rounded

@@ -139,3 +139,15 @@ def test_scratch_holds_the_tile_tickets(capi):
     plane64 = (100 * 30 * 8 + 255) // 256 * 256
     assert capi.lb_scratch_bytes(q) - capi.lb_scratch_bytes(p) == plane64 - plane32
     assert capi.lb_scratch_bytes(p) >= plane32 + 256
+
+
+def test_size_limit_of_32_bit_offsets(capi):
+    """The kernels index populations with 32-bit offsets: 9 nx ny must stay below
+    2^31.  15446^2 and 16384 x 14563 are accepted, one node row more is not."""
+    ok = capi.lb_derive(capi.make_params(15446, 15446))
+    assert ok["rho_l"] > ok["rho_g"]
+    capi.lb_derive(capi.make_params(16384, 14563))
+    for nx, ny in ((15447, 15447), (16384, 14564)):
+        with pytest.raises(capi.LBError) as ei:
+            capi.lb_derive(capi.make_params(nx, ny))
+        assert ei.value.code == capi.LB_EINVAL and "too large" in str(ei.value)

@@ -303,3 +303,22 @@ def test_diagonal_interface_matches_the_axis_aligned_one(orc, mistake):
         assert wd == pytest.approx(wa, rel=1e-2)
     else:
         assert abs(gd / ga - 1) > 8e-2 and abs(wd / wa - 1) > 5e-2
+
+
+def test_profiles_do_not_depend_on_K_EOS(orc):
+    """Supplement Fig. 2: at Tr = 0.8 and W = 10 (K_INT = 2.2949, CS EOS a = 1, b = 4)
+    the density profiles for K_EOS = 1e-2 ... 1e2 are identical.  With G from Eq. 21
+    and c from Eq. 22 the lattice-unit parameters lam = K_EOS / c^2 and G2 = G^2 / c^2
+    do not depend on K_EOS, so the runs agree to rounding; the flat interface they
+    relax to has the pressure-tensor thickness 10 within 2% (10.12 after 10,000
+    steps, still relaxing towards it: 10.07 after 20,000)."""
+    kw = dict(eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.8, K_int=2.2949)
+    ps = [op.from_physical(K_eos=k, **kw) for k in (1e-2, 1e-1, 1.0, 1e1, 1e2)]
+    for p in ps:
+        assert p.lam == pytest.approx(ps[2].lam, rel=1e-12) and p.G2 == pytest.approx(ps[2].G2, rel=1e-12)
+    W = thermo.interface(thermo.make_eos("cs", 1.0, 4.0, 1.0, 0.8), 2.2949)["W"]
+    assert W == pytest.approx(10.0, rel=1e-4)
+    prof = inputs.slab(160, 2, 80, W / np.arctanh(0.9), ps[0].rho_g, ps[0].rho_l)
+    runs = [orc.macro(p, orc.step(p, orc.init_feq(p, prof), 10000))[0][0] for p in (ps[0], ps[-1])]
+    assert np.abs(runs[0] - runs[1]).max() <= 1e-12 * runs[0].max()
+    assert _thickness(runs[0][:80], runs[0][0], runs[0][80]) == pytest.approx(W, rel=2e-2)
