@@ -144,7 +144,9 @@ size_t lb_scratch_bytes(const lb_params* p);
  * (rho0_on_device = 0; copied through f_b, synchronously) or the device (1).
  * The handle keeps the pointers; the caller keeps ownership and must keep the
  * buffers alive until lb_free.  Fails with LB_EINVAL for bad parameters or
- * non-positive densities on the host path, LB_ENOMEM for a short scratch. */
+ * non-positive densities on the host path, LB_ENOMEM for a short scratch or when
+ * 4096 handles are already live (each holds one slot of a static array of device
+ * words for lb_status until lb_free). */
 int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scratch,
             size_t scratch_bytes, const double* rho0, int rho0_on_device, void* stream);
 
@@ -294,6 +296,10 @@ void* lb_batch_state(lb_batch* b);
 int64_t lb_batch_steps_done(const lb_batch* b);
 int64_t lb_batch_offset(const lb_batch* b, int i);
 int lb_batch_row_stride(const lb_batch* b, int i);
+/* Density of lattice i at the time level of its last collision, rho = sum_i fbar_i
+ * (Eq. 5; the collision conserves mass): rho, a device array of ny*nx floats
+ * ([y][x]), written asynchronously on the batch's stream. */
+int lb_batch_density(lb_batch* b, int i, void* rho);
 int lb_batch_derived(const lb_batch* b, int i, lb_derived* out);
 const char* lb_batch_last_error(const lb_batch* b);
 void lb_batch_free(lb_batch* b);

@@ -237,7 +237,13 @@ class Batch:
         return [i for i, c in enumerate(counts) if c]
 
     def density(self, i: int):
-        return self.state(i).double().sum(0) + self.rho_refs[i]
+        """Density of lattice i ([ny, nx] float32 tensor on the device, lb_batch_density)."""
+        torch = _torch()
+        ny, nx = self.shapes[i]
+        rho = torch.empty((ny, nx), dtype=torch.float32, device=self.pool_a.device)
+        capi.lb_batch_density(self.b, i, rho.data_ptr())
+        self.stream.synchronize()
+        return rho
 
     def derived(self, i: int) -> dict:
         return capi.lb_batch_derived(self.b, i)

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("lb_batch_steps_done", ctypes.c_int64, [_V]),
     ("lb_batch_offset", ctypes.c_int64, [_V, ctypes.c_int]),
     ("lb_batch_row_stride", ctypes.c_int, [_V, ctypes.c_int]),
+    ("lb_batch_density", ctypes.c_int, [_V, ctypes.c_int, _V]),
     ("lb_batch_uses_tma", ctypes.c_int, [_V]),
     ("lb_batch_set_config", ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
     ("lb_batch_status", ctypes.c_int, [_V]),
@@ -279,6 +280,10 @@ def lb_batch_nonfinite(b: int, n: int) -> tuple[int, list[int]]:
     if rc < 0:
         check_batch(rc, b)
     return rc, list(counts)
+
+
+def lb_batch_density(b: int, i: int, rho: int) -> None:
+    check_batch(lib().lb_batch_density(b, i, rho), b)
 
 
 def lb_batch_state(b: int) -> int:

@@ -854,6 +854,18 @@ int lb_batch_row_stride(const lb_batch* b, int i) {
   return b->desc[0][i].sx;
 }
 
+int lb_batch_density(lb_batch* b, int i, void* rho) {
+  if (!b || i < 0 || i >= b->n || !rho) return LB_EINVAL;
+  const BatchLattice& L = b->desc[0][i];
+  const size_t N = size_t(L.nx) * L.ny;
+  k_rho_local<float, float><<<unsigned((N + 255) / 256), 256, 0, b->stream>>>(
+      static_cast<const float*>(b->pool[b->cur]) + L.offset, static_cast<float*>(rho), L.nx, L.ny,
+      lat_strides(L.sx, L.ny, b->rows), float(b->p[i].rho_ref));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return berr(b, LB_ECUDA, "lb_batch_density: %s", cudaGetErrorString(e));
+  return LB_OK;
+}
+
 int lb_batch_derived(const lb_batch* b, int i, lb_derived* out) {
   if (!b || i < 0 || i >= b->n || !out) return LB_EINVAL;
   *out = b->d[i];

@@ -110,6 +110,32 @@ def test_moments_and_reduce(orc):
     assert r["p_center"] == pytest.approx(orc.eos(p, rho_o[32, 32])[0], rel=1e-12)
 
 
+@pytest.mark.parametrize("static", [False, True])
+def test_reduce_carnahan_starling_against_the_oracle(orc, static):
+    """lb_reduce and lb_reduce_static on a Carnahan-Starling droplet (a = 1, b = 4,
+    Tr = 0.7, K_INT = 2, K_EOS = 0.5; 80 x 60, 40 FP64 steps): the sums against the
+    oracle's fields, and both probe pressures against the oracle's EOS (Eq. 20) at
+    the oracle's densities of the probe nodes."""
+    from paper_1809_02390_gb300 import capi
+
+    kw = dict(eos="cs", a=1.0, b=4.0, R=1.0, Tr=0.7, K_int=2.0, K_eos=0.5)
+    p = oracle_params(**kw)
+    rho0 = inputs.droplet(80, 60, 14.0, 8.0, p.rho_g, p.rho_l)
+    rho_o, ux_o, uy_o = orc.macro(p, orc.step(p, orc.init_feq(p, rho0), 40))
+    lat = lattice(rho0, "fp64", eos="cs", eos_a=1.0, eos_b=4.0, R_gas=1.0, Tr=0.7, K_int=2.0, K_eos=0.5)
+    lat.step(40)
+    v = capi.lb_reduce_static(lat.h) if static else capi.lb_reduce(lat.h)
+    mass, mx, my, p_c, p_0, n_liq, r_min, r_max = v
+    assert mass == pytest.approx(rho_o.sum(), rel=1e-13)
+    assert mx == pytest.approx((rho_o * ux_o).sum(), abs=1e-11)
+    assert my == pytest.approx((rho_o * uy_o).sum(), abs=1e-11)
+    assert p_c == pytest.approx(orc.eos(p, rho_o[30, 40])[0], rel=1e-12)
+    assert p_0 == pytest.approx(orc.eos(p, rho_o[0, 0])[0], rel=1e-12)
+    assert n_liq == (rho_o > 0.5 * (p.rho_g + p.rho_l)).sum()
+    assert r_min == pytest.approx(rho_o.min(), rel=1e-13) and r_max == pytest.approx(rho_o.max(), rel=1e-13)
+    lat.close()
+
+
 def test_deterministic():
     p, rho0 = droplet64()
     a = lattice(rho0, "fp32")
@@ -314,3 +340,34 @@ def test_set_equilibrium_matches_oracle(orc, layout):
     l32.set_equilibrium(rho, ux, None)
     ref = orc.init_eq(p, rho, ux, None)
     assert rel_inf(gpu_populations(l32), ref) <= 2e-7
+
+
+def test_largest_lattice_sampled(orc):
+    """The largest lattice the library accepts (9 nx ny just below 2^31, the limit of
+    its 32-bit population offsets): 16384 x 14563 FP32 in the rows layout of the
+    benchmark (8.6 GB per population buffer; 14563 rows leave a ragged last tile
+    row).  Two steps from a seeded spinodal field, checked at sampled nodes against
+    the oracle on each node's own 9 x 9 neighbourhood, including the last node of
+    the buffer, the four corners (periodic wrap) and the last ragged tile row."""
+    p = oracle_params(Tr=0.8, K_int=1.0)
+    nx, ny = 16384, 14563
+    assert 9 * nx * ny < 2 ** 31 <= 9 * nx * (ny + 1)
+    rho0 = inputs.spinodal(nx, ny, 0.5 * (p.rho_g + p.rho_l), 0.01, seed=5)
+    lat = lattice(rho0, "fp32", Tr=0.8, K_int=1.0, layout="rows")
+    steps = 2
+    lat.step(steps)
+    torch.cuda.synchronize()
+    st = lat.state()
+    rng = np.random.default_rng(9)
+    pts = [(0, 0), (nx - 1, ny - 1), (nx - 1, 0), (0, ny - 1), (8191, 14560), (31, ny - 3)]
+    pts += [(int(x), int(y)) for x, y in zip(rng.integers(0, nx, 12), rng.integers(0, ny, 12))]
+    worst = 0.0
+    for x, y in pts:
+        patch_rho = _patch(rho0[None], x, y, 2 * steps + 2)[0]
+        ref = orc.step(p, orc.init_feq(p, patch_rho), steps)[:, 2 * steps + 2, 2 * steps + 2]
+        got = st[:, y, x].double().cpu().numpy() + lat.rho_ref * W_REST
+        worst = max(worst, float(np.abs(got - ref).max() / np.abs(ref).max()))
+    assert worst <= 2e-6
+    lat.close()
+    del st
+    torch.cuda.empty_cache()
