@@ -135,7 +135,9 @@ def workload_rho(n: int, seed: int):
 
 
 def time_steps(lat, steps: int, torch) -> float:
-    """Milliseconds for `steps` time steps, CUDA events on the launching stream."""
+    """Milliseconds for `steps` time steps, CUDA events on the lattice's stream (runs
+    of 64 steps replay a graph on the handle's own stream, which lb_step orders
+    between the work before and after it on this one)."""
     s = lat.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

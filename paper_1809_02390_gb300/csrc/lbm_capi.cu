@@ -282,7 +282,13 @@ void release_wait_slot(lb_handle* h) {
 }
 
 void destroy(lb_handle* h) {
+  if (!h) return;
   release_wait_slot(h);
+  for (int k = 0; k < 2; ++k) {
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    if (h->gev[k]) cudaEventDestroy(h->gev[k]);
+  }
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h;
 }
 
@@ -574,15 +580,96 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   return LB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Steps per captured graph (even, so a replay ends on the buffer it started from).
+constexpr int kStepGraph = 64;
+
+void launch_one_step(lb_handle* h) {
+  switch (h->p.precision) {
+    case LB_FP64: launch_step<double, double, double>(h, h->cd, h->cd); break;
+    case LB_FP32: launch_step<f2, float, float>(h, h->c2, h->cf); break;
+    default: launch_step<f2, float, __half>(h, h->c2, h->cf); break;
+  }
+}
+
+// The launch configuration a graph bakes in: kernel form and grid sizes.
+long long step_config(const lb_handle* h) {
+  return (long long)h->variant | ((long long)h->use_tma << 2) | ((long long)h->use_dyn << 3) |
+         ((long long)h->tma_grid << 4) | ((long long)h->dyn_grid << 34);
+}
+
+// Captures (once per starting buffer and configuration) kStepGraph steps into a
+// graph on the internal stream.  False, with the handle left as it was, when the
+// graph cannot be made (then the steps are launched directly).
+bool ensure_step_graph(lb_handle* h) {
+  const int from = h->cur;
+  const long long cfg = step_config(h);
+  if (h->graph[from] && h->graph_cfg[from] == cfg) return true;
+  if (h->graph[from]) {
+    cudaGraphExecDestroy(h->graph[from]);
+    h->graph[from] = nullptr;
+  }
+  if (!h->gstream) {
+    if (cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    for (int k = 0; k < 2; ++k)
+      if (cudaEventCreateWithFlags(&h->gev[k], cudaEventDisableTiming) != cudaSuccess) return false;
+  }
+  cudaStream_t caller = h->stream;
+  h->stream = h->gstream;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int s = 0; s < kStepGraph; ++s) {
+      launch_one_step(h);
+      h->cur = 1 - h->cur;
+    }
+    e = cudaStreamEndCapture(h->gstream, &g);
+  }
+  h->stream = caller;
+  h->cur = from;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[from], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear a capture error; the direct launches report anything lasting
+    h->graph[from] = nullptr;
+    return false;
+  }
+  h->graph_cfg[from] = cfg;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lb_step(lb_handle* h, int64_t nsteps) {
   if (!h) return fail(nullptr, LB_EINVAL, "null handle");
   if (nsteps < 0) return fail(h, LB_EINVAL, "nsteps must be >= 0");
-  for (int64_t s = 0; s < nsteps; ++s) {
-    switch (h->p.precision) {
-      case LB_FP64: launch_step<double, double, double>(h, h->cd, h->cd); break;
-      case LB_FP32: launch_step<f2, float, float>(h, h->c2, h->cf); break;
-      default: launch_step<f2, float, __half>(h, h->c2, h->cf); break;
+  // Runs of kStepGraph steps replay a captured graph on the handle's internal
+  // stream, ordered after the caller's stream's earlier work and before its later
+  // work by two events.  FP16 storage launches every step directly: its stochastic
+  // rounding takes a new seed per step.
+  if (nsteps >= kStepGraph && h->p.precision != LB_FP16S && !h->graph_off) {
+    if (!ensure_step_graph(h)) {
+      h->graph_off = true;
+    } else {
+      LB_CUDA(h, cudaEventRecord(h->gev[0], h->stream));
+      LB_CUDA(h, cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
+      while (nsteps >= kStepGraph) {
+        if (!ensure_step_graph(h)) return fail(h, LB_ECUDA, "step graph capture failed");
+        LB_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->gstream));
+        h->steps += kStepGraph;
+        nsteps -= kStepGraph;
+      }
+      LB_CUDA(h, cudaEventRecord(h->gev[1], h->gstream));
+      LB_CUDA(h, cudaStreamWaitEvent(h->stream, h->gev[1], 0));
     }
+  }
+  for (int64_t s = 0; s < nsteps; ++s) {
+    launch_one_step(h);
     LB_CUDA(h, cudaGetLastError());
     h->cur = 1 - h->cur;
     ++h->steps;

@@ -27,6 +27,14 @@ struct lb_handle {
   CUtensorMap tmap[2];    // 3-D maps of f[0] and f[1]: (x, y, plane), rows layout (x, plane, y)
   int* wait_error;        // this handle's device word, set by a bounded wait that gave up
   int wait_slot;          // its index in the library's array of such words (-1: none taken)
+  // Replay of runs of steps (lb_step): graphs of kStepGraph steps captured on an
+  // internal stream, one per starting buffer, with the launch configuration they
+  // were captured for; events order them after and before the caller's stream.
+  cudaStream_t gstream;
+  cudaEvent_t gev[2];
+  cudaGraphExec_t graph[2];
+  long long graph_cfg[2];
+  bool graph_off;         // capture failed once: direct launches only
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
   lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
   lbm::VCoef<double> cd;

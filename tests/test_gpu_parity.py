@@ -161,7 +161,10 @@ def test_full_size_spinodal_sampled(orc):
     p = oracle_params(Tr=0.8, K_int=1.0)
     n = 4096
     rho0 = inputs.spinodal(n, n, 0.5 * (p.rho_g + p.rho_l), 0.01, seed=0)
-    lat = lattice(rho0, "fp32", Tr=0.8, K_int=1.0)
+    lat = lattice(rho0, "fp32", Tr=0.8, K_int=1.0, layout="rows")
+    from paper_1809_02390_gb300 import capi
+
+    assert capi.lb_uses_tma(lat.h) and capi.lb_tile_dispatch(lat.h)  # the benchmark's kernel
     steps = 2
     lat.step(steps)
     torch.cuda.synchronize()
@@ -340,6 +343,28 @@ def test_set_equilibrium_matches_oracle(orc, layout):
     l32.set_equilibrium(rho, ux, None)
     ref = orc.init_eq(p, rho, ux, None)
     assert rel_inf(gpu_populations(l32), ref) <= 2e-7
+
+
+def test_host_and_device_initial_densities_agree():
+    """lb_init from host densities (copied and checked on the device, the end-to-end
+    path of the benchmark) and from the same densities already on the device give
+    the same state, bit for bit, in every storage precision."""
+    from paper_1809_02390_gb300 import Lattice
+
+    p = oracle_params(Tr=0.8, K_int=1.0)
+    rho0 = inputs.spinodal(160, 96, 0.5 * (p.rho_g + p.rho_l), 0.01, seed=4)
+    shift = float(np.float32(rho0.mean()))  # the same storage shift for both (the default is a mean)
+    for precision in ("fp64", "fp32", "fp16s"):
+        a = Lattice(rho0, precision=precision, Tr=0.8, layout="rows", rho_ref=shift)
+        b = Lattice(torch.from_numpy(rho0).cuda(), precision=precision, Tr=0.8, layout="rows", rho_ref=shift)
+        torch.cuda.synchronize()
+        assert torch.equal(a.buffer(), b.buffer()), precision
+        a.step(10)
+        b.step(10)
+        torch.cuda.synchronize()
+        assert torch.equal(a.buffer(), b.buffer()), precision
+        a.close()
+        b.close()
 
 
 def test_largest_lattice_sampled(orc):
