@@ -105,33 +105,50 @@ __host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
   return x;
 }
 
-// FP32 -> FP16 with stochastic rounding: a dither of 13 bits (the mantissa bits a
-// half drops) is added to the magnitude's bit pattern, then the result is
-// truncated toward zero.  A value between two halves goes up with probability
-// equal to its distance from the lower one, so the rounding error has zero mean
-// (for normal halves; below 2^-14 the dither covers only part of the dropped bits).
-__device__ __forceinline__ void st_st_sr(__half* p, float v, unsigned dither) {
-  *p = __float2half_rz(__uint_as_float(__float_as_uint(v) + (dither & 0x1fffu)));
-}
-
 // Rounding of FP16 stores: stochastic with per-step seed, or nearest.
 struct Rounding {
   unsigned seed;
   int stochastic;
 };
 
-// Stores the nine populations of node `node` (index within the lattice) at
-// p + i * plane; stochastic rounding draws nine dithers from a linear
-// congruential sequence started at a hash of (node, seed).
+// FP32 -> FP16 pair with stochastic rounding (Blackwell's cvt.rs.f16x2.f32): each
+// value is rounded toward zero after 13 random bits are added below the half's
+// last mantissa bit (bits 12..0 of rbits for the low half, 28..16 for the high
+// one), so a value between two halves goes up with probability equal to its
+// distance from the lower one and the rounding error has zero mean.  The two
+// halves are converted independently.  Returns (high << 16) | low.
+__device__ __forceinline__ unsigned cvt_rs_f16x2(float lo, float hi, unsigned rbits) {
+  unsigned r;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(rbits));
+  return r;
+}
+
+// Random words of the FP16 stores.  The nodes (2j, y) and (2j + 1, y) of a row
+// form pair j; its words are a linear congruential sequence s_1, s_2, ... started
+// at a hash of (pair index, step seed), population i taking s_{i+1} whitened as
+// s xor (s >> 16) (the low half's bits then depend on the sequence's high bits).
+// Node 2j rounds with the low bits of the word, node 2j + 1 with the high ones,
+// whichever kernel stores it.
+__device__ __forceinline__ unsigned sr_start(int x, int y, int nx, unsigned seed) {
+  return mix32(unsigned(y * ((nx + 1) >> 1) + (x >> 1)) * 0x9e3779b9u + seed);
+}
+__device__ __forceinline__ unsigned sr_next(unsigned& s) {
+  s = s * 1664525u + 1013904223u;
+  return s ^ (s >> 16);
+}
+
+// Stores the nine populations of node (x, y) of a lattice nx wide at p + i * plane.
 template <typename store_t>
-__device__ __forceinline__ void store9(store_t* p, int plane, const float (&o)[9], unsigned node, Rounding r) {
+__device__ __forceinline__ void store9(store_t* p, int plane, const float (&o)[9], int x, int y, int nx, Rounding r) {
   if constexpr (sizeof(store_t) == 2) {
     if (r.stochastic) {
-      unsigned s = mix32(node * 0x9e3779b9u + r.seed);
+      unsigned s = sr_start(x, y, nx, r.seed);
+      const bool odd = x & 1;
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        s = s * 1664525u + 1013904223u;
-        st_st_sr(p + i * plane, o[i], s >> 19);
+        const unsigned w = sr_next(s);
+        const unsigned h = cvt_rs_f16x2(odd ? 0.f : o[i], odd ? o[i] : 0.f, w);
+        p[i * plane] = __ushort_as_half((unsigned short)(odd ? h >> 16 : h & 0xffffu));
       }
       return;
     }
@@ -140,9 +157,25 @@ __device__ __forceinline__ void store9(store_t* p, int plane, const float (&o)[9
   for (int i = 0; i < 9; ++i) st_st(p + i * plane, o[i]);
 }
 template <typename store_t>
-__device__ __forceinline__ void store9(store_t* p, int plane, const double (&o)[9], unsigned, Rounding) {
+__device__ __forceinline__ void store9(store_t* p, int plane, const double (&o)[9], int, int, int, Rounding) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) st_st(p + i * plane, o[i]);
+}
+
+// FP16: the nine populations of nodes (x, y) and (x + 1, y), x even, as one half
+// pair each at p + i * plane (p and plane even: 4-byte aligned pairs); the same
+// halves as two store9 calls.
+__device__ __forceinline__ void store9_pair(__half* p, int plane, const float (&o0)[9], const float (&o1)[9], int x,
+                                            int y, int nx, Rounding r) {
+  if (r.stochastic) {
+    unsigned s = sr_start(x, y, nx, r.seed);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      *reinterpret_cast<unsigned*>(p + i * plane) = cvt_rs_f16x2(o0[i], o1[i], sr_next(s));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) *reinterpret_cast<__half2*>(p + i * plane) = __floats2half2_rn(o0[i], o1[i]);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -83,21 +83,79 @@ struct TileShape {
   static constexpr int ring = 2 * (kTileX + 2) + 2 * TY;
 };
 
+// The two nodes of a TX x TY tile a thread owns (tile-local column lx(k), row
+// ly(k), k = 0, 1).  Row pairs: (t mod 32, t / 32 + k TY / 2), one warp per
+// 32-column strip.  Column pairs (XP; the FP16-storage kernels): (2 (t mod 16) + k,
+// row(t)), so that the two nodes' populations are adjacent in memory and leave as
+// one 4-byte half pair per population, and their stencils come from aligned
+// 8-byte reads of the density tile.  Warp w covers rows r and r + 2, r = 4 (w / 2)
+// + w mod 2: two window rows apart in shared memory are 48 words (FP16 windows,
+// 24 words a row) or 80 (FP32, 40), 16 banks apart, so the two half-warps' reads
+// of a window row fall in different banks.
+template <int TY, bool XP>
+struct NodeMap {
+  static_assert(!XP || TY % 4 == 0, "column pairs take rows in groups of four");
+  __device__ static int lx(int k) { return XP ? 2 * int(threadIdx.x & 15u) + k : int(threadIdx.x & 31u); }
+  __device__ static int ly(int k) {
+    if constexpr (XP) {
+      const int w = int(threadIdx.x >> 5);
+      return 4 * (w >> 1) + (w & 1) + 2 * int((threadIdx.x >> 4) & 1u);
+    } else {
+      return int(threadIdx.x >> 5) + k * (TY / kTileRows);
+    }
+  }
+};
+
+// Column pairs for 2-byte storage.
+template <typename S>
+__host__ __device__ constexpr bool xpairs() {
+  return sizeof(S) == 2;
+}
+
 // Phase 2 of a tile, arithmetic part: force stencil of each thread's two nodes
 // from the shared densities and the collision (one packed FP32x2 evaluation for
 // V = f2); out[k] = post-collision deviations of the thread's node in row ty + k
 // stride.
-template <typename V, int TY>
+template <typename V, int TY, bool XP = false>
 __device__ __forceinline__ void collide_nodes(const typename LaneType<V>::type (&f)[kTileRows][9], const VCoef<V>& c,
                                               const LatCoef<V>& l,
                                               const typename LaneType<V>::type (*rs)[kTileX + 2],
                                               typename LaneType<V>::type (&out)[kTileRows][9]) {
   using real = typename LaneType<V>::type;
-  using Shape = TileShape<TY>;
-  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  if constexpr (Lanes<V>::n == 2) {
+  if constexpr (Lanes<V>::n == 2 && XP) {
+    // Lanes = columns 2j + 1, 2j + 2 of density rows ly .. ly + 2 (j = t mod 16);
+    // each row's cells 2j .. 2j + 3 arrive as two aligned float2 reads (rows of
+    // 34 floats, the tile 8-byte aligned): the pairs at dx = -1 and +1 as they are,
+    // the one at dx = 0 from their inner halves.
+    const int j = threadIdx.x & 15u, ly = NodeMap<TY, XP>::ly(0);
+    float2 a[3], b[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float2* q = reinterpret_cast<const float2*>(rs[ly + r]) + j;
+      a[r] = q[0];
+      b[r] = q[1];
+    }
+    auto mid = [&](int r) {
+      V v;
+      v.v = make_float2(a[r].y, b[r].x);
+      return v;
+    };
+    const V ml{a[0]}, mc = mid(0), mr{b[0]}, cl{a[1]}, cr{b[1]}, pl{a[2]}, pc = mid(2), pr{b[2]};
+    const V Sxp = fmav(c.third, cr - cl, c.twelfth * ((pr - pl) + (mr - ml)));
+    const V Syp = fmav(c.third, pc - mc, c.twelfth * ((pr + pl) - (mr + ml)));
+    V d[9], o[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i].v = make_float2(f[0][i], f[1][i]);
+    collide(c, l, d, Sxp, Syp, o);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      out[0][i] = o[i].v.x;
+      out[1][i] = o[i].v.y;
+    }
+  } else if constexpr (Lanes<V>::n == 2) {
     // Both nodes' stencils as one packed evaluation: lane k reads row ty + k stride.
-    const int lx = tx + 1, l0 = ty + 1, l1 = ty + Shape::stride + 1;
+    const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+    const int lx = tx + 1, l0 = ty + 1, l1 = ty + TileShape<TY>::stride + 1;
     auto pair = [&](int dy, int dx) {
       V v;
       v.v = make_float2(rs[l0 + dy][lx + dx], rs[l1 + dy][lx + dx]);
@@ -117,9 +175,10 @@ __device__ __forceinline__ void collide_nodes(const typename LaneType<V>::type (
       out[1][i] = o[i].v.y;
     }
   } else {
+    using M = NodeMap<TY, XP>;
 #pragma unroll
     for (int k = 0; k < kTileRows; ++k) {
-      const int ly = ty + k * Shape::stride + 1, lx = tx + 1;
+      const int ly = M::ly(k) + 1, lx = M::lx(k) + 1;
       real Sx, Sy;
       stencil(rs[ly - 1][lx - 1], rs[ly - 1][lx], rs[ly - 1][lx + 1], rs[ly][lx - 1], rs[ly][lx + 1],
               rs[ly + 1][lx - 1], rs[ly + 1][lx], rs[ly + 1][lx + 1], Sx, Sy);
@@ -129,31 +188,35 @@ __device__ __forceinline__ void collide_nodes(const typename LaneType<V>::type (
 }
 
 // Phase 2 of a tile, store part: the thread's two nodes of the tile at (x0, y0).
-template <typename real, typename store_t, int TY>
+// FP16 column pairs of an even-width lattice leave as half pairs.
+template <typename real, typename store_t, int TY, bool XP = false>
 __device__ __forceinline__ void store_nodes(const real (&out)[kTileRows][9], store_t* __restrict__ fout, int nx,
                                             int ny, Strides st, int x0, int y0, Rounding rnd) {
-  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
-  const int gx = x0 + tx;
+  using M = NodeMap<TY, XP>;
+  if constexpr (XP && sizeof(real) == 4 && sizeof(store_t) == 2) {
+    const int gx = x0 + M::lx(0), gy = y0 + M::ly(0);
+    if ((nx & 1) == 0) {  // gx even, so gx < nx implies gx + 1 < nx
+      if (gx < nx && gy < ny) store9_pair(fout + (gy * st.rs + gx), st.ps, out[0], out[1], gx, gy, nx, rnd);
+      return;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * TileShape<TY>::stride;
-    if (gx < nx && gy < ny) {
-      const int off = gy * st.rs + gx;
-      store9(fout + off, st.ps, out[k], unsigned(gy * nx + gx), rnd);
-    }
+    const int gx = x0 + M::lx(k), gy = y0 + M::ly(k);
+    if (gx < nx && gy < ny) store9(fout + (gy * st.rs + gx), st.ps, out[k], gx, gy, nx, rnd);
   }
 }
 
 // Phase 2 of a tile: collide_nodes, then store_nodes.
-template <typename V, typename store_t, int TY>
+template <typename V, typename store_t, int TY, bool XP = false>
 __device__ __forceinline__ void collide_tile(const typename LaneType<V>::type (&f)[kTileRows][9],
                                              store_t* __restrict__ fout, int nx, int ny, Strides st, const VCoef<V>& c,
                                              const LatCoef<V>& l, int x0, int y0,
                                              const typename LaneType<V>::type (*rs)[kTileX + 2],
                                              Rounding rnd = Rounding{0u, 0}) {
   typename LaneType<V>::type out[kTileRows][9];
-  collide_nodes<V, TY>(f, c, l, rs, out);
-  store_nodes<typename LaneType<V>::type, store_t, TY>(out, fout, nx, ny, st, x0, y0, rnd);
+  collide_nodes<V, TY, XP>(f, c, l, rs, out);
+  store_nodes<typename LaneType<V>::type, store_t, TY, XP>(out, fout, nx, ny, st, x0, y0, rnd);
 }
 
 struct NoHook {
@@ -164,18 +227,17 @@ struct NoHook {
 // nodes into f and writes the densities of tile + ring to rs (shared array of
 // (TY + 2) x (TX + 2) densities).  (x0, y0): tile origin; st: the layout.
 // Periodic wrap.
-template <typename real, typename store_t, int TY>
+template <typename real, typename store_t, int TY, bool XP = false>
 __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int nx, int ny, Strides st, int x0,
                                           int y0, real (&f)[kTileRows][9], real (*rs)[kTileX + 2]) {
   using Shape = TileShape<TY>;
-  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  using M = NodeMap<TY, XP>;
   const bool small = nx <= kTileX || ny <= TY;  // tiles may wrap more than once
-  const int gx = x0 + tx;
-  const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
-  const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
 #pragma unroll
   for (int k = 0; k < kTileRows; ++k) {
-    const int gy = y0 + ty + k * Shape::stride;
+    const int gx = x0 + M::lx(k), gy = y0 + M::ly(k);
+    const int xc = small ? wrap(gx, nx) : wrap1(gx, nx);
+    const int xm = xc == 0 ? nx - 1 : xc - 1, xp = xc == nx - 1 ? 0 : xc + 1;
     pull_row(fin, st.ps, st.rs, ny, small ? wrap(gy, ny) : wrap1(gy, ny), xm, xc, xp, f[k]);
   }
   // Ring: the row above, the row below, then the left and right columns.
@@ -198,33 +260,34 @@ __device__ __forceinline__ void load_tile(const store_t* __restrict__ fin, int n
     pull_row(fin, st.ps, st.rs, ny, hy, hx == 0 ? nx - 1 : hx - 1, hx, hx == nx - 1 ? 0 : hx + 1, g);
   }
 #pragma unroll
-  for (int k = 0; k < kTileRows; ++k) rs[ty + k * Shape::stride + 1][tx + 1] = sum9(f[k]);
+  for (int k = 0; k < kTileRows; ++k) rs[M::ly(k) + 1][M::lx(k) + 1] = sum9(f[k]);
   if (ring) rs[wy][wx] = sum9(g);
 }
 
 // One fused step of a tile: load_tile, block barrier, collide_tile.
 // before_sync() runs after all phase-1 loads are issued and before the block
 // barrier (the batched kernel stores its lattice coefficients there).
-template <typename V, typename store_t, int TY, typename Hook = NoHook>
+template <typename V, typename store_t, int TY, typename Hook = NoHook, bool XP = false>
 __device__ __forceinline__ void step_tile(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx,
                                           int ny, Strides st, const VCoef<V>& c, const LatCoef<V>& l, int x0, int y0,
                                           typename LaneType<V>::type (*rs)[kTileX + 2],
                                           const Hook& before_sync = Hook(), Rounding rnd = Rounding{0u, 0}) {
   using real = typename LaneType<V>::type;
   real f[kTileRows][9];
-  load_tile<real, store_t, TY>(fin, nx, ny, st, x0, y0, f, rs);
+  load_tile<real, store_t, TY, XP>(fin, nx, ny, st, x0, y0, f, rs);
   before_sync();
   __syncthreads();
-  collide_tile<V, store_t, TY>(f, fout, nx, ny, st, c, l, x0, y0, rs, rnd);
+  collide_tile<V, store_t, TY, XP>(f, fout, nx, ny, st, c, l, x0, y0, rs, rnd);
 }
 
 template <typename V, typename store_t>
 __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
     k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, Strides st,
                  VCoef<V> c, Rounding rnd) {
-  __shared__ typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
-  step_tile<V, store_t, kTileY>(fin, fout, nx, ny, st, c, lattice_part(c), blockIdx.x * kTileX, blockIdx.y * kTileY,
-                                rs, NoHook(), rnd);
+  __shared__ __align__(16) typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
+  constexpr bool XP = xpairs<store_t>() && Lanes<V>::n == 2;
+  step_tile<V, store_t, kTileY, NoHook, XP>(fin, fout, nx, ny, st, c, lattice_part(c), blockIdx.x * kTileX,
+                                            blockIdx.y * kTileY, rs, NoHook(), rnd);
 }
 
 // Two-pass variant, pass 1: density plane rho_dev(x) = sum_i fbar_i(x - e_i).
@@ -256,7 +319,7 @@ __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restri
           __ldg(rpp + x), __ldg(rpp + xp), Sx, Sy);
   real o[9];
   collide(c, f, Sx, Sy, o);
-  store9(fout + st.at(0, x, y), st.ps, o, unsigned(y * nx + x), rnd);
+  store9(fout + st.at(0, x, y), st.ps, o, x, y, nx, rnd);
 }
 
 }  // namespace lbm

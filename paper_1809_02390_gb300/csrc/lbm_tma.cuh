@@ -220,17 +220,37 @@ __device__ __forceinline__ void issue_window_async(float* win, const float* __re
 
 // Phase 1 of an interior tile from its staged windows: the populations of the
 // thread's two nodes (window row ly + 1, column lx + xoff - e_ix for plane i) into
-// f, the densities of tile + ring into rs.
-template <typename S>
+// f, the densities of tile + ring into rs.  XP: column pairs (NodeMap); with FP16
+// storage a population's two cells are read as 4-byte half pairs (one for e_ix =
+// 0, the two that hold it otherwise: window columns are even at the pairs).
+template <typename S, bool XP = false>
 __device__ __forceinline__ void window_tile(const S* __restrict__ win, float (&f)[kTileRows][9],
                                             float (*rs)[kTileX + 2]) {
   using W = Win<S>;
-  const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+  using M = NodeMap<kTileY, XP>;
+  if constexpr (XP && sizeof(S) == 2) {
+    static_assert(W::plane % 2 == 0 && W::cols % 2 == 0 && W::xoff % 2 == 0, "half pairs start at even columns");
+    const __half2* w2 = reinterpret_cast<const __half2*>(win);
 #pragma unroll
-  for (int k = 0; k < kTileRows; ++k) {
-    const int ly = ty + k * kRowStride;
+    for (int i = 0; i < 9; ++i) {
+      const int e = ex_of(i);
+      const int h = (i * W::plane + (M::ly(0) + 1) * W::cols + M::lx(0) + W::xoff) / 2;  // cells lx, lx + 1 at e = 0
+      if (e == 0) {
+        const __half2 v = w2[h];
+        f[0][i] = __low2float(v);
+        f[1][i] = __high2float(v);
+      } else {
+        const __half2 u = w2[h - (e > 0 ? 1 : 0)], v = w2[h + (e > 0 ? 0 : 1)];
+        f[0][i] = __high2float(u);
+        f[1][i] = __low2float(v);
+      }
+    }
+  } else {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[k][i] = W::get(win[i * W::plane + (ly + 1) * W::cols + tx + W::xoff - ex_of(i)]);
+    for (int k = 0; k < kTileRows; ++k)
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        f[k][i] = W::get(win[i * W::plane + (M::ly(k) + 1) * W::cols + M::lx(k) + W::xoff - ex_of(i)]);
   }
   // Both densities as one packed sum (lane k = node k; the same additions in the
   // same order as the scalar sum).
@@ -238,8 +258,8 @@ __device__ __forceinline__ void window_tile(const S* __restrict__ win, float (&f
 #pragma unroll
   for (int i = 0; i < 9; ++i) d[i].v = make_float2(f[0][i], f[1][i]);
   const f2 rho = sum9(d);
-  rs[ty + 1][tx + 1] = rho.v.x;
-  rs[ty + kRowStride + 1][tx + 1] = rho.v.y;
+  rs[M::ly(0) + 1][M::lx(0) + 1] = rho.v.x;
+  rs[M::ly(1) + 1][M::lx(1) + 1] = rho.v.y;
   if (threadIdx.x < TileShape<kTileY>::ring) {
     int wx, wy;
     ring_cell(threadIdx.x, wx, wy);
@@ -297,7 +317,8 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   using real = float;
   extern __shared__ __align__(128) unsigned char dyn[];
   S* win = reinterpret_cast<S*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
-  __shared__ real rs[2][kTileY + 2][kTileX + 2];
+  constexpr bool XP = xpairs<S>();
+  __shared__ __align__(16) real rs[2][kTileY + 2][kTileX + 2];
   __shared__ __align__(8) unsigned long long bar;
   const int tiles_x = (nx + kTileX - 1) / kTileX;
   const int total = tiles_x * ((ny + kTileY - 1) / kTileY);
@@ -344,9 +365,9 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       __syncthreads();
     }
     if (kind == kPlainLoad)
-      load_tile<real, S, kTileY>(fin, nx, ny, st, x0, y0, f, rs[buf]);
+      load_tile<real, S, kTileY, XP>(fin, nx, ny, st, x0, y0, f, rs[buf]);
     else  // read even after a failed wait (in bounds; the block then returns)
-      window_tile(win, f, rs[buf]);
+      window_tile<S, XP>(win, f, rs[buf]);
     // The window is consumed and the densities are in place.  A wait that gave up
     // (uniform decision through the barrier) ends the block: it records the
     // failure, waits once more (bounded) for the copies it issued, and returns.
@@ -359,7 +380,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     }
     advance(tc, tr);
     if (t + gridDim.x < total) issue(tc, tr);
-    collide_tile<V, S, kTileY>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[buf], rnd);
+    collide_tile<V, S, kTileY, XP>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[buf], rnd);
     buf ^= 1;
   }
 }
@@ -397,7 +418,8 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
   static_assert(Win2<S>::buffer % 128 == 0, "window buffers start on 128-byte boundaries");
   extern __shared__ __align__(128) unsigned char dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
-  __shared__ real rs[2][kTileY + 2][kTileX + 2];
+  constexpr bool XP = xpairs<S>();
+  __shared__ __align__(16) real rs[2][kTileY + 2][kTileX + 2];
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ int tq[2];   // tile staged in each window buffer (>= total: none)
   __shared__ int2 tp[2];  // its origin (x0, y0), written by the issuer with tq
@@ -456,9 +478,9 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       ph ^= 1u << slot;
     }
     if (kind == kPlainLoad)
-      load_tile<real, S, kTileY>(fin, nx, ny, st, x0, y0, f, rs[slot]);
+      load_tile<real, S, kTileY, XP>(fin, nx, ny, st, x0, y0, f, rs[slot]);
     else  // read even after a failed wait (in bounds; the block then stops)
-      window_tile(win(slot), f, rs[slot]);
+      window_tile<S, XP>(win(slot), f, rs[slot]);
     if (__syncthreads_or(late)) {
       if (threadIdx.x == kIssuer) {
         atomicExch(err, 1);
@@ -475,7 +497,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
       issue(pending, tp[slot], slot);
       pending = draw();
     }
-    collide_tile<V, S, kTileY>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[slot], rnd);
+    collide_tile<V, S, kTileY, XP>(f, fout, nx, ny, st, c, lattice_part(c), x0, y0, rs[slot], rnd);
   }
   if (threadIdx.x == kIssuer) {
     __threadfence();

@@ -35,7 +35,7 @@ def test_flat_interface_densities_against_the_oracle(orc, Tr):
     nodes; the GPU runs the same profile on 128 x 64 nodes (rows layout, so the
     FP32 and FP16 steps take the tensor-copy kernel of the benchmark): the problem
     does not depend on y, so every FP32 row is the same and must match the
-    oracle's; FP16 stores round stochastically with a dither keyed by the node,
+    oracle's; FP16 stores round stochastically with random bits keyed by the node,
     so its rows differ and their means are compared."""
     from paper_1809_02390_gb300 import Lattice
 

@@ -1,8 +1,9 @@
 """The rows layout f[ny][9][nx] against the oracle and against the planes layout.
 
 Both layouts run the same arithmetic on every node (only the addresses of the
-loads and stores differ, and the stochastic-rounding dither of FP16 stores is keyed
-by the node index, not the address), so after any number of steps the two states
+loads and stores differ, and the random words of the FP16 stores' stochastic
+rounding are keyed by the node's coordinates, not the address), so after any
+number of steps the two states
 agree bit for bit, and so do the densities, pressures and reductions computed from
 them.  The FP64 rows path is also checked against the oracle directly."""
 import numpy as np

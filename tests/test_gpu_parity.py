@@ -283,6 +283,38 @@ def test_fp16_stochastic_rounding_keeps_mass():
     assert drift["nearest"] > 2 * drift["stochastic"]
 
 
+@pytest.mark.parametrize("layout", ["rows", "planes"])
+def test_fp16_pair_and_single_node_stores_round_alike(layout):
+    """FP16 stores round with random words drawn per pair of x-neighbours: the fused
+    step writes each pair with one packed conversion, the two-pass step one node at
+    a time, taking the pair's word and its half of it.  One step of each from the
+    same state (160 x 96: tensor-copy tiles, wrapping tiles, both nodes of every
+    pair) gives the same halves, except where the two steps' FP32 arithmetic
+    already differs in the last bit (about 0.3% of the values) and that difference
+    crosses a rounding boundary (chance about 2^-13 each); random words used
+    inconsistently would change about half of all halves."""
+    from paper_1809_02390_gb300 import capi
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    rho0 = inputs.droplet(160, 96, 30, 5, p.rho_g, p.rho_l, center=(70.3, 50.6))
+    a = lattice(rho0, "fp16s", "fused", layout=layout, Tr=0.85, K_int=1.0)
+    b = lattice(rho0, "fp16s", "two_pass", layout=layout, Tr=0.85, K_int=1.0)
+    assert capi.lb_uses_tma(a.h) and not capi.lb_uses_tma(b.h)
+    for lat in (a, b):
+        lat.step(1)
+    torch.cuda.synchronize()
+    def ordered(lat):  # halves as integers in value order (sign-magnitude to two's complement; -0 = +0)
+        h = lat.state().view(torch.int16).to(torch.int32)
+        return torch.where(h < 0, -(h & 0x7FFF), h)
+
+    diff = (ordered(a) - ordered(b)).abs()
+    assert int((diff != 0).sum()) <= 20
+    assert int(diff.max()) <= 1
+    for lat in (a, b):
+        capi.lb_status(lat.h)
+        lat.close()
+
+
 def test_bounded_wait_gives_up_and_is_reported(orc):
     """A wait that nothing completes (lb_wait_selftest) ends after its poll budget,
     is reported as LB_ETIMEOUT once (the flag is then clear), and the context stays
