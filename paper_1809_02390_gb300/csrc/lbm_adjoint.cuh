@@ -5,8 +5,9 @@
 // post-streaming populations of the node, S = sum_i omega_i rho(x + e_i) e_i the
 // force stencil (Eq. 12), theta = (R T, G^2/c^2, K_EOS/c^2).  Given the cotangent
 // ob of o, collide_vjp returns the cotangents of d, of S and of theta.  The
-// forward values are recomputed here (in the same order as collide) and then
-// every assignment is transposed in reverse order.
+// forward values are recomputed here (the formulas of collide, grouped in the
+// paper's form: F_m in full, the storage shift in m1 and m2) and then every
+// assignment is transposed in reverse order.
 //
 // Written once for a value type V (double, float, or f2 = two FP32 nodes per
 // packed FFMA2 / FADD2 / FMUL2 instruction, as in collide); every constant comes

@@ -86,6 +86,10 @@ VCoef<V> make_vcoef(const lb_params& p, const lb_derived& d) {
   c.Q78 = bc<V>(sp / 12.0);
   c.neg_a = bc<V>(-a);
   c.h15 = bc<V>(1.5);
+  c.m3 = bc<V>(-3.0);
+  c.mhalf = bc<V>(-0.5);
+  c.two_om_eps = bc<V>(2.0 - seps);
+  c.two_om_q = bc<V>(2.0 - sq);
   c.eight = bc<V>(8.0);
   c.twenty = bc<V>(20.0);
   c.third = bc<V>(1.0 / 3.0);

@@ -188,9 +188,11 @@ struct VCoef {
   V R11, R17, R18, R71, R77, R81, R88, T1a, negT1b, X1, T7, T7b, X7, T8, X8, Q1G2, Q2G2, Q78G2;
   // literals and products of parameters with literals
   V one, mone, two, three, four, six, m6, nine, eighteen, half, m2, m4, m2rr, g15, ninth, i36, sixth, i12,
-      quarter;
-  // used by the adjoint only: -a, 1.5, 8, 20 and the S Q_m factors without G^2
-  V neg_a, h15, eight, twenty, Q1, Q2, Q78;
+      quarter, h15, m3, mhalf;
+  // 2 (1 - s_eps/2), 2 (1 - s_q/2): rows 2, 4, 6 of steps (3) and (5) in one factor
+  V two_om_eps, two_om_q;
+  // used by the adjoint only: -a, 8, 20 and the S Q_m factors without G^2
+  V neg_a, eight, twenty, Q1, Q2, Q78;
   // stencil weights omega = 1/3 (axes), 1/12 (diagonals) of Eq. 12
   V third, twelfth;
 };
@@ -238,17 +240,23 @@ __device__ __forceinline__ void eos(const VCoef<V>& c, V rho, V& pe, V& dpe) {
 // One node (or a pair of nodes for V = f2).  d: post-streaming populations
 // stored as deviations f_i - w_i rho_ref; (Sx, Sy) = sum_i omega_i rho(x + e_i) e_i
 // (Eq. 12, = grad rho of supplement Eq. 61); o: post-collision deviations.
+// The sequence is the paper's; its terms are grouped to share products (the
+// halves of F_m enter G directly, ux Sy and uy Sx serve the forcing and the
+// corrections, rho u is taken from Eq. 5 before the division by rho).
 template <typename V>
 __device__ __forceinline__ void collide(const VCoef<V>& c, const LatCoef<V>& l, const V (&d)[9], V Sx, V Sy,
                                         V (&o)[9]) {
-  // Moment transform (supplement Eq. 4) with shared sums; M w = (1, -2, 1, 0, ...).
+  // Moment transform (supplement Eq. 4) with shared sums.  M w = (1, -2, 1, 0, ...):
+  // the energy moments are carried as e + 2 rho_ref and eps - rho_ref (the moments
+  // of the stored deviations) and their equilibria shifted alike, so that the
+  // shift cancels in m - m_eq and in the inverse transform of mbar - rho_ref M w.
   const V a13 = d[1] + d[3], a24 = d[2] + d[4], a57 = d[5] + d[7], a68 = d[6] + d[8];
   const V s13 = d[1] - d[3], s24 = d[2] - d[4], s57 = d[5] - d[7], s68 = d[6] - d[8];
   const V axis = a13 + a24, diag = a57 + a68;
   const V rho_dev = d[0] + (axis + diag);
   const V rho = rho_dev + l.rho_ref;
-  const V m1 = fmav(c.m4, d[0], fmav(c.two, diag, l.m2rr) - axis);       // -4 d0 - axis + 2 diag - 2 rho_ref
-  const V m2 = fmav(c.four, d[0], fmav(c.m2, axis, diag + l.rho_ref));   //  4 d0 - 2 axis + diag + rho_ref
+  const V m1 = fmav(c.m4, d[0], (diag + diag) - axis);   // e + 2 rho_ref: -4 d0 - axis + 2 diag
+  const V m2 = fmav(c.four, d[0], fmav(c.m2, axis, diag));  // eps - rho_ref: 4 d0 - 2 axis + diag
   const V dm = s57 - s68, dp = s57 + s68;
   const V jx = s13 + dm, jy = s24 + dp;
   const V m4 = fmav(c.m2, s13, dm);
@@ -259,9 +267,9 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const LatCoef<V>& l, 
   // Interaction force (Eq. 12) and velocity (Eq. 5), c = 1.
   const V G2rho = l.G2 * rho;
   const V Fx = G2rho * Sx, Fy = G2rho * Sy;
+  const V Jx = fmav(c.half, Fx, jx), Jy = fmav(c.half, Fy, jy);  // rho u
   const V inv_rho = rcp(rho);
-  const V ux = fmav(c.half, Fx, jx) * inv_rho;
-  const V uy = fmav(c.half, Fy, jy) * inv_rho;
+  const V ux = Jx * inv_rho, uy = Jy * inv_rho;
 
   // Self-tuning EOS: p_LBE = p_EOS + G^2 rho^2/2 (Eq. 18) = c_s^2 (rho + eta);
   // grad p_LBE = (p_EOS' + G^2 rho) grad rho (supplement Eq. 61).
@@ -270,62 +278,65 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const LatCoef<V>& l, 
   const V eta = fmav(c.three, pe, rho * fmav(l.g15, rho, c.mone));  // 3 pe + 1.5 G2 rho^2 - rho
   const V g = G2rho + dpe;
 
-  const V x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2;
+  const V x2 = ux * ux, y2 = uy * uy, xy = ux * uy, u2 = x2 + y2, x2my2 = x2 - y2;
   const V r3u2 = c.three * rho * u2;
-  // Equilibrium (Eq. 3, alpha_1 = -1, beta_1 = 1, alpha_2 = 1), non-conserved rows.
-  const V meq1 = fmav(c.two, eta - rho, r3u2);
-  const V meq2 = fmav(c.nine * rho * x2, y2, fmav(c.beta2, eta, rho) - r3u2);
-  const V meq4 = rho * ux * fmav(c.three, y2, c.mone);   // rho ux (3 uy^2 - 1)
-  const V meq6 = rho * uy * fmav(c.three, x2, c.mone);   // rho uy (3 ux^2 - 1)
-  const V meq7 = rho * (x2 - y2);
+  // Equilibrium (Eq. 3, alpha_1 = -1, beta_1 = 1, alpha_2 = 1), non-conserved rows
+  // (rows 1 and 2 shifted by 2 rho_ref and -rho_ref, as m1 and m2).
+  const V meq1 = fmav(c.two, eta - rho_dev, r3u2);
+  const V meq2 = fmav(c.nine * rho * x2, y2, fmav(c.beta2, eta, rho_dev) - r3u2);
+  const V meq4 = Jx * fmav(c.three, y2, c.mone);  // rho ux (3 uy^2 - 1)
+  const V meq6 = Jy * fmav(c.three, x2, c.mone);  // rho uy (3 ux^2 - 1)
+  const V meq7 = rho * x2my2;
   const V meq8 = rho * xy;
-  // Forcing (Eq. 4), brackets summed over the force's positions.
-  const V Fu = fmav(Fx, ux, Fy * uy);
-  const V Fc = fmav(Fx, uy, Fy * ux);                                    // Fx uy + Fy ux
-  const V Fm1 = c.six * Fu;
-  const V Fm2 = fmav(c.eighteen * xy, Fc, c.m6 * Fu);                    // -6 Fu + 18 xy Fc
-  const V Fm4 = fmav(c.three, fmav(Fx, y2, (c.two * Fy) * xy), c.mone * Fx);  // -Fx + 3(Fx y2 + 2 Fy xy)
-  const V Fm6 = fmav(c.three, fmav(Fy, x2, (c.two * Fx) * xy), c.mone * Fy);  // -Fy + 3(2 Fx xy + Fy x2)
-  const V Fm7 = c.two * (Fx * ux - Fy * uy);
-  const V Fm8 = Fc;
+  // Forcing (Eq. 4), brackets summed over the force's positions, taken at half
+  // weight: F_m/2 = (0, 3 Fu, -3 Fu + 9 xy Fc, ., -Fx/2 + 3/2 (Fx y2 + 2 Fy xy), .,
+  // -Fy/2 + 3/2 (Fy x2 + 2 Fx xy), Fx ux - Fy uy, Fc/2), Fu = F.u, Fc = Fx uy + Fy ux.
+  const V uySx = uy * Sx, uxSy = ux * Sy;
+  const V uSp = uySx + uxSy, uSm = uySx - uxSy;
+  const V FyUy = Fy * uy;
+  const V Fu = fmav(Fx, ux, FyUy);
+  const V Fc = G2rho * uSp;
+  const V xy2 = xy + xy;
 
   // (1): D = m - m_eq, G = D + F_m / 2, and mbar starts as 2 m_eq - m = m_eq - D.
   const V D1 = m1 - meq1, D2 = m2 - meq2, D4 = m4 - meq4, D6 = m6 - meq6, D7 = m7 - meq7, D8 = m8 - meq8;
-  const V G1 = fmav(c.half, Fm1, D1), G2 = fmav(c.half, Fm2, D2);
-  const V G4 = fmav(c.half, Fm4, D4), G6 = fmav(c.half, Fm6, D6);
-  const V G7 = fmav(c.half, Fm7, D7), G8 = fmav(c.half, Fm8, D8);
-  // (2) off-diagonal part of S, then (3) I - diag(S)/2.
+  const V G1 = fmav(c.three, Fu, D1);
+  const V G2 = fmav(c.nine * xy, Fc, fmav(c.m3, Fu, D2));
+  const V G4 = fmav(c.h15, fmav(Fx, y2, Fy * xy2), fmav(c.mhalf, Fx, D4));
+  const V G6 = fmav(c.h15, fmav(Fy, x2, Fx * xy2), fmav(c.mhalf, Fy, D6));
+  const V G7 = fmav(Fx, ux, D7 - FyUy);
+  const V G8 = fmav(c.half, Fc, D8);
+  // (2) off-diagonal part of S, then (3) I - diag(S)/2 (rows 2, 4, 6 enter step (5)
+  // as 2 A with the factor 2 (1 - s/2) taken into one constant).
   const V uG = fmav(ux, G4, uy * G6), vG = ux * G4 - uy * G6, wG = fmav(uy, G4, ux * G6);
   const V A1 = c.om_e * fmav(c.hh_sq, uG, fmav(c.hk_seps, G2, G1));
-  const V A2 = c.om_eps * G2;
-  const V A4 = c.om_q * G4, A6 = c.om_q * G6;
   const V A7 = c.om_p * fmav(c.b_sq, vG, G7);
   const V A8 = c.om_p * fmav(c.hb_sq, wG, G8);
   // (4) cubic-velocity correction: R (I - S/2) G + T . grad rho + X . grad p_LBE
   // (supplement Eqs. 34, 37, 40), with grad p_LBE = g S.
   const V ax = x2 * ux * Sx, ay = y2 * uy * Sy;
-  const V xyS1 = xy * fmav(uy, Sx, ux * Sy), xyS7 = xy * (uy * Sx - ux * Sy);
-  const V cr1 = fmav(c.T1a, ax + ay, fmav(g, c.X1, c.negT1b) * xyS1);
-  const V cr7 = fmav(c.T7, ax - ay, fmav(g, c.X7, c.T7b) * xyS7);
-  const V cr8 = fmav(g, c.X8, c.T8) * fmav(fmav(c.two, x2, y2) * uy, Sx, fmav(c.two, y2, x2) * ux * Sy);
-  const V x2my2 = x2 - y2;
+  const V cr1 = fmav(c.T1a, ax + ay, fmav(g, c.X1, c.negT1b) * (xy * uSp));
+  const V cr7 = fmav(c.T7, ax - ay, fmav(g, c.X7, c.T7b) * (xy * uSm));
+  // (2 x2 + y2) uy Sx + (2 y2 + x2) ux Sy = u2 (uy Sx + ux Sy) + x2 uy Sx + y2 ux Sy.
+  const V cr8 = fmav(g, c.X8, c.T8) * fmav(u2, uSp, fmav(x2, uySx, y2 * uxSy));
   const V corr1 = fmav(c.R11 * u2, A1, fmav(c.R17 * x2my2, A7, fmav(c.R18 * xy, A8, cr1)));
   const V corr7 = fmav(c.R71 * x2my2, A1, fmav(c.R77 * u2, A7, cr7));
   const V corr8 = fmav(c.R81 * xy, A1, fmav(c.R88 * u2, A8, cr8));
   // (5): mbar = m_eq - D + 2 A - corrections; (6): + S Q_m with |F~|^2 = G^2 |S|^2.
   const V sxx = Sx * Sx, syy = Sy * Sy, ss = sxx + syy;
   const V mb1 = fmav(l.Q1G2, ss, fmav(c.two, A1, meq1 - D1) - corr1);
-  const V mb2 = fmav(l.Q2G2, ss, fmav(c.two, A2, meq2 - D2));
-  const V mb4 = fmav(c.two, A4, meq4 - D4);
-  const V mb6 = fmav(c.two, A6, meq6 - D6);
+  const V mb2 = fmav(l.Q2G2, ss, fmav(c.two_om_eps, G2, meq2 - D2));
+  const V mb4 = fmav(c.two_om_q, G4, meq4 - D4);
+  const V mb6 = fmav(c.two_om_q, G6, meq6 - D6);
   const V mb7 = fmav(l.Q78G2, sxx - syy, fmav(c.two, A7, meq7 - D7) - corr7);
   const V mb8 = fmav(l.Q78G2 * Sx, Sy, fmav(c.two, A8, meq8 - D8) - corr8);
 
   // Inverse transform M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4),
-  // applied to mbar - rho_ref M w (deviation storage); conserved: rho, j + F.
+  // applied to mbar - rho_ref M w (deviation storage; rows 1 and 2 are already
+  // shifted); conserved: rho, j + F.
   const V n0 = rho_dev * c.ninth;
-  const V n1 = fmav(c.two, l.rho_ref, mb1) * c.i36;
-  const V n2 = (mb2 - l.rho_ref) * c.i36;
+  const V n1 = mb1 * c.i36;
+  const V n2 = mb2 * c.i36;
   const V n3 = (jx + Fx) * c.sixth;
   const V n4 = mb4 * c.i12;
   const V n5 = (jy + Fy) * c.sixth;
