@@ -90,7 +90,11 @@ typedef struct lb_params {
   double s_q, s_e, s_eps; /* <= 0: s_q and s_e from tau_p tau_q = (k+1) tau_e tau_q = 1/12
                              (Eq. 16), s_eps = s_e; otherwise in (0, 2) */
   double s_0, s_j;        /* rates of the conserved moments (act on zero); <= 0 selects 1 */
-  double rho_ref;         /* storage shift: populations stored as fbar_i - w_i rho_ref */
+  double rho_ref;         /* storage shift: populations stored as fbar_i - w_i rho_ref
+                             (rounded to float for FP32 and FP16 storage).  NaN: the mean
+                             of the initial density, summed in FP64 on the device by
+                             lb_init / lb_batch_init (lb_get_params, lb_batch_params
+                             return the value taken); infinite values are rejected */
   int32_t layout;         /* enum lb_layout.  LB_LAYOUT_ROWS: forward step, moments, pressure,
                              reductions, batched solver (all lattices of a batch in one
                              layout); the adjoint calls take LB_LAYOUT_PLANES only
@@ -307,6 +311,8 @@ int lb_batch_row_stride(const lb_batch* b, int i);
  * ([y][x]), written asynchronously on the batch's stream. */
 int lb_batch_density(lb_batch* b, int i, void* rho);
 int lb_batch_derived(const lb_batch* b, int i, lb_derived* out);
+/* Parameters of lattice i as used (rho_ref as stored).  LB_EINVAL for a bad index. */
+int lb_batch_params(const lb_batch* b, int i, lb_params* out);
 const char* lb_batch_last_error(const lb_batch* b);
 void lb_batch_free(lb_batch* b);
 
@@ -373,6 +379,10 @@ int lb_set_step_blocks(lb_handle* h, int blocks);
 
 /* Derived parameters in use by the handle. */
 int lb_get_derived(const lb_handle* h, lb_derived* out);
+
+/* The handle's parameters as used (rho_ref as stored: the mean initial density
+ * when lb_init was given NaN).  LB_EINVAL for null arguments. */
+int lb_get_params(const lb_handle* h, lb_params* out);
 
 /* Message of the last error on this handle (h = NULL: of the last failed
  * lb_derive / lb_init on this thread).  Never NULL. */

@@ -69,9 +69,9 @@ class Lattice:
             on_device = rho_t.is_cuda
             if not on_device:
                 rho_t = rho_t.pin_memory()
-        if rho_ref is None:
-            rho_ref = 0.0 if precision == "fp64" else float(rho_t.double().mean())
-        if precision != "fp64":
+        if rho_ref is None:  # FP32 / FP16: NaN asks lb_init for the mean initial density
+            rho_ref = 0.0 if precision == "fp64" else float("nan")
+        elif precision != "fp64":
             rho_ref = float(np.float32(rho_ref))  # the library stores the shift in float
         self.p = params(nx, ny, precision=precision, eos=eos, variant=variant, rho_ref=rho_ref, layout=layout,
                         **kw)
@@ -89,6 +89,8 @@ class Lattice:
         self._rho0_keep = rho_t
         self.h = capi.lb_init(self.p, self.f_a.data_ptr(), self.f_b.data_ptr(), self.scratch.data_ptr(), nscr,
                               rho_t.data_ptr(), on_device, self.stream.cuda_stream)
+        self.p = capi.lb_get_params(self.h)
+        self.rho_ref = self.p.rho_ref
         self.derived = capi.lb_get_derived(self.h)
 
     def step(self, nsteps: int = 1) -> None:
@@ -179,9 +181,11 @@ class Batch:
         self.n = n
         self.shapes = [np.asarray(r).shape for r in rho0s]
         self.layout = kws[0].get("layout", "planes")
-        self.rho_refs = [float(np.float32(kw.pop("rho_ref", float(np.mean(r))))) for r, kw in zip(rho0s, kws)]
+        kws = [dict(kw) for kw in kws]
+        # No rho_ref: NaN asks lb_batch_init for the lattice's mean initial density.
+        refs = [float(np.float32(kw.pop("rho_ref"))) if "rho_ref" in kw else float("nan") for kw in kws]
         ps = (capi.lb_params * n)(*[params(s[1], s[0], precision="fp32", rho_ref=rr, **kw)
-                                    for s, rr, kw in zip(self.shapes, self.rho_refs, kws)])
+                                    for s, rr, kw in zip(self.shapes, refs, kws)])
         self._ps = ps
         self.stream = stream if stream is not None else torch.cuda.Stream()
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -194,6 +198,7 @@ class Batch:
         torch.cuda.current_stream().synchronize()
         self.b = capi.lb_batch_init(ps, self.pool_a.data_ptr(), self.pool_b.data_ptr(), self.meta.data_ptr(), mb,
                                     self._rho_host.data_ptr(), False, self.stream.cuda_stream)
+        self.rho_refs = [capi.lb_batch_params(self.b, i).rho_ref for i in range(n)]
 
     def run(self, nsteps: int) -> None:
         capi.lb_batch_run(self.b, nsteps)

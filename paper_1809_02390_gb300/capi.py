@@ -84,11 +84,13 @@ SIGNATURES = [
     ("lb_batch_set_config", ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int]),
     ("lb_batch_status", ctypes.c_int, [_V]),
     ("lb_batch_derived", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(lb_derived)]),
+    ("lb_batch_params", ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(lb_params)]),
     ("lb_batch_last_error", ctypes.c_char_p, [_V]),
     ("lb_batch_free", None, [_V]),
     ("lb_get_state", ctypes.c_int, [_V, _V]),
     ("lb_set_state", ctypes.c_int, [_V, _V]),
     ("lb_get_derived", ctypes.c_int, [_V, ctypes.POINTER(lb_derived)]),
+    ("lb_get_params", ctypes.c_int, [_V, ctypes.POINTER(lb_params)]),
     ("lb_status", ctypes.c_int, [_V]),
     ("lb_wait_selftest", ctypes.c_int, [_V, ctypes.c_longlong]),
     ("lb_stream_copy", ctypes.c_int, [_V]),
@@ -225,6 +227,12 @@ def lb_get_derived(h: int) -> dict:
     return d.as_dict()
 
 
+def lb_get_params(h: int) -> lb_params:
+    p = lb_params()
+    check(lib().lb_get_params(h, ctypes.byref(p)), h)
+    return p
+
+
 def check_batch(rc: int, b=None) -> int:
     if rc != LB_OK:
         msg = lib().lb_batch_last_error(b)
@@ -306,6 +314,12 @@ def lb_batch_derived(b: int, i: int) -> dict:
     d = lb_derived()
     check_batch(lib().lb_batch_derived(b, i, ctypes.byref(d)), b)
     return d.as_dict()
+
+
+def lb_batch_params(b: int, i: int) -> lb_params:
+    p = lb_params()
+    check_batch(lib().lb_batch_params(b, i, ctypes.byref(p)), b)
+    return p
 
 
 def lb_batch_free(b: int) -> None:

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -536,6 +537,39 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
     delete b;
     return code;
   };
+  // rho_ref = NaN: that lattice's storage shift is its mean initial density (as in
+  // lb_init), from the densities staged in pool_b, block sums in pool_a.
+  std::vector<double> mean(n, 0.0);
+  bool staged = false;
+  {
+    bool any = false;
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+      if (ps[i].nx < 1 || ps[i].ny < 1) return bail(LB_EINVAL, "lb_batch_init: lattice sides must be positive");
+      total += size_t(ps[i].nx) * ps[i].ny;
+      any = any || std::isnan(ps[i].rho_ref);
+    }
+    if (any) {
+      cudaError_t e = cudaSuccess;
+      const double* x = rho0;
+      if (!rho0_on_device) {
+        e = cudaMemcpyAsync(pool_b, rho0, total * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+        x = static_cast<const double*>(pool_b);
+        staged = true;
+      }
+      size_t at = 0;
+      for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const size_t N = size_t(ps[i].nx) * ps[i].ny;
+        if (std::isnan(ps[i].rho_ref)) e = device_mean(x + at, N, pool_a, lb_batch_pool_bytes(ps, n), b->stream, &mean[i]);
+        at += N;
+      }
+      if (e != cudaSuccess) {
+        char msg[512];
+        std::snprintf(msg, sizeof(msg), "lb_batch_init: mean initial density: %s", cudaGetErrorString(e));
+        return bail(LB_ECUDA, msg);
+      }
+    }
+  }
   std::vector<LatCoef<f2>> h_coef(n);
   size_t off = 0, total_nodes = 0;
   for (int i = 0; i < n; ++i) {
@@ -548,7 +582,7 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
       std::snprintf(m, sizeof(m), "lattice %d: %s", i, err);
       return bail(LB_EINVAL, m);
     }
-    b->p[i].rho_ref = double(float(ps[i].rho_ref));
+    b->p[i].rho_ref = double(float(std::isnan(ps[i].rho_ref) ? mean[i] : ps[i].rho_ref));
     const VCoef<f2> full = make_vcoef<f2>(b->p[i], b->d[i]);
     if (i == 0) b->common = full;
     // Everything but the per-lattice part must agree across the batch.
@@ -656,8 +690,8 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
   // Initial state: rest equilibrium of each lattice's density (host path staged in pool_b).
-  const double* rd = rho0;
-  if (e == cudaSuccess && !rho0_on_device) {
+  const double* rd = staged ? static_cast<const double*>(pool_b) : rho0;
+  if (e == cudaSuccess && !rho0_on_device && !staged) {
     e = cudaMemcpyAsync(pool_b, rho0, total_nodes * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     rd = static_cast<const double*>(pool_b);
   }
@@ -869,6 +903,12 @@ int lb_batch_density(lb_batch* b, int i, void* rho) {
 int lb_batch_derived(const lb_batch* b, int i, lb_derived* out) {
   if (!b || i < 0 || i >= b->n || !out) return LB_EINVAL;
   *out = b->d[i];
+  return LB_OK;
+}
+
+int lb_batch_params(const lb_batch* b, int i, lb_params* out) {
+  if (!b || i < 0 || i >= b->n || !out) return LB_EINVAL;
+  *out = b->p[i];
   return LB_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <type_traits>
+#include <vector>
 
 #include "lbm_handle.cuh"
 #include "lbm_fields.cuh"
@@ -201,6 +202,24 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 }  // namespace
 
 namespace lbm {
+
+cudaError_t device_mean(const double* x, size_t n, void* work, size_t work_bytes, cudaStream_t stream, double* mean) {
+  size_t blocks = (n + 8 * kReduceThreads - 1) / (8 * kReduceThreads);
+  if (blocks > size_t(kMaxReduceBlocks)) blocks = kMaxReduceBlocks;
+  if (blocks > work_bytes / sizeof(double)) blocks = work_bytes / sizeof(double);
+  if (blocks < 1) blocks = 1;
+  double* partial = static_cast<double*>(work);
+  k_sum_partial<<<unsigned(blocks), kReduceThreads, 0, stream>>>(x, (long long)n, partial);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double> h(blocks);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), partial, blocks * sizeof(double), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return e;
+  double sum = 0.0;
+  for (double v : h) sum += v;
+  *mean = sum / double(n);
+  return cudaSuccess;
+}
 
 // 3-D map of one FP32 (elem_bytes 4) or FP16 (2) population buffer: x (nx), y (ny,
 // row stride sx), plane (9); box of one plane window (40 x 18 floats or 48 x 18
@@ -549,6 +568,18 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
     if (e != cudaSuccess) return bail(e, "cudaMemcpyAsync(rho0)");
     rho_dev = static_cast<const double*>(f_b);
   }
+  // rho_ref = NaN: the storage shift is the mean initial density (block sums in
+  // f_a, which the initial state overwrites next), rounded to float for FP32 and
+  // FP16 storage; the coefficients that hold it are made again.
+  if (std::isnan(p->rho_ref)) {
+    double mean = 0.0;
+    e = device_mean(rho_dev, N, f_a, lb_state_bytes(p), h->stream, &mean);
+    if (e != cudaSuccess) return bail(e, "mean initial density");
+    h->p.rho_ref = p->precision != LB_FP64 ? double(float(mean)) : mean;
+    h->cf = make_vcoef<float>(h->p, d);
+    h->c2 = make_vcoef<f2>(h->p, d);
+    h->cd = make_vcoef<double>(h->p, d);
+  }
   const unsigned blocks = unsigned((N + 255) / 256);
   const double vdw_b = p->eos == LB_EOS_VDW ? p->eos_b : 0.0;
   switch (p->precision) {
@@ -767,6 +798,12 @@ int lb_set_state(lb_handle* h, const void* src) {
 int lb_get_derived(const lb_handle* h, lb_derived* out) {
   if (!h || !out) return LB_EINVAL;
   *out = h->d;
+  return LB_OK;
+}
+
+int lb_get_params(const lb_handle* h, lb_params* out) {
+  if (!h || !out) return LB_EINVAL;
+  *out = h->p;
   return LB_OK;
 }
 

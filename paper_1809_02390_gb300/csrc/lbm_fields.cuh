@@ -234,6 +234,24 @@ __global__ void __launch_bounds__(kReduceThreads)
   }
 }
 
+// Block sums of x[0 .. n) in FP64: partial[b] = the sum of block b's grid-stride
+// share (a fixed order for a given grid, so that repeated calls agree bit for bit).
+static __global__ void __launch_bounds__(kReduceThreads)
+    k_sum_partial(const double* __restrict__ x, long long n, double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    s += x[k];
+  __shared__ double sh[kReduceThreads / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = sh[0];
+    for (int j = 1; j < kReduceThreads / 32; ++j) v += sh[j];
+    partial[blockIdx.x] = v;
+  }
+}
+
 // Folds the block partials in a fixed order (deterministic) into out[kReduceSlots].
 static __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
   const int k = threadIdx.x;

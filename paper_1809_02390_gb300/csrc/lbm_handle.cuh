@@ -54,4 +54,9 @@ bool encode_plane_map(CUtensorMap* map, const void* base, int nx, int ny, int pl
 // Device address of lb_reduce_static's static scratch on the current device
 // (looked up once per device, which commits the array there; lbm_static.cu).
 int static_scratch_address(lb_handle* h, void** out);
+// Mean of the n doubles at x (device memory), summed in FP64 on `stream` with
+// block partials written to `work` (device memory of work_bytes >= 8), folded on
+// the host in a fixed order; synchronous.  cudaSuccess or the CUDA error
+// (lbm_capi.cu).
+cudaError_t device_mean(const double* x, size_t n, void* work, size_t work_bytes, cudaStream_t stream, double* mean);
 }  // namespace lbm

@@ -243,7 +243,7 @@ int derive(const lb_params* p, lb_derived* d, char* err, size_t errlen) {
   d->s_j = p->s_j > 0 ? p->s_j : 1.0;
   if (!rate_ok(d->s_q) || !rate_ok(d->s_e) || !rate_ok(d->s_eps) || !rate_ok(d->s_0) || !rate_ok(d->s_j))
     return fail("relaxation rates must lie in (0, 2)");
-  if (!std::isfinite(p->rho_ref)) return fail("rho_ref must be finite");
+  if (std::isinf(p->rho_ref)) return fail("rho_ref must be finite (or NaN: the mean initial density)");
   return LB_OK;
 }
 

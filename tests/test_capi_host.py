@@ -151,3 +151,16 @@ def test_size_limit_of_32_bit_offsets(capi):
         with pytest.raises(capi.LBError) as ei:
             capi.lb_derive(capi.make_params(nx, ny))
         assert ei.value.code == capi.LB_EINVAL and "too large" in str(ei.value)
+
+
+def test_storage_shift_nan_means_the_mean_density(capi):
+    """rho_ref = NaN asks lb_init / lb_batch_init for the mean initial density, so
+    lb_derive accepts it; an infinite shift is rejected."""
+    p = capi.make_params(64, 64)
+    p.rho_ref = float("nan")
+    assert capi.lb_derive(p)["rho_l"] > 0
+    for bad in (float("inf"), float("-inf")):
+        p.rho_ref = bad
+        with pytest.raises(capi.LBError) as ei:
+            capi.lb_derive(p)
+        assert ei.value.code == capi.LB_EINVAL and "rho_ref" in str(ei.value)

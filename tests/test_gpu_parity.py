@@ -315,6 +315,36 @@ def test_fp16_pair_and_single_node_stores_round_alike(layout):
         lat.close()
 
 
+@pytest.mark.parametrize("precision,layout,on_device", [("fp32", "rows", False), ("fp16s", "planes", False),
+                                                       ("fp32", "planes", True)])
+def test_storage_shift_defaults_to_the_mean_density(precision, layout, on_device):
+    """Without rho_ref the binding passes NaN and lb_init takes the mean initial
+    density (FP64 sum on the device, rounded to float); the lattice then steps bit
+    for bit like one given that value explicitly, and a batch takes the same value
+    for the same density."""
+    from paper_1809_02390_gb300 import Batch, capi
+
+    p = oracle_params(Tr=0.85, K_int=1.0)
+    rho0 = inputs.droplet(160, 96, 30, 5, p.rho_g, p.rho_l, center=(70.3, 50.6))
+    src = torch.from_numpy(rho0).cuda() if on_device else rho0
+    a = lattice(src, precision, layout=layout, Tr=0.85, K_int=1.0)
+    want = float(np.float32(rho0.mean()))
+    assert abs(a.rho_ref - want) <= abs(want) * 2.0 ** -23
+    assert a.rho_ref == float(np.float32(a.rho_ref))
+    b = lattice(rho0, precision, layout=layout, Tr=0.85, K_int=1.0, rho_ref=a.rho_ref)
+    for lat in (a, b):
+        lat.step(40)
+    torch.cuda.synchronize()
+    assert torch.equal(a.buffer(), b.buffer())
+    if precision == "fp32":
+        bt = Batch([rho0, rho0[:64, :80]], [dict(Tr=0.85, K_int=1.0, layout=layout)] * 2)
+        assert bt.rho_refs[0] == a.rho_ref
+        assert abs(bt.rho_refs[1] - float(np.float32(rho0[:64, :80].mean()))) <= 2.0 ** -22
+        bt.close()
+    for lat in (a, b):
+        lat.close()
+
+
 def test_bounded_wait_gives_up_and_is_reported(orc):
     """A wait that nothing completes (lb_wait_selftest) ends after its poll budget,
     is reported as LB_ETIMEOUT once (the flag is then clear), and the context stays
