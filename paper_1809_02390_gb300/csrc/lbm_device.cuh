@@ -124,17 +124,19 @@ __device__ __forceinline__ unsigned cvt_rs_f16x2(float lo, float hi, unsigned rb
 }
 
 // Random words of the FP16 stores.  The nodes (2j, y) and (2j + 1, y) of a row
-// form pair j; its words are a linear congruential sequence s_1, s_2, ... started
-// at a hash of (pair index, step seed), population i taking s_{i+1} whitened as
-// s xor (s >> 16) (the low half's bits then depend on the sequence's high bits).
-// Node 2j rounds with the low bits of the word, node 2j + 1 with the high ones,
-// whichever kernel stores it.
+// form pair j; its words are a linear congruential sequence s_1, s_2, ... (mod
+// 2^32) started at a hash of (pair index, step seed), population i taking s_{i+1}.
+// Node 2j rounds with bits 12..0 of the word, node 2j + 1 with bits 28..16,
+// whichever kernel stores it.  With a uniformly distributed start every s_i is
+// uniform, so the two disjoint bit fields are independent and uniform and each
+// rounding is unbiased; the short periods of an LCG's low bits only correlate the
+// dithers of one node's nine populations, which does not bias any of them.
 __device__ __forceinline__ unsigned sr_start(int x, int y, int nx, unsigned seed) {
   return mix32(unsigned(y * ((nx + 1) >> 1) + (x >> 1)) * 0x9e3779b9u + seed);
 }
 __device__ __forceinline__ unsigned sr_next(unsigned& s) {
   s = s * 1664525u + 1013904223u;
-  return s ^ (s >> 16);
+  return s;
 }
 
 // Stores the nine populations of node (x, y) of a lattice nx wide at p + i * plane.
@@ -282,12 +284,12 @@ __device__ __forceinline__ void collide(const VCoef<V>& c, const LatCoef<V>& l, 
   const V r3u2 = c.three * rho * u2;
   // Equilibrium (Eq. 3, alpha_1 = -1, beta_1 = 1, alpha_2 = 1), non-conserved rows
   // (rows 1 and 2 shifted by 2 rho_ref and -rho_ref, as m1 and m2).
+  const V meq8 = rho * xy;
   const V meq1 = fmav(c.two, eta - rho_dev, r3u2);
-  const V meq2 = fmav(c.nine * rho * x2, y2, fmav(c.beta2, eta, rho_dev) - r3u2);
+  const V meq2 = fmav(c.nine * meq8, xy, fmav(c.beta2, eta, rho_dev) - r3u2);  // 9 rho ux^2 uy^2 + ...
   const V meq4 = Jx * fmav(c.three, y2, c.mone);  // rho ux (3 uy^2 - 1)
   const V meq6 = Jy * fmav(c.three, x2, c.mone);  // rho uy (3 ux^2 - 1)
   const V meq7 = rho * x2my2;
-  const V meq8 = rho * xy;
   // Forcing (Eq. 4), brackets summed over the force's positions, taken at half
   // weight: F_m/2 = (0, 3 Fu, -3 Fu + 9 xy Fc, ., -Fx/2 + 3/2 (Fx y2 + 2 Fy xy), .,
   // -Fy/2 + 3/2 (Fy x2 + 2 Fx xy), Fx ux - Fy uy, Fc/2), Fu = F.u, Fc = Fx uy + Fy ux.
