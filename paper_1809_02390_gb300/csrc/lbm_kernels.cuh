@@ -89,9 +89,8 @@ struct TileShape {
 // row(t)), so that the two nodes' populations are adjacent in memory and leave as
 // one 4-byte half pair per population, and their stencils come from aligned
 // 8-byte reads of the density tile.  Warp w covers rows r and r + 2, r = 4 (w / 2)
-// + w mod 2: two window rows apart in shared memory are 48 words (FP16 windows,
-// 24 words a row) or 80 (FP32, 40), 16 banks apart, so the two half-warps' reads
-// of a window row fall in different banks.
+// + w mod 2: two rows of an FP16 window (24 words a row) are 48 words, 16 banks,
+// apart, so the two half-warps' reads of a window row fall in different banks.
 template <int TY, bool XP>
 struct NodeMap {
   static_assert(!XP || TY % 4 == 0, "column pairs take rows in groups of four");
@@ -114,8 +113,7 @@ __host__ __device__ constexpr bool xpairs() {
 
 // Phase 2 of a tile, arithmetic part: force stencil of each thread's two nodes
 // from the shared densities and the collision (one packed FP32x2 evaluation for
-// V = f2); out[k] = post-collision deviations of the thread's node in row ty + k
-// stride.
+// V = f2); out[k] = post-collision deviations of the thread's node k (NodeMap).
 template <typename V, int TY, bool XP = false>
 __device__ __forceinline__ void collide_nodes(const typename LaneType<V>::type (&f)[kTileRows][9], const VCoef<V>& c,
                                               const LatCoef<V>& l,
