@@ -155,12 +155,12 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
             size_t scratch_bytes, const double* rho0, int rho0_on_device, void* stream);
 
 /* Advances nsteps >= 0 time steps (Eq. 13 + supplement Eq. 2) on the stream.
- * Asynchronous.  For FP64 and FP32 storage, runs of 64 steps replay a CUDA graph
- * that the handle captures on first use (again after lb_set_step_blocks or
- * lb_set_tile_dispatch change the launch); the graph runs on a stream the handle
- * owns, ordered after the caller's stream's earlier work and before its later
- * work, and gives the same bits as 64 separate launches.  FP16 storage launches
- * each step (its stochastic rounding draws a new seed per step). */
+ * Asynchronous.  Runs of 64 steps replay a CUDA graph that the handle captures on
+ * first use (again after lb_set_step_blocks or lb_set_tile_dispatch change the
+ * launch); the graph runs on a stream the handle owns, ordered after the caller's
+ * stream's earlier work and before its later work, and gives the same bits as 64
+ * separate launches (FP16 stores take their per-step seed from a device word with
+ * the step count, written before each replay). */
 int lb_step(lb_handle* h, int64_t nsteps);
 
 /* Device pointer of the buffer holding the current state. */

@@ -161,8 +161,13 @@ void launch_step(lb_handle* h, const VCoef<V>& cv, const VCoef<real>& c) {
   const store_t* fin = static_cast<const store_t*>(h->f[h->cur]);
   store_t* fout = static_cast<store_t*>(h->f[1 - h->cur]);
   const int nx = h->p.nx, ny = h->p.ny;
-  // FP16 stores: a fresh dither sequence every step (seed from the step count).
-  const Rounding rnd{mix32(unsigned(h->steps) * 2654435761u + 12345u), h->p.rounding == LB_ROUND_STOCHASTIC};
+  // FP16 stores: a fresh dither sequence every step (seed from the step count; a
+  // launch captured into a graph reads the count from the handle's step word).
+  Rounding rnd{step_seed(unsigned(h->steps)), h->p.rounding == LB_ROUND_STOCHASTIC, nullptr, 0};
+  if (h->graph_k >= 0) {
+    rnd.step = h->step_word;
+    rnd.k = h->graph_k;
+  }
   if (h->variant == LB_FUSED) {
     const dim3 grd((nx + kTileX - 1) / kTileX, (ny + kTileY - 1) / kTileY);
     if constexpr (sizeof(store_t) <= 4 && std::is_same<V, f2>::value) {
@@ -284,6 +289,10 @@ namespace {
 // serves the handle on whichever device it lives (each device has its own array).
 constexpr int kWaitSlots = 4096;
 __device__ int g_wait_flags[kWaitSlots];
+// Per handle slot: the step count that the FP16 steps of a replayed graph seed from.
+__device__ unsigned g_step_words[kWaitSlots];
+
+__global__ void k_set_word(unsigned* w, unsigned v) { *w = v; }
 std::mutex g_slot_mu;
 bool g_slot_used[kWaitSlots] = {false};
 
@@ -381,6 +390,8 @@ int configure(lb_handle* h) {
   LB_CUDA(h, cudaGetSymbolAddress(&w, g_wait_flags));
   h->wait_error = static_cast<int*>(w) + h->wait_slot;
   LB_CUDA(h, cudaMemsetAsync(h->wait_error, 0, sizeof(int), h->stream));
+  LB_CUDA(h, cudaGetSymbolAddress(&w, g_step_words));
+  h->step_word = static_cast<unsigned*>(w) + h->wait_slot;
   // lb_reduce_static's array is committed now, while the caller can still spare
   // the memory, rather than at its first call.
   void* st = nullptr;
@@ -542,6 +553,7 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
   h->c2 = make_vcoef<f2>(h->p, d);
   h->cd = make_vcoef<double>(h->p, d);
   h->wait_slot = -1;
+  h->graph_k = -1;
   rc = configure(h);
   if (rc != LB_OK) {
     set_thread_error(h->err);
@@ -658,11 +670,13 @@ bool ensure_step_graph(lb_handle* h) {
   cudaError_t e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int s = 0; s < kStepGraph; ++s) {
+      h->graph_k = s;
       launch_one_step(h);
       h->cur = 1 - h->cur;
     }
     e = cudaStreamEndCapture(h->gstream, &g);
   }
+  h->graph_k = -1;
   h->stream = caller;
   h->cur = from;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[from], g, 0);
@@ -685,9 +699,10 @@ int lb_step(lb_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, LB_EINVAL, "nsteps must be >= 0");
   // Runs of kStepGraph steps replay a captured graph on the handle's internal
   // stream, ordered after the caller's stream's earlier work and before its later
-  // work by two events.  FP16 storage launches every step directly: its stochastic
-  // rounding takes a new seed per step.
-  if (nsteps >= kStepGraph && h->p.precision != LB_FP16S && !h->graph_off) {
+  // work by two events.  FP16 stores seed from the step count: before each replay
+  // a one-thread launch writes it to the handle's step word, which the graph's
+  // steps read (step k of the graph adds k).
+  if (nsteps >= kStepGraph && !h->graph_off) {
     if (!ensure_step_graph(h)) {
       h->graph_off = true;
     } else {
@@ -695,6 +710,10 @@ int lb_step(lb_handle* h, int64_t nsteps) {
       LB_CUDA(h, cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
       while (nsteps >= kStepGraph) {
         if (!ensure_step_graph(h)) return fail(h, LB_ECUDA, "step graph capture failed");
+        if (h->p.precision == LB_FP16S) {
+          k_set_word<<<1, 1, 0, h->gstream>>>(h->step_word, unsigned(h->steps));
+          LB_CUDA(h, cudaGetLastError());
+        }
         LB_CUDA(h, cudaGraphLaunch(h->graph[h->cur], h->gstream));
         h->steps += kStepGraph;
         nsteps -= kStepGraph;

@@ -105,11 +105,23 @@ __host__ __device__ __forceinline__ unsigned mix32(unsigned x) {
   return x;
 }
 
-// Rounding of FP16 stores: stochastic with per-step seed, or nearest.
+// Rounding of FP16 stores: stochastic with a per-step seed, or nearest.  A launch
+// that a graph replays reads the step count from device memory (*step + k, k its
+// place in the graph); a direct launch carries the seed itself.
 struct Rounding {
   unsigned seed;
   int stochastic;
+  const unsigned* step;
+  int k;
 };
+
+// Seed of the FP16 stores of time step n.
+__host__ __device__ __forceinline__ unsigned step_seed(unsigned n) { return mix32(n * 2654435761u + 12345u); }
+
+__device__ __forceinline__ Rounding resolve(Rounding r) {
+  if (r.step) r.seed = step_seed(*r.step + unsigned(r.k));
+  return r;
+}
 
 // FP32 -> FP16 pair with stochastic rounding (Blackwell's cvt.rs.f16x2.f32): each
 // value is rounded toward zero after 13 random bits are added below the half's

@@ -35,6 +35,8 @@ struct lb_handle {
   cudaGraphExec_t graph[2];
   long long graph_cfg[2];
   bool graph_off;         // capture failed once: direct launches only
+  unsigned* step_word;    // device word with the step count a replayed FP16 graph seeds from
+  int graph_k;            // while capturing: the place of the launch in the graph (else -1)
   lbm::VCoef<float> cf;  // FP32 scalar (two-pass variant, moments)
   lbm::VCoef<lbm::f2> c2;     // FP32 pairs (fused variant)
   lbm::VCoef<double> cd;

@@ -282,6 +282,7 @@ template <typename V, typename store_t>
 __global__ void __launch_bounds__(kFusedThreads, fused_min_blocks<V>())
     k_step_fused(const store_t* __restrict__ fin, store_t* __restrict__ fout, int nx, int ny, Strides st,
                  VCoef<V> c, Rounding rnd) {
+  rnd = resolve(rnd);
   __shared__ __align__(16) typename LaneType<V>::type rs[kTileY + 2][kTileX + 2];
   constexpr bool XP = xpairs<store_t>() && Lanes<V>::n == 2;
   step_tile<V, store_t, kTileY, NoHook, XP>(fin, fout, nx, ny, st, c, lattice_part(c), blockIdx.x * kTileX,
@@ -303,6 +304,7 @@ template <typename real, typename store_t>
 __global__ void k_collide_rho(const store_t* __restrict__ fin, store_t* __restrict__ fout,
                               const real* __restrict__ rho, int nx, int ny, Strides st, VCoef<real> c,
                               Rounding rnd) {
+  rnd = resolve(rnd);
   const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
   const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;

@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     k_step_tma(const __grid_constant__ CUtensorMap tin, const S* __restrict__ fin, S* __restrict__ fout, int nx,
                int ny, Strides st, VCoef<V> c, int* __restrict__ err, Rounding rnd) {
   static_assert(!ASYNC_EDGES || sizeof(S) == 4, "asynchronous edge windows exist for FP32 storage only");
+  rnd = resolve(rnd);
   using real = float;
   extern __shared__ __align__(128) unsigned char dyn[];
   S* win = reinterpret_cast<S*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(kFusedThreads, kTmaMinBlocks)
     k_step_tma_dyn(const __grid_constant__ CUtensorMap tin, const S* __restrict__ fin, S* __restrict__ fout, int nx,
                    int ny, Strides st, VCoef<V> c, int* __restrict__ err, Rounding rnd, unsigned* __restrict__ queue) {
   using real = float;
+  rnd = resolve(rnd);
   static_assert(Win2<S>::buffer % 128 == 0, "window buffers start on 128-byte boundaries");
   extern __shared__ __align__(128) unsigned char dyn[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn) + 127) & ~uintptr_t(127));

@@ -99,12 +99,14 @@ def test_dispatch_not_available_without_tensor_copies():
                                                             ("fp32", "fused", "planes", (70, 45)),
                                                             ("fp64", "fused", "planes", (64, 64)),
                                                             ("fp32", "two_pass", "planes", (64, 48)),
-                                                            ("fp16s", "fused", "rows", (160, 96))])
+                                                            ("fp16s", "fused", "rows", (160, 96)),
+                                                            ("fp16s", "two_pass", "planes", (64, 48))])
 def test_graph_replayed_steps_equal_direct_launches(precision, variant, layout, shape):
     """lb_step replays runs of 64 steps from a captured graph on the handle's own
-    stream (FP16 storage excepted: its rounding seed changes every step); the result
-    is bit-identical to launching the steps one call at a time, including after the
-    launch configuration changes (the graph is captured again)."""
+    stream (FP16 stores seed from the step count, which the replayed steps read from
+    a device word set before each replay); the result is bit-identical to launching
+    the steps one call at a time, including after the launch configuration changes
+    (the graph is captured again)."""
     from paper_1809_02390_gb300 import Lattice, capi, derive
 
     nx, ny = shape
