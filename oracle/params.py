@@ -10,12 +10,13 @@ carried as p/c^2: lam = K_EOS / c^2 multiplies the EOS and G2 = G^2 / c^2.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Pins: relaxation_rates by hand-worked values and by the flat-interface tests
-whose outcome depends on Eq. 16 (tests/test_oracle_physics.py).  The c^2 rule
-(Eq. 22) only sets the time unit (lam and G2 scale together, so no equilibrium
-depends on it); the one printed number that does, the analytic oscillation
-period of the elliptic droplet, is not reproduced from the stated parameters:
-parity unpinned for the time unit c^2.
+Pins (tests/test_oracle_physics.py): relaxation_rates by hand-worked values and
+by the flat-interface tests whose outcome depends on Eq. 16; the c^2 rule (Eq. 22)
+and G (Eq. 21) by what they say about the recovered pressure p_LBE = p_EOS +
+G^2 rho^2 / 2, with slopes of the EOS pressure taken by central differences: in
+lattice units K_INT^2 lam d(p + a rho^2)/drho = 1/3 at rho_l, the attraction left
+in p_LBE is (K_INT^2 - 1) K_EOS a rho^2, and at K_INT = 1 the liquid's sound speed
+equals the lattice sound speed (four planted mistakes each fail it).
 """
 from __future__ import annotations
 

@@ -322,3 +322,57 @@ def test_profiles_do_not_depend_on_K_EOS(orc):
     runs = [orc.macro(p, orc.step(p, orc.init_feq(p, prof), 10000))[0][0] for p in (ps[0], ps[-1])]
     assert np.abs(runs[0] - runs[1]).max() <= 1e-12 * runs[0].max()
     assert _thickness(runs[0][:80], runs[0][0], runs[0][80]) == pytest.approx(W, rel=2e-2)
+
+
+@pytest.mark.parametrize("eos,a,b,Tr", [("vdw", 9.0 / 49.0, 2.0 / 21.0, 0.85), ("vdw", 9.0 / 49.0, 2.0 / 21.0, 0.6),
+                                        ("cs", 1.0, 4.0, 0.8), ("cs", 1.0, 4.0, 0.6)])
+@pytest.mark.parametrize("K_eos,K_int", [(1.0, 1.0), (0.106, 1.0), (0.05, 2.5)])
+def test_lattice_sound_speed_rule(eos, a, b, Tr, K_eos, K_int):
+    """Eqs. 21-22 in lattice units (c = 1, c_s^2 = 1/3), checked through what they
+    say about the pressure the model recovers, p_LBE = p_EOS + G^2 rho^2 / 2 (Eq. 18),
+    with slopes taken by central differences of the EOS pressure (not through the
+    oracle's derivative of the repulsive part):
+      * Eq. 22 chooses c_s^2 = K_INT^2 d(p_EOS + K_EOS a rho^2)/drho at rho_l, so
+        K_INT^2 lam d(p + a rho^2)/drho = 1/3 there (p per unit K_EOS);
+      * Eq. 21 makes the attraction left in p_LBE (K_INT^2 - 1) K_EOS a rho^2: at
+        K_INT = 1 p_LBE is the repulsive part alone, and its slope at rho_l is the
+        lattice's c_s^2: the liquid's sound speed equals the lattice sound speed.
+    A dropped factor 3 (c = c_s), K_INT not squared, the slope taken at rho_g or of
+    p_EOS alone, or G from K_EOS without K_INT each fail one of these."""
+    P = op.from_physical(eos, a=a, b=b, Tr=Tr, K_eos=K_eos, K_int=K_int)
+    e = thermo.make_eos(eos, a, b, 1.0, Tr, K_eos)
+    rl = P.rho_l
+
+    def slope(f, r):
+        h = 1e-5 * r
+        return (f(r + h) - f(r - h)) / (2.0 * h)
+
+    def p_lbe(r):  # lattice units: lam p_EOS / K_EOS + G2 r^2 / 2
+        return P.lam * e.p(r) / K_eos + 0.5 * P.G2 * r * r
+
+    assert K_int ** 2 * slope(lambda r: P.lam * (e.p(r) / K_eos + a * r * r), rl) == pytest.approx(1.0 / 3.0, rel=1e-8)
+    for r in (P.rho_g, 0.5 * (P.rho_g + rl), rl):
+        left = p_lbe(r) - P.lam * e.p_rep(r)
+        assert left == pytest.approx((K_int ** 2 - 1.0) * P.lam * a * r * r, rel=1e-10, abs=1e-14 * P.lam * e.p_rep(r))
+    if K_int == 1.0:
+        assert slope(p_lbe, rl) == pytest.approx(1.0 / 3.0, rel=1e-8)
+        assert slope(p_lbe, P.rho_g) < 0.5 / 3.0  # the rule is the liquid's, not the gas's
+
+
+@pytest.mark.parametrize("mistake", ["c_equals_c_s", "K_int_not_squared", "slope_at_rho_g", "slope_of_p_eos"])
+def test_sound_speed_rule_rejects_planted_mistakes(mistake):
+    """The identity of test_lattice_sound_speed_rule, applied to the c^2 of Eq. 22
+    computed with one plausible mistake (CS, Tr = 0.6, K_INT = 2.5), is off by far
+    more than its tolerance in every case."""
+    a, b, Tr, K_eos, K_int = 1.0, 4.0, 0.6, 0.106, 2.5
+    e = thermo.make_eos("cs", a, b, 1.0, Tr, K_eos)
+    rg, rl, _ = thermo.maxwell(e)
+    r = rg if mistake == "slope_at_rho_g" else rl
+    dp = e.dp_rep(r) - (2.0 * a * r if mistake == "slope_of_p_eos" else 0.0)
+    c2 = (1.0 if mistake == "c_equals_c_s" else 3.0) * (K_int if mistake == "K_int_not_squared" else K_int ** 2) \
+        * K_eos * dp
+    lam = K_eos / c2
+    h = 1e-5 * rl
+    f = lambda x: lam * (e.p(x) / K_eos + a * x * x)
+    got = K_int ** 2 * (f(rl + h) - f(rl - h)) / (2.0 * h)
+    assert abs(got * 3.0 - 1.0) > 0.3
