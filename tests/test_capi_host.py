@@ -164,3 +164,17 @@ def test_storage_shift_nan_means_the_mean_density(capi):
         with pytest.raises(capi.LBError) as ei:
             capi.lb_derive(p)
         assert ei.value.code == capi.LB_EINVAL and "rho_ref" in str(ei.value)
+
+
+def test_null_and_empty_arguments_are_rejected_without_a_gpu(capi):
+    """Calls on a null handle or an empty batch return LB_EINVAL before any CUDA
+    work: lb_step, lb_moments, lb_reduce, lb_batch_init with n = 0."""
+    lib = capi.lib()
+    assert lib.lb_step(None, 1) == capi.LB_EINVAL
+    assert lib.lb_step(None, -1) == capi.LB_EINVAL
+    out = (ctypes.c_double * 8)()
+    assert lib.lb_reduce(None, out) == capi.LB_EINVAL
+    b = ctypes.c_void_p()
+    ps = (capi.lb_params * 1)(capi.make_params(8, 8))
+    rc = lib.lb_batch_init(ctypes.byref(b), ps, 0, 1 << 40, 2 << 40, 3 << 40, 1 << 20, None, 0, None)
+    assert rc == capi.LB_EINVAL and not b.value

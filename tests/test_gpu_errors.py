@@ -105,3 +105,33 @@ def test_wait_give_up_is_reported_on_its_own_handle():
     assert torch.equal(a.buffer(), b.buffer())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_zero_steps_change_nothing_and_negative_counts_are_rejected(precision):
+    """lb_step(h, 0) and lb_batch_run(b, 0) leave the state and the step count as
+    they are; a negative count is LB_EINVAL and launches nothing."""
+    from paper_1809_02390_gb300 import Batch, Lattice, capi, derive
+
+    d = derive(96, 64, Tr=0.85)
+    rho0 = inputs.droplet(96, 64, 16, 5, d["rho_g"], d["rho_l"])
+    lat = Lattice(rho0, precision=precision, Tr=0.85)
+    lat.step(3)
+    torch.cuda.synchronize()
+    before = lat.buffer().clone()
+    lat.step(0)
+    with pytest.raises(capi.LBError) as ei:
+        lat.step(-1)
+    assert ei.value.code == capi.LB_EINVAL
+    torch.cuda.synchronize()
+    assert torch.equal(lat.buffer(), before) and lat.steps_done == 3
+    lat.close()
+    if precision == "fp32":
+        b = Batch([rho0, rho0[:40, :50]], [dict(Tr=0.85)] * 2)
+        b.run(2)
+        s0 = b.state(1).clone()
+        b.run(0)
+        with pytest.raises(capi.LBError):
+            b.run(-5)
+        assert torch.equal(b.state(1), s0) and b.steps_done == 2
+        b.close()
