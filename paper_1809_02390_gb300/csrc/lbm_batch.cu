@@ -550,6 +550,18 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
       any = any || std::isnan(ps[i].rho_ref);
     }
     if (any) {
+      // Invalid parameters never reach the GPU: check every lattice first.
+      for (int i = 0; i < n; ++i) {
+        lb_derived tmp;
+        char err[512] = {0};
+        if (ps[i].precision != LB_FP32 || ps[i].layout != ps[0].layout ||
+            derive(&ps[i], &tmp, err, sizeof(err)) != LB_OK) {
+          any = false;  // the loop below reports the error
+          break;
+        }
+      }
+    }
+    if (any) {
       cudaError_t e = cudaSuccess;
       const double* x = rho0;
       if (!rho0_on_device) {

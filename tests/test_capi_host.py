@@ -119,6 +119,25 @@ def test_batch_rejects_mixed_layouts_before_any_gpu_work(capi):
     assert rc == capi.LB_ENOTSUP and "share the layout" in capi.lb_last_error(None)
 
 
+def test_batch_with_automatic_shifts_validates_before_any_gpu_work(capi):
+    """rho_ref = NaN makes lb_batch_init sum densities on the device, but only after
+    every lattice's parameters are checked: a batch whose second lattice has no two
+    phases (Tr > 1) is refused with LB_EINVAL on the host (on a machine without a
+    GPU, any device work would have failed with LB_ECUDA instead)."""
+    import numpy as np
+
+    a = capi.make_params(64, 64)
+    bad = capi.make_params(64, 64, Tr=1.2)
+    for q in (a, bad):
+        q.rho_ref = float("nan")
+    ps = (capi.lb_params * 2)(a, bad)
+    rho = np.full(2 * 64 * 64, 2.0)
+    b = ctypes.c_void_p()
+    meta = capi.lib().lb_batch_meta_bytes(ps, 2)
+    rc = capi.lib().lb_batch_init(ctypes.byref(b), ps, 2, 1 << 40, 2 << 40, 3 << 40, meta, rho.ctypes.data, 0, None)
+    assert rc == capi.LB_EINVAL and not b.value
+
+
 def test_new_entry_points_reject_null_handles(capi):
     """The equilibrium, dispatch and tuning calls check their handle
     before any GPU work."""
