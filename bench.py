@@ -638,6 +638,25 @@ def run_ours(args):
         del lt
         torch.cuda.empty_cache()
 
+    # Carnahan-Starling EOS (Eq. 20 with the paper's a = 1, b = 4): the same spinodal
+    # recipe between its own coexistence densities, FP32 and FP64 (rows as above).
+    from paper_1809_02390_gb300 import derive as lderive, inputs as linputs
+
+    cs = dict(eos="cs", eos_a=1.0, eos_b=4.0, Tr=TR)
+    dcs = lderive(n, n, **cs)
+    rho_cs = linputs.spinodal(n, n, 0.5 * (dcs["rho_g"] + dcs["rho_l"]), 0.01, seed=rank)
+    for prec, k in (("fp32", quarter), ("fp64", 30)):
+        lt = Lattice(rho_cs, precision=prec, layout=args.layout, **cs)
+        lt.step(3)
+        m = time_steps(lt, k, torch) / k
+        variants["%s_fused_%s_carnahan_starling" % (prec, args.layout)] = {
+            "MLUPS": round(nodes / (m * 1e-3) / 1e6, 1), "ms_per_step": round(m, 4),
+            "algorithmic_GBps": round(BYTES_PER_LU[prec] * nodes / (m * 1e-3) / 1e9, 1)}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
+    del rho_cs
+
     # --- end to end through the public API with host buffers -------------------
     rho_host = torch.from_numpy(np.ascontiguousarray(rho0)).pin_memory()
     out_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
