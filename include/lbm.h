@@ -160,7 +160,8 @@ int lb_init(lb_handle** out, const lb_params* p, void* f_a, void* f_b, void* scr
  * launch); the graph runs on a stream the handle owns, ordered after the caller's
  * stream's earlier work and before its later work, and gives the same bits as 64
  * separate launches (FP16 stores take their per-step seed from a device word with
- * the step count, written before each replay). */
+ * the step count, written before each replay).  While the caller's stream is being
+ * captured into a graph of its own, every step is a plain launch on that stream. */
 int lb_step(lb_handle* h, int64_t nsteps);
 
 /* Device pointer of the buffer holding the current state. */

@@ -702,7 +702,13 @@ int lb_step(lb_handle* h, int64_t nsteps) {
   // work by two events.  FP16 stores seed from the step count: before each replay
   // a one-thread launch writes it to the handle's step word, which the graph's
   // steps read (step k of the graph adds k).
-  if (nsteps >= kStepGraph && !h->graph_off) {
+  // A caller capturing its own stream gets plain launches, which its graph records.
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &capture) != cudaSuccess) {
+    cudaGetLastError();
+    capture = cudaStreamCaptureStatusActive;  // unknown: take the plain launches
+  }
+  if (nsteps >= kStepGraph && !h->graph_off && capture == cudaStreamCaptureStatusNone) {
     if (!ensure_step_graph(h)) {
       h->graph_off = true;
     } else {

@@ -162,3 +162,26 @@ def test_graph_replay_follows_buffer_flips_and_new_states(precision):
     same_run(128)
     a.close()
     b.close()
+
+
+def test_steps_inside_a_callers_graph_capture():
+    """A caller that captures its own stream into a CUDA graph (here torch's
+    CUDAGraph) gets plain launches from lb_step, which the graph records: one
+    replay of 70 captured steps equals 70 steps run directly, bit for bit."""
+    from paper_1809_02390_gb300 import Lattice, derive
+
+    d = derive(160, 96, Tr=0.85)
+    rho0 = inputs.droplet(160, 96, 24, 5, d["rho_g"], d["rho_l"])
+    s = torch.cuda.Stream()
+    a = Lattice(rho0, precision="fp32", layout="rows", Tr=0.85, stream=s)
+    b = Lattice(rho0, precision="fp32", layout="rows", Tr=0.85)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        a.step(70)
+    g.replay()
+    b.step(70)
+    torch.cuda.synchronize()
+    assert torch.equal(a.state(), b.state())
+    a.close()
+    b.close()
