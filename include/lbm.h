@@ -268,7 +268,10 @@ size_t lb_batch_pool_bytes(const lb_params* ps, int n);
 size_t lb_batch_meta_bytes(const lb_params* ps, int n);
 int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void* pool_b, void* meta,
                   size_t meta_bytes, const double* rho0, int rho0_on_device, void* stream);
-/* Advances every lattice by nsteps. */
+/* Advances every lattice by nsteps.  While the batch's stream is being captured
+ * into the caller's own CUDA graph, the steps go in as plain launches (a graph
+ * of the library's own is never replayed into another capture); the results
+ * are the same bits either way. */
 int lb_batch_run(lb_batch* b, int64_t nsteps);
 /* Autotuner: times each launch shape (plain loads: tile height 16 or 32, register
  * budget, and either one block per tile or a persistent grid of 1..max resident

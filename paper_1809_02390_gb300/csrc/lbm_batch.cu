@@ -737,8 +737,14 @@ int lb_batch_init(lb_batch** out, const lb_params* ps, int n, void* pool_a, void
 int lb_batch_run(lb_batch* b, int64_t nsteps) {
   if (!b) return LB_EINVAL;
   if (nsteps < 0) return berr(b, LB_EINVAL, "nsteps must be >= 0%s");
-  // The legacy default stream cannot be captured: plain launches there.
-  while (b->stream != nullptr && nsteps >= kGraphSteps) {
+  // The legacy default stream cannot be captured, and a stream that the caller is
+  // capturing records plain launches in its own graph: plain launches there.
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (b->stream != nullptr && cudaStreamIsCapturing(b->stream, &capture) != cudaSuccess) {
+    cudaGetLastError();
+    capture = cudaStreamCaptureStatusActive;
+  }
+  while (b->stream != nullptr && capture == cudaStreamCaptureStatusNone && nsteps >= kGraphSteps) {
     const int rc = ensure_graph(b, b->cur);
     if (rc != LB_OK) return rc;
     const cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);

@@ -186,3 +186,23 @@ def test_status_names_the_lattices_that_go_non_finite(orc):
     for i, ref in zip((0, 2), singles):
         assert torch.equal(b.state(i), ref)
     b.close()
+
+
+def test_batch_steps_inside_a_callers_graph_capture():
+    """A batch whose stream the caller captures into its own CUDA graph records
+    plain launches: one replay of 70 captured steps equals 70 single-lattice steps."""
+    from paper_1809_02390_gb300 import Batch
+
+    rhos, kws = _inputs()
+    s = torch.cuda.Stream()
+    b = Batch(rhos, kws, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(70)
+    g.replay()
+    torch.cuda.synchronize()
+    ref = _singles(rhos, kws, 70)
+    for i in range(len(rhos)):
+        assert torch.equal(b.state(i), ref[i]), i
+    b.close()
