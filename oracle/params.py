@@ -79,3 +79,55 @@ def from_physical(eos: str = "vdw", a: float = 9.0 / 49.0, b: float = 2.0 / 21.0
                          G2=g2, varpi=varpi, s0=s0, se=se, seps=se if s_eps is None else s_eps,
                          sj=sj, sq=sq_d if s_q is None else s_q, sp=s_p, rho_g=rg, rho_l=rl,
                          Tc=thermo.critical_temperature(eos, a, b, R))
+
+
+# --- D3Q19 form of the model (lbm3d_oracle.cpp) ---------------------------------
+
+def k_3d(varpi: float) -> float:
+    """k of the 3-D collision matrix: the bulk viscosity (1 - 11 k / 38) (2/3) c_s^2 tau_e
+    is varpi times the plain lattice's, so k = 38 (1 - varpi) / 11."""
+    return 38.0 * (1.0 - varpi) / 11.0
+
+
+def relaxation_rates_3d(s_p: float, varpi: float) -> tuple[float, float]:
+    """(s_q, s_e) from the D3Q19 closure tau_p tau_q = (1 + 5 k / 19) tau_e tau_q = 1/12,
+    the 3-D counterpart of Eq. 16 (the isotropic error term of the steady third-order
+    analysis is proportional to (1 + 5k/19) tau_e tau_q - tau_p tau_q, the anisotropic
+    one to 12 tau_p tau_q - 1, as on D2Q9 with k + 1 in place of 1 + 5k/19)."""
+    tau_p = 1.0 / s_p - 0.5
+    tau_q = 1.0 / (12.0 * tau_p)
+    tau_e = 1.0 / (12.0 * (1.0 + 5.0 * k_3d(varpi) / 19.0) * tau_q)
+    return 1.0 / (tau_q + 0.5), 1.0 / (tau_e + 0.5)
+
+
+@dataclass
+class LatticeParams3(LatticeParams):
+    """D3Q19 parameters: the D2Q9 set plus the rates of the third-order m moments
+    (s_m) and the anisotropic fourth-order pi moments (s_pi)."""
+    sm: float = 1.0
+    spi: float = 1.0
+
+
+S_EPS_3D = 1.75
+
+
+def from_physical_3d(s_m: float | None = None, s_pi: float | None = None, **kw) -> LatticeParams3:
+    """As from_physical (same EOS, G, c^2 and coexistence densities: the recovered
+    pressure tensor of the 3-D model is that of Eq. 17), with the 3-D rate closure.
+    Unless given, s_eps = 1.75, s_m = s_q (all third-order moments at one rate) and
+    s_pi = s_eps (all fourth-order moments at one rate).  None of the three enters
+    the Navier-Stokes stress or the steady third-order terms; s_eps = s_e (the 2-D
+    default) leaves the checkerboard mode k = (pi, pi, pi) of the e-eps block
+    unstable in the gas (|lambda| = 1.26 per step at Tr = 0.8), s_eps = s_pi in
+    [1.7, 1.8] makes the uniform gas and liquid linearly stable at every wave vector."""
+    s_p = kw.get("s_p", 1.0)
+    varpi = kw.get("varpi", 1.0 / 6.0)
+    sq, se = relaxation_rates_3d(s_p, varpi)
+    kw.setdefault("s_q", sq)
+    kw.setdefault("s_e", se)
+    kw.setdefault("s_eps", S_EPS_3D)
+    base = from_physical(**kw)
+    d = base.as_dict()
+    d["sm"] = base.sq if s_m is None else s_m
+    d["spi"] = base.seps if s_pi is None else s_pi
+    return LatticeParams3(**d)
