@@ -34,6 +34,7 @@ N_SIDE = 4096
 TR = 0.8
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 BYTES_PER_LU = {"fp64": 144, "fp32": 72, "fp16s": 36}  # read 9 + write 9 populations
+BYTES_PER_LU_D3Q19 = {"fp64": 304, "fp32": 152}  # read 19 + write 19 populations
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
 # for the kernel code they were measured on (sha256 of the files below with
 # comments and blank lines removed).
@@ -656,6 +657,30 @@ def run_ours(args):
         del lt
         torch.cuda.empty_cache()
     del rho_cs
+
+    # D3Q19 form of the step (include/lbm3d.h): a 256^3 spinodal decomposition at the
+    # same Tr (16.8M nodes, as many as the 4096^2 lattice), FP32 and FP64; the fused
+    # step reads and writes 19 populations per node (152 / 304 bytes).
+    import numpy as np
+
+    from paper_1809_02390_gb300 import Lattice3
+
+    n3 = 256
+    d3 = lderive(n, n, Tr=TR)
+    rho3 = 0.5 * (d3["rho_g"] + d3["rho_l"]) * (1 + 0.01 * np.random.default_rng(rank).uniform(-1, 1, (n3,) * 3))
+    for prec, k in (("fp32", quarter), ("fp64", 30)):
+        lt = Lattice3(rho3, precision=prec, Tr=TR)
+        lt.step(3)
+        m = time_steps(lt, k, torch) / k
+        gbs = BYTES_PER_LU_D3Q19[prec] * n3 ** 3 / (m * 1e-3) / 1e9
+        variants["d3q19_%s_256cubed" % prec] = {
+            "MLUPS": round(n3 ** 3 / (m * 1e-3) / 1e6, 1), "ms_per_step": round(m, 4),
+            "algorithmic_GBps": round(gbs, 1), "frac_of_measured_hbm": round(gbs / pk["hbm_gbs"], 4),
+            "kernel": "k_d3_step<%s>" % ("float, true" if prec == "fp32" else "double, false")}
+        lt.close()
+        del lt
+        torch.cuda.empty_cache()
+    del rho3
 
     # --- end to end through the public API with host buffers -------------------
     rho_host = torch.from_numpy(np.ascontiguousarray(rho0)).pin_memory()

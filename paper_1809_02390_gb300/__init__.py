@@ -2,7 +2,8 @@
 
 Implements the per-node time step of Huang, Wu & Adams, "Lattice Boltzmann
 model with self-tuning equation of state for multiphase flows"
-(arXiv:1809.02390) as hand-written CUDA behind the C ABI of include/lbm.h.
+(arXiv:1809.02390) as hand-written CUDA behind the C ABI of include/lbm.h,
+and its D3Q19 form behind include/lbm3d.h (Lattice3).
 PyTorch only provides device memory and streams.
 
     lat = Lattice(rho0, precision="fp32", Tr=0.85)
@@ -166,6 +167,84 @@ class Lattice:
         except Exception:
             pass
 
+
+
+class Lattice3:
+    """One periodic D3Q19 lattice (the 3-D form of the model, include/lbm3d.h) on
+    the current CUDA device and stream.
+
+    rho0: initial density [nz, ny, nx] (numpy array, or a float64 tensor).
+    precision "fp32" or "fp64"; keyword arguments are the fields of ``lb_params``.
+    ``rho_ref=None`` stores deviations from the rest state at the mean initial
+    density (FP32) or at 0 (FP64)."""
+
+    def __init__(self, rho0, precision: str = "fp32", eos: str = "vdw", rho_ref: float | None = None, stream=None,
+                 **kw):
+        torch = _torch()
+        if isinstance(rho0, np.ndarray):
+            rho_t = torch.from_numpy(np.ascontiguousarray(rho0, dtype=np.float64)).pin_memory()
+            on_device = False
+        else:
+            rho_t = rho0.to(dtype=torch.float64).contiguous()
+            on_device = rho_t.is_cuda
+            if not on_device:
+                rho_t = rho_t.pin_memory()
+        nz, ny, nx = rho_t.shape
+        if rho_ref is None:
+            rho_ref = 0.0 if precision == "fp64" else float("nan")
+        self.p = params(nx, ny, precision=precision, eos=eos, rho_ref=rho_ref, **kw)
+        self.nx, self.ny, self.nz, self.precision = nx, ny, nz, precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.f_a = torch.empty((19, nz, ny, nx), dtype=self.dtype, device=dev)
+        self.f_b = torch.empty_like(self.f_a)
+        self._rho0_keep = rho_t
+        self.h = capi.lb_d3_init(self.p, nz, self.f_a.data_ptr(), self.f_b.data_ptr(), rho_t.data_ptr(), on_device,
+                                 self.stream.cuda_stream)
+        self.p, self.derived = capi.lb_d3_get_params(self.h)
+        self.rho_ref = self.p.rho_ref
+        self.velocities = capi.lb_d3_velocities()
+
+    def step(self, nsteps: int = 1) -> None:
+        capi.lb_d3_step(self.h, nsteps)
+
+    def state(self):
+        """The current state [19, nz, ny, nx], stored as deviations f_i - w_i rho_ref."""
+        return self.f_a if capi.lb_d3_state(self.h) == self.f_a.data_ptr() else self.f_b
+
+    def populations(self):
+        """Post-collision populations in FP64 (storage shift added back)."""
+        torch = _torch()
+        w = torch.tensor([1 / 3 if sum(c * c for c in e) == 0 else (1 / 18 if sum(c * c for c in e) == 1 else 1 / 36)
+                          for e in self.velocities], dtype=torch.float64, device=self.f_a.device)
+        return self.state().double() + self.rho_ref * w[:, None, None, None]
+
+    def set_state(self, f) -> None:
+        """Loads a [19, nz, ny, nx] state (deviations, the storage type) from the device."""
+        f = f.to(device=self.f_a.device, dtype=self.dtype).contiguous()
+        capi.lb_d3_set_state(self.h, f.data_ptr())
+        self.stream.synchronize()
+
+    def moments(self, velocity: bool = True):
+        """(rho, ux, uy, uz) as FP64 [nz, ny, nx] tensors (rho only if not velocity)."""
+        torch = _torch()
+        shape = (self.nz, self.ny, self.nx)
+        rho = torch.empty(shape, dtype=torch.float64, device=self.f_a.device)
+        u = [torch.empty_like(rho) for _ in range(3)] if velocity else [None] * 3
+        capi.lb_d3_moments(self.h, rho.data_ptr(), *[t.data_ptr() if t is not None else None for t in u])
+        return (rho, *u) if velocity else rho
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            capi.lb_d3_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 class Batch:
     """Independent FP32 lattices advanced together (lb_batch_*).

@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbm_capi.cu", "lbm_static.cu", "lbm_adjoint.cu", "lbm_batch.cu", "lbm_thermo.cpp"]
+SOURCES = ["lbm_capi.cu", "lbm_static.cu", "lbm_adjoint.cu", "lbm_batch.cu", "lbm3d.cu", "lbm_thermo.cpp"]
 HEADERS = ["lbm_internal.h", "lbm_device.cuh", "lbm_kernels.cuh", "lbm_handle.cuh", "lbm_adjoint.cuh", "lbm_tma.cuh",
            "lbm_fields.cuh"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(HERE, "..", "include")]
@@ -28,6 +28,7 @@ def _stale() -> bool:
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, s) for s in _sources()] + [os.path.join(CSRC, h) for h in HEADERS]
     deps.append(os.path.join(HERE, "..", "include", "lbm.h"))
+    deps.append(os.path.join(HERE, "..", "include", "lbm3d.h"))
     return any(os.path.exists(d) and os.path.getmtime(d) > t for d in deps)
 
 

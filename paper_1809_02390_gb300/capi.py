@@ -102,6 +102,19 @@ SIGNATURES = [
     ("lb_set_step_blocks", ctypes.c_int, [_V, ctypes.c_int]),
     ("lb_last_error", ctypes.c_char_p, [_V]),
     ("lb_free", None, [_V]),
+    # D3Q19 form of the step (include/lbm3d.h)
+    ("lb_d3_velocities", None, [ctypes.POINTER(ctypes.c_int)] * 3),
+    ("lb_d3_derive", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lb_derived)]),
+    ("lb_d3_state_bytes", ctypes.c_size_t, [_P, ctypes.c_int32]),
+    ("lb_d3_init", ctypes.c_int, [ctypes.POINTER(_V), _P, ctypes.c_int32, _V, _V, _V, ctypes.c_int, _V]),
+    ("lb_d3_step", ctypes.c_int, [_V, ctypes.c_int64]),
+    ("lb_d3_moments", ctypes.c_int, [_V, _V, _V, _V, _V]),
+    ("lb_d3_state", _V, [_V]),
+    ("lb_d3_get_state", ctypes.c_int, [_V, _V]),
+    ("lb_d3_set_state", ctypes.c_int, [_V, _V]),
+    ("lb_d3_get_params", ctypes.c_int, [_V, ctypes.POINTER(lb_params), ctypes.POINTER(lb_derived)]),
+    ("lb_d3_last_error", ctypes.c_char_p, [_V]),
+    ("lb_d3_free", None, [_V]),
 ]
 
 
@@ -369,3 +382,65 @@ def lb_last_error(h: int | None = None) -> str:
 
 def lb_free(h: int) -> None:
     lib().lb_free(h)
+
+
+# --- D3Q19 step ------------------------------------------------------------------
+
+def check_d3(rc: int, h=None) -> int:
+    if rc != LB_OK:
+        msg = lib().lb_d3_last_error(h)
+        raise LBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lb_d3_velocities() -> list[tuple[int, int, int]]:
+    e = [(ctypes.c_int * 19)() for _ in range(3)]
+    lib().lb_d3_velocities(*e)
+    return list(zip(*[list(a) for a in e]))
+
+
+def lb_d3_derive(p: lb_params, nz: int) -> dict:
+    d = lb_derived()
+    check_d3(lib().lb_d3_derive(ctypes.byref(p), int(nz), ctypes.byref(d)))
+    return d.as_dict()
+
+
+def lb_d3_state_bytes(p: lb_params, nz: int) -> int:
+    return lib().lb_d3_state_bytes(ctypes.byref(p), int(nz))
+
+
+def lb_d3_init(p: lb_params, nz: int, f_a: int, f_b: int, rho0: int, rho0_on_device: bool, stream: int) -> int:
+    h = ctypes.c_void_p()
+    check_d3(lib().lb_d3_init(ctypes.byref(h), ctypes.byref(p), int(nz), f_a, f_b, rho0, int(bool(rho0_on_device)),
+                              stream or None))
+    return h.value
+
+
+def lb_d3_step(h: int, nsteps: int) -> None:
+    check_d3(lib().lb_d3_step(h, int(nsteps)), h)
+
+
+def lb_d3_moments(h: int, rho: int, ux: int | None, uy: int | None, uz: int | None) -> None:
+    check_d3(lib().lb_d3_moments(h, rho, ux, uy, uz), h)
+
+
+def lb_d3_state(h: int) -> int:
+    return lib().lb_d3_state(h)
+
+
+def lb_d3_get_state(h: int, dst: int) -> None:
+    check_d3(lib().lb_d3_get_state(h, dst), h)
+
+
+def lb_d3_set_state(h: int, src: int) -> None:
+    check_d3(lib().lb_d3_set_state(h, src), h)
+
+
+def lb_d3_get_params(h: int) -> tuple[lb_params, dict]:
+    p, d = lb_params(), lb_derived()
+    check_d3(lib().lb_d3_get_params(h, ctypes.byref(p), ctypes.byref(d)), h)
+    return p, d.as_dict()
+
+
+def lb_d3_free(h: int) -> None:
+    lib().lb_d3_free(h)

@@ -197,3 +197,70 @@ def test_null_and_empty_arguments_are_rejected_without_a_gpu(capi):
     ps = (capi.lb_params * 1)(capi.make_params(8, 8))
     rc = lib.lb_batch_init(ctypes.byref(b), ps, 0, 1 << 40, 2 << 40, 3 << 40, 1 << 20, None, 0, None)
     assert rc == capi.LB_EINVAL and not b.value
+
+
+def test_d3_velocities_are_the_d3q19_set(capi):
+    e = capi.lb_d3_velocities()
+    assert len(set(e)) == 19 and e[0] == (0, 0, 0)
+    assert sorted(sum(c * c for c in v) for v in e) == [0] + [1] * 6 + [2] * 12
+    assert all(e[2 * P + 2] == tuple(-c for c in e[2 * P + 1]) for P in range(9))
+
+
+@pytest.mark.parametrize("varpi,s_p", [(1 / 6, 1.0), (0.3, 1.25), (0.05, 0.8)])
+def test_d3_derived_parameters_match_the_3d_oracle(capi, varpi, s_p):
+    """The library's 3-D coefficients and closure against the D3Q19 oracle's (host
+    code on both sides; the oracle's are pinned in tests/test_oracle_d3q19.py)."""
+    from oracle import d3q19
+
+    d3q19.build()
+    p = capi.make_params(40, 20, Tr=0.8, K_int=1.5, varpi=varpi, s_p=s_p)
+    d = capi.lb_d3_derive(p, 10)
+    o = op.from_physical_3d(Tr=0.8, K_int=1.5, varpi=varpi, s_p=s_p)
+    c = d3q19.coefficients(o)
+    for k_lib, v in (("s_e", o.se), ("s_q", o.sq), ("s_eps", o.seps), ("lam", o.lam), ("G2", o.G2),
+                     ("rho_g", o.rho_g), ("rho_l", o.rho_l), ("k", c["k"]), ("h", c["h"]), ("b", c["b"]),
+                     ("beta2", c["beta2"])):
+        assert d[k_lib] == pytest.approx(v, rel=1e-12), k_lib
+
+
+@pytest.mark.parametrize("field,value,nz,code,needle", [
+    ("precision", 2, 4, "ENOTSUP", "FP64 or FP32"), ("layout", 1, 4, "ENOTSUP", "planes"),
+    ("variant", 2, 4, "ENOTSUP", "fused"), ("varpi", 7 / 18, 4, "EINVAL", "7/18"), ("varpi", 1.0, 4, "EINVAL", "varpi"),
+    ("nx", 0, 4, "EINVAL", ">= 1"), ("nx", 40, 0, "EINVAL", ">= 1"), ("nx", 1024, 128, "EINVAL", "too large"),
+    ("s_p", 2.0, 4, "EINVAL", "s_p"), ("Tr", 1.2, 4, "EINVAL", "coexistence")])
+def test_d3_invalid_parameters_are_rejected(capi, field, value, nz, code, needle):
+    p = capi.make_params(40, 20)
+    setattr(p, field, value)
+    if field == "nx" and value == 1024:
+        p.ny = 1024
+    with pytest.raises(capi.LBError) as ei:
+        capi.lb_d3_derive(p, nz)
+    assert ei.value.code == getattr(capi, "LB_" + code) and needle in str(ei.value)
+
+
+def test_d3_varpi_one_third_is_regular_in_3d(capi):
+    """varpi = 1/3 is singular for the D2Q9 coefficients (h, b of Eq. 7) but not for
+    the D3Q19 ones (singular at 7/18)."""
+    p = capi.make_params(16, 16, varpi=1 / 3)
+    with pytest.raises(capi.LBError):
+        capi.lb_derive(p)
+    d = capi.lb_d3_derive(p, 16)
+    assert d["b"] == pytest.approx(21 * (2 / 3) / (5 * (7 - 6)))
+
+
+def test_d3_init_rejects_bad_arguments_before_any_gpu_work(capi):
+    import numpy as np
+
+    lib = capi.lib()
+    p = capi.make_params(8, 8)
+    rho = np.full(8 * 8 * 4, 2.0)
+    h = ctypes.c_void_p()
+    buf = (ctypes.c_char * 16)()
+    assert lib.lb_d3_init(ctypes.byref(h), ctypes.byref(p), 4, ctypes.addressof(buf), ctypes.addressof(buf),
+                          rho.ctypes.data, 0, None) == capi.LB_EINVAL
+    assert lib.lb_d3_init(ctypes.byref(h), ctypes.byref(p), 4, 1 << 40, 2 << 40, None, 0, None) == capi.LB_EINVAL
+    assert not h.value
+    assert lib.lb_d3_step(None, 1) == capi.LB_EINVAL and lib.lb_d3_moments(None, None, None, None, None) == capi.LB_EINVAL
+    assert capi.lb_d3_state_bytes(p, 4) == 19 * 8 * 8 * 4 * 4
+    p.precision = capi.LB_FP64
+    assert capi.lb_d3_state_bytes(p, 4) == 19 * 8 * 8 * 4 * 8

@@ -1,0 +1,243 @@
+"""Parity of the D3Q19 CUDA step (through the C ABI of include/lbm3d.h) with the
+FP64 D3Q19 oracle, and its physics at sizes the oracle cannot run.
+
+Tolerances: FP64 <= 1e-12 relative on f (rounding order of the moment sums,
+which differ between the kernel's even/odd pair sums and the oracle's matrix
+products); FP32 storage and arithmetic <= 2e-5 relative on rho after 200 steps
+(the FP32 rounding of ~700 operations per node, relative 6e-8 each, accumulated
+over the steps as in the D2Q9 bound).  Relative error = max|diff| / max|reference|.
+The library's plane order is mapped onto the oracle's by the velocity vectors."""
+import numpy as np
+import pytest
+
+from paper_1809_02390_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_02390_gb300 import build
+
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def o3():
+    from oracle import d3q19
+
+    d3q19.build()
+    return d3q19
+
+
+def _perm(o3):
+    """perm[i] = oracle plane of the library's plane i."""
+    from paper_1809_02390_gb300 import capi
+
+    lib_e = capi.lb_d3_velocities()
+    ore = [tuple(int(v) for v in c) for c in o3.velocities().T]
+    return np.array([ore.index(tuple(e)) for e in lib_e])
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _params(**kw):
+    from oracle import params as op
+
+    return op.from_physical_3d(**kw)
+
+
+def _lattice(rho0, precision, **kw):
+    from paper_1809_02390_gb300 import Lattice3
+
+    return Lattice3(rho0, precision=precision, **kw)
+
+
+def _sphere(shape, R, W, rg, rl, centre=None):
+    nz, ny, nx = shape
+    c = centre or (nx / 2 - 0.3, ny / 2 + 0.2, nz / 2 - 0.1)
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    return 0.5 * (rg + rl) - 0.5 * (rl - rg) * np.tanh(2.0 * (r - R) / W)
+
+
+# (nz, ny, nx): several 32 x 8 x 16 tiles with ragged tails in every direction,
+# a lattice smaller than one tile, and lattices one node thick.
+SHAPES = [(19, 11, 37), (3, 3, 3), (1, 1, 40), (17, 9, 33), (2, 5, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp64_init_and_steps_match_the_oracle(o3, shape):
+    """A droplet (radius 4 or what fits) at Tr = 0.85, 60 steps."""
+    p = _params(Tr=0.85, K_int=1.0)
+    R = max(1.0, min(4.0, min(s for s in shape if s > 1) / 3.0)) if max(shape) > 1 else 1.0
+    rho0 = _sphere(shape, R, 4.0, p.rho_g, p.rho_l)
+    lat = _lattice(rho0, "fp64", Tr=0.85, K_int=1.0)
+    perm = _perm(o3)
+    f0 = o3.init_eq(p, rho0)
+    assert _rel(lat.populations().cpu().numpy(), f0[perm]) <= 1e-15
+    lat.step(60)
+    torch.cuda.synchronize()
+    ref = o3.step(p, f0, 60)
+    assert _rel(lat.populations().cpu().numpy(), ref[perm]) <= 1e-12
+
+
+def test_fp64_with_flow_matches_the_oracle(o3):
+    """A state with random velocities (the oracle's equilibrium, loaded through
+    lb_d3_set_state) exercises every velocity-dependent entry of S, the forcing
+    and the cubic terms of the equilibrium's second moment."""
+    rng = np.random.default_rng(5)
+    shape = (18, 10, 35)
+    p = _params(Tr=0.8, K_int=1.0)
+    rho0 = _sphere(shape, 5.0, 4.0, p.rho_g, p.rho_l)
+    u = [rng.uniform(-0.03, 0.03, shape) for _ in range(3)]
+    f0 = o3.init_eq(p, rho0, *u)
+    lat = _lattice(rho0, "fp64", Tr=0.8, K_int=1.0)
+    w = np.array([1 / 3 if sum(c * c for c in e) == 0 else (1 / 18 if sum(c * c for c in e) == 1 else 1 / 36)
+                  for e in lat.velocities])
+    lat.set_state(torch.from_numpy(f0[_perm(o3)] - lat.rho_ref * w[:, None, None, None]).cuda())
+    lat.step(40)
+    torch.cuda.synchronize()
+    ref = o3.step(p, f0, 40)
+    assert _rel(lat.populations().cpu().numpy(), ref[_perm(o3)]) <= 1e-12
+    rho, ux, uy, uz = [t.cpu().numpy() for t in lat.moments()]
+    r_o, ux_o, uy_o, uz_o = o3.macro(p, ref)
+    assert _rel(rho, r_o) <= 1e-13
+    for a, b in ((ux, ux_o), (uy, uy_o), (uz, uz_o)):
+        assert np.abs(a - b).max() <= 1e-12
+
+
+@pytest.mark.parametrize("eos", ["vdw", "cs"])
+def test_fp32_matches_the_oracle(o3, eos):
+    kw = dict(Tr=0.85, K_int=1.0) if eos == "vdw" else dict(eos="cs", a=1.0, b=4.0, Tr=0.8, K_int=1.5)
+    p = _params(**kw)
+    shape = (19, 11, 37)
+    rho0 = _sphere(shape, 5.0, 4.5, p.rho_g, p.rho_l)
+    lkw = dict(Tr=kw["Tr"], K_int=kw["K_int"])
+    if eos == "cs":
+        lkw.update(eos_a=1.0, eos_b=4.0)
+    lat = _lattice(rho0, "fp32", eos=eos, **lkw)
+    lat.step(200)
+    rho = lat.moments(velocity=False).cpu().numpy()
+    ref = o3.macro(p, o3.step(p, o3.init_eq(p, rho0), 200))[0]
+    assert _rel(rho, ref) <= 2e-5
+
+
+def test_zero_steps_and_state_round_trip():
+    p = _params(Tr=0.85)
+    rho0 = _sphere((16, 8, 32), 4.0, 4.0, p.rho_g, p.rho_l)
+    lat = _lattice(rho0, "fp32", Tr=0.85)
+    f0 = lat.state().clone()
+    lat.step(0)
+    torch.cuda.synchronize()
+    assert torch.equal(lat.state(), f0)
+    lat.step(3)
+    f3 = lat.state().clone()
+    lat.set_state(f0)
+    lat.step(3)
+    torch.cuda.synchronize()
+    assert torch.equal(lat.state(), f3)
+
+
+def test_invalid_initial_density_is_rejected():
+    from paper_1809_02390_gb300 import LBError, capi
+
+    p = _params(Tr=0.85)
+    rho0 = np.full((4, 4, 8), p.rho_l)
+    rho0[2, 1, 3] = -1.0
+    with pytest.raises(LBError) as ei:
+        _lattice(rho0, "fp32", Tr=0.85)
+    assert ei.value.code == capi.LB_EINVAL and "node %d" % (2 * 32 + 1 * 8 + 3) in str(ei.value)
+    rho0[2, 1, 3] = 12.0  # above 1/b = 10.5 of the vdW EOS
+    with pytest.raises(LBError) as ei:
+        _lattice(rho0, "fp64", Tr=0.85)
+    assert "1/b" in str(ei.value)
+
+
+def _node_inputs(f, e, w, rho_ref, z, y, x):
+    """Post-streaming populations (FP64, shift added back) and the force stencil sum
+    of node (z, y, x) of a stored [19, nz, ny, nx] state: pull streaming and the
+    densities of the 18 neighbours, each from its own 19 pulled populations."""
+    nz, ny, nx = f.shape[1:]
+
+    def pulled(zz, yy, xx):
+        return np.array([float(f[i, (zz - e[i][2]) % nz, (yy - e[i][1]) % ny, (xx - e[i][0]) % nx]) + w[i] * rho_ref
+                         for i in range(19)])
+
+    s = np.zeros(3)
+    for i in range(1, 19):
+        wt = 1 / 6 if sum(c * c for c in e[i]) == 1 else 1 / 12
+        r = pulled(z + e[i][2], y + e[i][1], x + e[i][0]).sum()
+        s += wt * r * np.array(e[i], dtype=float)
+    return pulled(z, y, x), s
+
+
+def test_full_size_step_on_sampled_nodes(o3):
+    """The benchmark lattice (256^3, FP32, spinodal decomposition, Tr = 0.8) in the
+    launch configuration the benchmark times: after 30 steps one more step is taken
+    and 64 sampled nodes (corners, faces, tile edges, random) are recomputed by the
+    oracle's node collision from the stored state (FP64 arithmetic on the FP32
+    inputs); the FP32 kernel agrees within 2e-5 of the populations' scale."""
+    p = _params(Tr=0.8, K_int=1.0)
+    n = 256
+    rng = np.random.default_rng(3)
+    mean = 0.5 * (p.rho_g + p.rho_l)
+    lat = _lattice(mean * (1 + 0.01 * rng.uniform(-1, 1, (n, n, n))), "fp32", Tr=0.8, K_int=1.0)
+    lat.step(30)
+    before = lat.state().cpu().numpy()
+    lat.step(1)
+    after = lat.state().cpu().numpy()
+    perm = _perm(o3)
+    inv = np.argsort(perm)
+    e = [tuple(v) for v in lat.velocities]
+    w = np.array([1 / 3 if sum(c * c for c in v) == 0 else (1 / 18 if sum(c * c for c in v) == 1 else 1 / 36) for v in e])
+    picks = [(0, 0, 0), (255, 255, 255), (0, 255, 17), (15, 7, 31), (16, 8, 32), (255, 0, 128)]
+    picks += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(58)]
+    scale = np.abs(after).max() + lat.rho_ref / 3
+    for (z, y, x) in picks:
+        g, s = _node_inputs(before, e, w, lat.rho_ref, z, y, x)
+        out = o3.collide_node(p, g[inv], s)[perm] - w * lat.rho_ref
+        assert np.abs(after[:, z, y, x] - out).max() <= 2e-5 * scale, (z, y, x)
+
+
+def test_laplace_law_of_a_sphere():
+    """dp = 2 sigma / R for a droplet (R = 16, W = 4.7, 64^3, FP64, 3,000 steps),
+    sigma from the pressure tensor (Eq. 17, the 3-D model's): within 3% (the
+    cylinder of the same R/W obeys dp = sigma/R to 2.3% in the oracle)."""
+    from oracle import params as op
+    from oracle import thermo
+    import oracle as orc
+
+    orc.build()
+    p = op.from_physical_3d(Tr=0.85, K_int=1.0)
+    sigma = thermo.interface(thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, 0.85), 1.0)["sigma"] * p.lam
+    n = 64
+    rho0 = _sphere((n, n, n), 16.0, 4.7, p.rho_g, p.rho_l, centre=(32.0, 32.0, 32.0))
+    lat = _lattice(rho0, "fp64", Tr=0.85, K_int=1.0)
+    lat.step(3000)
+    rho = lat.moments(velocity=False).cpu().numpy()
+    dp = orc.eos(p, rho[32, 32, 32])[0] - orc.eos(p, rho[0, 0, 0])[0]
+    R = (3 * (rho > 0.5 * (p.rho_g + p.rho_l)).sum() / (4 * np.pi)) ** (1 / 3)
+    assert dp * R / (2 * sigma) == pytest.approx(1.0, rel=3e-2)
+
+
+def test_spinodal_decomposition_in_3d_stays_on_coexistence():
+    """128^3 FP32 spinodal decomposition at Tr = 0.8 for 3,000 steps: finite, both
+    phases within 2% of the Maxwell densities, spurious currents small."""
+    p = _params(Tr=0.8, K_int=1.0)
+    n = 128
+    rng = np.random.default_rng(1)
+    mean = 0.5 * (p.rho_g + p.rho_l)
+    lat = _lattice(mean * (1 + 0.01 * rng.uniform(-1, 1, (n, n, n))), "fp32", Tr=0.8, K_int=1.0)
+    lat.step(3000)
+    rho, ux, uy, uz = [t.cpu().numpy() for t in lat.moments()]
+    assert np.isfinite(rho).all()
+    assert np.percentile(rho, 2) == pytest.approx(p.rho_g, rel=2e-2)
+    assert np.percentile(rho, 98) == pytest.approx(p.rho_l, rel=2e-2)
+    assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 0.05
