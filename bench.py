@@ -750,6 +750,28 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_d3q19(args):
+    """The D3Q19 step alone: an N^3 spinodal lattice at Tr = 0.8 (mean density plus 1%
+    uniform noise, seed 0), W untimed steps, K timed steps (CUDA events), one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1809_02390_gb300 import Lattice3, derive
+
+    n = args.only_d3q19
+    d = derive(64, 64, Tr=TR)
+    rho = 0.5 * (d["rho_g"] + d["rho_l"]) * (1 + 0.01 * np.random.default_rng(0).uniform(-1, 1, (n,) * 3))
+    lat = Lattice3(rho, precision=args.d3q19_precision, Tr=TR)
+    lat.step(args.warmup)
+    ms = time_steps(lat, args.steps, torch) / args.steps
+    ok = bool(torch.isfinite(lat.moments(velocity=False)).all())
+    b = BYTES_PER_LU_D3Q19[args.d3q19_precision]
+    print(json.dumps({"only_d3q19": True, "size": n, "precision": args.d3q19_precision, "steps": args.steps,
+                      "ms_per_step": round(ms, 5), "MLUPS": round(n ** 3 / (ms * 1e-3) / 1e6, 1),
+                      "algorithmic_GBps": round(b * n ** 3 / (ms * 1e-3) / 1e9, 1), "finite": ok}))
+    lat.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -763,6 +785,10 @@ def main():
     ap.add_argument("--main-variant", choices=["fused", "two_pass"], default="fused",
                     help="with --only-main: fused step or the two-pass variant (profiling)")
     ap.add_argument("--only-adjoint", action="store_true", help="time the FP32 adjoint at --size only (profiling)")
+    ap.add_argument("--only-d3q19", type=int, default=0, metavar="N",
+                    help="time the D3Q19 step on an N^3 spinodal lattice only (profiling)")
+    ap.add_argument("--d3q19-precision", choices=["fp32", "fp64"], default="fp32",
+                    help="with --only-d3q19: storage precision")
     ap.add_argument("--only-batch", action="store_true", help="time the 256-lattice batch only (profiling)")
     ap.add_argument("--only-precision", action="store_true", help="run the FP64/FP32/FP16 study only")
     ap.add_argument("--only-validation", action="store_true", help="run the oscillation and W/sigma sweeps only")
@@ -778,6 +804,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_d3q19:
+        run_d3q19(args)
     else:
         run_ours(args)
 

@@ -2,7 +2,7 @@
 // (Huang, Wu & Adams, arXiv:1809.02390, extended to three dimensions) and the
 // lb_d3_* C ABI of include/lbm3d.h.
 //
-// One launch per time step: each block owns a 32 x 8 column of the x-y plane and
+// One launch per time step: each block owns a 32 x 4 column of the x-y plane and
 // marches through 16 z-planes.  For every plane it pulls the populations of its
 // nodes (pull streaming, supplement Eq. 2), sums them into the density and puts
 // the density, with a one-node ring in x and y, into a three-plane ring buffer
@@ -38,9 +38,10 @@ __constant__ int cEX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 
 __constant__ int cEY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ int cEZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 
-constexpr int TX = 32, TY = 8, TZ = 16;
+constexpr int TX = 32, TY = 4, TZ = 16;
 constexpr int HX = TX + 2, HY = TY + 2;
-constexpr int kRing = 2 * HX + 2 * TY;  // ring slots of one density plane (84)
+constexpr int kRing = 2 * HX + 2 * TY;  // ring slots of one density plane (76)
+static_assert(kRing <= TX * TY, "every ring slot needs a thread of the block");
 constexpr double kSEps3 = 1.75;
 
 // Collision constants (host: make_c3).
@@ -264,11 +265,12 @@ __device__ __forceinline__ int wrap(int a, int n) {
 __device__ __forceinline__ int dec(int a, int n) { return a == 0 ? n - 1 : a - 1; }
 __device__ __forceinline__ int inc(int a, int n) { return a == n - 1 ? 0 : a + 1; }
 
-// The fused step.  Grid (ceil(nx/32), ceil(ny/8), ceil(nz/16)), block (32, 8).
+// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/16)), block (32, 4); four
+// blocks (16 warps) per SM at 128 registers.
 // Threads of ragged tiles that lie outside the lattice fill their ring-buffer
 // slot with the density of the wrapped node and do not collide.
 template <typename T, bool KEEP>
-__global__ void __launch_bounds__(TX* TY, 2)
+__global__ void __launch_bounds__(TX* TY, 4)
     k_d3_step(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nz, C3<T> c) {
   __shared__ T pl[3][HY][HX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
