@@ -8,9 +8,10 @@
 // the density, with a one-node ring in x and y, into a three-plane ring buffer
 // in shared memory; the collision of plane z runs once plane z + 1 is there, so
 // the force stencil (Eq. 12) of every node reads its 18 neighbours' densities
-// from shared memory.  The populations of the plane being collided stay in
-// registers (FP32) or are read again from L1/L2 (FP64, to keep the register
-// count down), so each population crosses DRAM once per step in each direction.
+// from shared memory.  In FP32 the populations stay in registers and the pulls of
+// plane z + 2 are in flight while plane z collides; in FP64 the populations of
+// the plane being collided are read again from L1/L2 (to keep the register count
+// down).  Each population crosses DRAM once per step in each direction.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -265,12 +266,37 @@ __device__ __forceinline__ int wrap(int a, int n) {
 __device__ __forceinline__ int dec(int a, int n) { return a == 0 ? n - 1 : a - 1; }
 __device__ __forceinline__ int inc(int a, int n) { return a == n - 1 ? 0 : a + 1; }
 
-// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/16)), block (32, 4); four
-// blocks (16 warps) per SM at 128 registers.
+// Force stencil of node (ly, lx) from the density planes of z - 1 (a), z (b) and
+// z + 1 (e), collision and store of its 19 outputs.
+template <typename T>
+__device__ __forceinline__ void stencil_collide_store(const C3<T>& c, const T (*a)[HX], const T (*b)[HX],
+                                                      const T (*e)[HX], int ly, int lx, const T* fc, T* __restrict__ fout,
+                                                      int N, int idx) {
+  const T sxv = T(1.0 / 6.0) * (b[ly][lx + 1] - b[ly][lx - 1]) +
+                T(1.0 / 12.0) * ((b[ly + 1][lx + 1] - b[ly - 1][lx - 1]) + (b[ly - 1][lx + 1] - b[ly + 1][lx - 1]) +
+                                 (e[ly][lx + 1] - a[ly][lx - 1]) + (a[ly][lx + 1] - e[ly][lx - 1]));
+  const T syv = T(1.0 / 6.0) * (b[ly + 1][lx] - b[ly - 1][lx]) +
+                T(1.0 / 12.0) * ((b[ly + 1][lx + 1] - b[ly - 1][lx - 1]) + (b[ly + 1][lx - 1] - b[ly - 1][lx + 1]) +
+                                 (e[ly + 1][lx] - a[ly - 1][lx]) + (a[ly + 1][lx] - e[ly - 1][lx]));
+  const T szv = T(1.0 / 6.0) * (e[ly][lx] - a[ly][lx]) +
+                T(1.0 / 12.0) * ((e[ly][lx + 1] - a[ly][lx - 1]) + (e[ly][lx - 1] - a[ly][lx + 1]) +
+                                 (e[ly + 1][lx] - a[ly - 1][lx]) + (e[ly - 1][lx] - a[ly + 1][lx]));
+  T o[Q];
+  collide3(c, fc, b[ly][lx], sxv, syv, szv, o);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) fout[i * N + idx] = o[i];
+}
+
+// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/16)), block (32, 4).
 // Threads of ragged tiles that lie outside the lattice fill their ring-buffer
 // slot with the density of the wrapped node and do not collide.
+//   KEEP (FP32, 3 blocks per SM, up to 170 registers): software pipeline in
+//   registers; while plane z collides, the pulls of plane z + 2 are in flight,
+//   plane z + 1 is summed and held, plane z is in fc.
+//   !KEEP (FP64, 4 blocks per SM): plane z + 1 is pulled and summed before the
+//   collision of plane z, whose populations are read again (L1 / L2).
 template <typename T, bool KEEP>
-__global__ void __launch_bounds__(TX* TY, 4)
+__global__ void __launch_bounds__(TX* TY, KEEP ? 3 : 4)
     k_d3_step(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nz, C3<T> c) {
   __shared__ T pl[3][HY][HX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -281,7 +307,7 @@ __global__ void __launch_bounds__(TX* TY, 4)
   const bool active = x < nx && y < ny;
   const int xg = x % nx, yg = y % ny;
   const int xm = dec(xg, nx), xp = inc(xg, nx), ym = dec(yg, ny), yp = inc(yg, ny);
-  // Ring slot of this thread (threads 0..83): top row, bottom row, left and right columns.
+  // Ring slot of this thread (threads 0..75): top row, bottom row, left and right columns.
   const bool ring = tid < kRing;
   int hsx = 0, hsy = 0;
   if (tid < HX) {
@@ -296,60 +322,75 @@ __global__ void __launch_bounds__(TX* TY, 4)
   }
   const int hx = wrap(x0 - 1 + hsx, nx), hy = wrap(y0 - 1 + hsy, ny);
   const int hxm = dec(hx, nx), hxp = inc(hx, nx), hym = dec(hy, ny), hyp = inc(hy, ny);
+  auto pull_node = [&](int zraw, T* v) {
+    const int z = wrap(zraw, nz), zm = dec(z, nz), zp = inc(z, nz);
+    pull19(fin, N, nx, ny, xm, xg, xp, ym, yg, yp, zm, z, zp, v);
+  };
+  auto pull_ring = [&](int zraw, T* v) {
+    const int z = wrap(zraw, nz), zm = dec(z, nz), zp = inc(z, nz);
+    pull19(fin, N, nx, ny, hxm, hx, hxp, hym, hy, hyp, zm, z, zp, v);
+  };
+  auto put = [&](int slot, const T* v, const T* r) {
+    pl[slot][ty + 1][tx + 1] = sum19(v);
+    if (ring) pl[slot][hsy][hsx] = sum19(r);
+  };
 
   T fc[Q], fn[Q];
-  auto density = [&](int zraw, int slot, T* keep) {
-    const int z = wrap(zraw, nz), zm = dec(z, nz), zp = inc(z, nz);
-    T v[Q];
-    pull19(fin, N, nx, ny, xm, xg, xp, ym, yg, yp, zm, z, zp, v);
-    pl[slot][ty + 1][tx + 1] = sum19(v);
-    if (KEEP && keep) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) keep[i] = v[i];
-    }
-    if (ring) {
-      pull19(fin, N, nx, ny, hxm, hx, hxp, hym, hy, hyp, zm, z, zp, v);
-      pl[slot][hsy][hsx] = sum19(v);
-    }
-  };
-  density(z0 - 1, 0, nullptr);
-  density(z0, 1, fc);
   int sp = 0, sc = 1, sn = 2;
-  for (int z = z0; z < z1; ++z) {
-    density(z + 1, sn, fn);
-    __syncthreads();
-    if (active) {
-      const int lx = tx + 1, ly = ty + 1;
-      const T(*a)[HX] = pl[sp];
-      const T(*b)[HX] = pl[sc];
-      const T(*e)[HX] = pl[sn];
-      const T sxv = T(1.0 / 6.0) * (b[ly][lx + 1] - b[ly][lx - 1]) +
-                    T(1.0 / 12.0) * ((b[ly + 1][lx + 1] - b[ly - 1][lx - 1]) + (b[ly - 1][lx + 1] - b[ly + 1][lx - 1]) +
-                                     (e[ly][lx + 1] - a[ly][lx - 1]) + (a[ly][lx + 1] - e[ly][lx - 1]));
-      const T syv = T(1.0 / 6.0) * (b[ly + 1][lx] - b[ly - 1][lx]) +
-                    T(1.0 / 12.0) * ((b[ly + 1][lx + 1] - b[ly - 1][lx - 1]) + (b[ly + 1][lx - 1] - b[ly - 1][lx + 1]) +
-                                     (e[ly + 1][lx] - a[ly - 1][lx]) + (a[ly + 1][lx] - e[ly - 1][lx]));
-      const T szv = T(1.0 / 6.0) * (e[ly][lx] - a[ly][lx]) +
-                    T(1.0 / 12.0) * ((e[ly][lx + 1] - a[ly][lx - 1]) + (e[ly][lx - 1] - a[ly][lx + 1]) +
-                                     (e[ly + 1][lx] - a[ly - 1][lx]) + (e[ly - 1][lx] - a[ly + 1][lx]));
-      if (!KEEP) {
-        const int zz = z, zm = dec(zz, nz), zp = inc(zz, nz);
-        pull19(fin, N, nx, ny, xm, xg, xp, ym, yg, yp, zm, zz, zp, fc);
+  if constexpr (KEEP) {
+    T fr[Q], gn[Q], gr[Q];
+    pull_node(z0 - 1, fn);
+    if (ring) pull_ring(z0 - 1, fr);
+    put(0, fn, fr);
+    pull_node(z0, fc);
+    if (ring) pull_ring(z0, fr);
+    put(1, fc, fr);
+    pull_node(z0 + 1, fn);
+    if (ring) pull_ring(z0 + 1, fr);
+    for (int z = z0; z < z1; ++z) {
+      put(sn, fn, fr);
+      if (z + 1 < z1) {
+        pull_node(z + 2, gn);
+        if (ring) pull_ring(z + 2, gr);
       }
-      T o[Q];
-      collide3(c, fc, b[ly][lx], sxv, syv, szv, o);
-      const int idx = (z * ny + y) * nx + x;
+      __syncthreads();
+      if (active) stencil_collide_store(c, pl[sp], pl[sc], pl[sn], ty + 1, tx + 1, fc, fout, N, (z * ny + y) * nx + x);
+      __syncthreads();
+      const int t = sp;
+      sp = sc;
+      sc = sn;
+      sn = t;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fout[i * N + idx] = o[i];
+      for (int i = 0; i < Q; ++i) {
+        fc[i] = fn[i];
+        fn[i] = gn[i];
+        fr[i] = gr[i];
+      }
     }
-    __syncthreads();
-    const int t = sp;
-    sp = sc;
-    sc = sn;
-    sn = t;
-    if (KEEP) {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) fc[i] = fn[i];
+  } else {
+    // One array at a time: pull, sum, then the ring slot's pull and sum.
+    auto density = [&](int zraw, int slot) {
+      pull_node(zraw, fn);
+      pl[slot][ty + 1][tx + 1] = sum19(fn);
+      if (ring) {
+        pull_ring(zraw, fn);
+        pl[slot][hsy][hsx] = sum19(fn);
+      }
+    };
+    density(z0 - 1, 0);
+    density(z0, 1);
+    for (int z = z0; z < z1; ++z) {
+      density(z + 1, sn);
+      __syncthreads();
+      if (active) {
+        pull_node(z, fc);
+        stencil_collide_store(c, pl[sp], pl[sc], pl[sn], ty + 1, tx + 1, fc, fout, N, (z * ny + y) * nx + x);
+      }
+      __syncthreads();
+      const int t = sp;
+      sp = sc;
+      sc = sn;
+      sn = t;
     }
   }
 }
