@@ -245,3 +245,21 @@ def test_spinodal_decomposition_in_3d_stays_on_coexistence():
     assert np.median(rho[rho < mid]) == pytest.approx(p.rho_g, rel=4e-2)
     assert np.median(rho[rho > mid]) == pytest.approx(p.rho_l, rel=1e-2)
     assert max(np.abs(ux).max(), np.abs(uy).max(), np.abs(uz).max()) < 0.05
+
+
+def test_steps_inside_a_callers_graph_capture():
+    """lb_d3_step issues plain kernel launches on the handle's stream, so a caller
+    can capture them into a CUDA graph of its own; replaying it gives the same
+    bits as stepping directly."""
+    p = _params(Tr=0.85)
+    rho0 = _sphere((20, 9, 35), 4.0, 4.0, p.rho_g, p.rho_l)
+    s = torch.cuda.Stream()
+    a = _lattice(rho0, "fp32", Tr=0.85, stream=s)
+    b = _lattice(rho0, "fp32", Tr=0.85, stream=s)
+    a.step(6)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.step(6)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(a.state(), b.state())
