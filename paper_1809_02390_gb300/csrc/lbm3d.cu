@@ -3,7 +3,7 @@
 // lb_d3_* C ABI of include/lbm3d.h.
 //
 // One launch per time step: each block owns a 32 x 4 column of the x-y plane and
-// marches through 16 z-planes.  For every plane it pulls the populations of its
+// marches through 32 z-planes.  For every plane it pulls the populations of its
 // nodes (pull streaming, supplement Eq. 2), sums them into the density and puts
 // the density, with a one-node ring in x and y, into a three-plane ring buffer
 // in shared memory; the collision of plane z runs once plane z + 1 is there, so
@@ -39,7 +39,7 @@ __constant__ int cEX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 
 __constant__ int cEY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ int cEZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 
-constexpr int TX = 32, TY = 4, TZ = 16;
+constexpr int TX = 32, TY = 4, TZ = 32;
 constexpr int HX = TX + 2, HY = TY + 2;
 constexpr int kRing = 2 * HX + 2 * TY;  // ring slots of one density plane (76)
 static_assert(kRing <= TX * TY, "every ring slot needs a thread of the block");
@@ -287,7 +287,7 @@ __device__ __forceinline__ void stencil_collide_store(const C3<T>& c, const T (*
   for (int i = 0; i < Q; ++i) fout[i * N + idx] = o[i];
 }
 
-// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/16)), block (32, 4).
+// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/32)), block (32, 4).
 // Threads of ragged tiles that lie outside the lattice fill their ring-buffer
 // slot with the density of the wrapped node and do not collide.
 //   KEEP (FP32, 3 blocks per SM, up to 170 registers): software pipeline in
@@ -322,12 +322,14 @@ __global__ void __launch_bounds__(TX* TY, KEEP ? 3 : 4)
   }
   const int hx = wrap(x0 - 1 + hsx, nx), hy = wrap(y0 - 1 + hsy, ny);
   const int hxm = dec(hx, nx), hxp = inc(hx, nx), hym = dec(hy, ny), hyp = inc(hy, ny);
+  // Plane indices run from z0 - 1 to z1, at most one lattice length outside [0, nz).
+  auto zwrap = [&](int zraw) { return zraw < 0 ? zraw + nz : (zraw >= nz ? zraw - nz : zraw); };
   auto pull_node = [&](int zraw, T* v) {
-    const int z = wrap(zraw, nz), zm = dec(z, nz), zp = inc(z, nz);
+    const int z = zwrap(zraw), zm = dec(z, nz), zp = inc(z, nz);
     pull19(fin, N, nx, ny, xm, xg, xp, ym, yg, yp, zm, z, zp, v);
   };
   auto pull_ring = [&](int zraw, T* v) {
-    const int z = wrap(zraw, nz), zm = dec(z, nz), zp = inc(z, nz);
+    const int z = zwrap(zraw), zm = dec(z, nz), zp = inc(z, nz);
     pull19(fin, N, nx, ny, hxm, hx, hxp, hym, hy, hyp, zm, z, zp, v);
   };
   auto put = [&](int slot, const T* v, const T* r) {

@@ -67,9 +67,9 @@ def _sphere(shape, R, W, rg, rl, centre=None):
     return 0.5 * (rg + rl) - 0.5 * (rl - rg) * np.tanh(2.0 * (r - R) / W)
 
 
-# (nz, ny, nx): several 32 x 4 x 16 tiles with ragged tails in every direction,
+# (nz, ny, nx): several 32 x 4 x 32 tiles with ragged tails in every direction,
 # a lattice smaller than one tile, and lattices one node thick.
-SHAPES = [(19, 11, 37), (3, 3, 3), (1, 1, 40), (17, 9, 33), (2, 5, 1)]
+SHAPES = [(19, 11, 37), (3, 3, 3), (1, 1, 40), (17, 9, 33), (2, 5, 1), (37, 5, 33)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
