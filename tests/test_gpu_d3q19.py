@@ -263,3 +263,93 @@ def test_steps_inside_a_callers_graph_capture():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(a.state(), b.state())
+
+
+def _planar_profile(n, normal, W, rg, rl):
+    """rho(x, y, z) of a liquid slab whose normal is `normal` (integer vector) on a
+    periodic n^3 lattice (n x 1 x 1 for the x normal): rho depends on
+    s = (normal . x) mod n, a distance s / |normal| along the normal."""
+    norm = np.sqrt(sum(c * c for c in normal))
+    if normal == (1, 0, 0):
+        x = np.arange(n)[None, None, :].astype(float)
+        s = x / norm
+    else:
+        z, y, x = np.mgrid[0:n, 0:n, 0:n]
+        s = ((normal[0] * x + normal[1] * y + normal[2] * z) % n) / norm
+    period = n / norm
+    d = np.abs(s - period / 2) - period / 4
+    mid, half = 0.5 * (rg + rl), 0.5 * (rl - rg)
+    return mid - half * np.tanh(2.0 * np.arctanh(0.9) * d / W)
+
+
+def _profile_along_x(rho):
+    return rho[0, 0, :]
+
+
+def _thickness(profile, rg, rl):
+    lo, hi = rg + 0.05 * (rl - rg), rg + 0.95 * (rl - rg)
+    x = np.arange(len(profile))
+    return np.interp(hi, profile, x) - np.interp(lo, profile, x)
+
+
+def test_interfaces_normal_to_x_110_and_111_agree():
+    """Isotropy of the 3-D model (FP64, Tr = 0.8, K_INT = 1.5): flat interfaces normal
+    to x, (1,1,0) and (1,1,1) relax to the same coexistence densities and thickness
+    (rho depends on (n . x) mod 96; the profile is read along the x axis, where it
+    advances by 1/|n| per node).  (1,1,1) is the direction of the corner velocities
+    D3Q19 does not have.  Measured: gas within 0.6% and W within 1% of the axis
+    values; the axis gas density within 0.3% of the Maxwell construction."""
+    from oracle import thermo
+
+    Tr, K, n = 0.8, 1.5, 96
+    p = _params(Tr=Tr, K_int=K)
+    W = thermo.interface(thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, Tr), K)["W"]
+    out = {}
+    for normal in ((1, 0, 0), (1, 1, 0), (1, 1, 1)):
+        lat = _lattice(_planar_profile(n, normal, W, p.rho_g, p.rho_l), "fp64", Tr=Tr, K_int=K)
+        lat.step(6000)
+        prof = _profile_along_x(lat.moments(velocity=False).cpu().numpy())
+        lat.close()
+        norm = np.sqrt(sum(c * c for c in normal))
+        k = int(round(n / (2 * 1)))  # liquid centre along x for every normal (s = n/2 at x = n/2)
+        rg, rl = prof[0], prof[k]
+        out[normal] = (rg, rl, _thickness(prof[: n // 2], rg, rl) / norm)
+    ga, la, wa = out[(1, 0, 0)]
+    assert ga == pytest.approx(p.rho_g, rel=3e-3) and la == pytest.approx(p.rho_l, rel=5e-4)
+    for normal in ((1, 1, 0), (1, 1, 1)):
+        g, l, w = out[normal]
+        assert g == pytest.approx(ga, rel=1e-2), normal
+        assert l == pytest.approx(la, rel=2e-3), normal
+        assert w == pytest.approx(wa, rel=2e-2), normal
+
+
+@pytest.mark.parametrize("Tr", [0.95, 0.9, 0.8, 0.7, 0.6])
+def test_coexistence_curve_in_3d(Tr):
+    """Flat interfaces (FP64, K_INT chosen for W = 6 by the pressure tensor, 20,000
+    steps) at five temperatures.  The 3-D model (256 x 1 x 1) and the D2Q9 model
+    (256 x 4) share the recovered pressure tensor of Eq. 17, so they must give the same
+    coexistence densities: gas within 0.5%, liquid within 0.1% of each other.  Both
+    follow the Maxwell construction (main-text Fig. 1): liquid within 0.3%, gas within
+    1% for Tr >= 0.7.  At Tr = 0.6 both gas densities are 6% high at W = 6 (2.8% at
+    W = 8, 2.2% at W = 10: the paper's remark that the gas branch below Tr = 0.6 needs
+    wider interfaces)."""
+    from oracle import thermo
+    from paper_1809_02390_gb300 import Lattice
+
+    e = thermo.make_eos("vdw", 9 / 49, 2 / 21, 1.0, Tr)
+    K = 6.0 / thermo.interface(e, 1.0)["W"]
+    p = _params(Tr=Tr, K_int=K)
+    n = 256
+    slab = inputs.slab(n, 4, n // 2, 6.0, p.rho_g, p.rho_l)
+    lat = _lattice(slab[0][None, None, :], "fp64", Tr=Tr, K_int=K)
+    lat.step(20000)
+    prof3 = lat.moments(velocity=False).cpu().numpy()[0, 0]
+    lat.close()
+    lat2 = Lattice(slab, precision="fp64", Tr=Tr, K_int=K)
+    lat2.step(20000)
+    prof2 = lat2.moments(velocity=False).cpu().numpy()[0]
+    lat2.close()
+    assert prof3[0] == pytest.approx(prof2[0], rel=5e-3)
+    assert prof3[n // 2] == pytest.approx(prof2[n // 2], rel=1e-3)
+    assert prof3[n // 2] == pytest.approx(p.rho_l, rel=3e-3)
+    assert prof3[0] == pytest.approx(p.rho_g, rel=1e-2 if Tr >= 0.7 else 7e-2)
