@@ -88,17 +88,24 @@ def test_fp64_init_and_steps_match_the_oracle(o3, shape):
     assert _rel(lat.populations().cpu().numpy(), ref[perm]) <= 1e-12
 
 
-def test_fp64_with_flow_matches_the_oracle(o3):
+@pytest.mark.parametrize("eos", ["vdw", "cs"])
+def test_fp64_with_flow_matches_the_oracle(o3, eos):
     """A state with random velocities (the oracle's equilibrium, loaded through
     lb_d3_set_state) exercises every velocity-dependent entry of S, the forcing
-    and the cubic terms of the equilibrium's second moment."""
+    and the cubic terms of the equilibrium's second moment; van der Waals and
+    Carnahan-Starling (Eq. 20 with a = 1, b = 4)."""
     rng = np.random.default_rng(5)
     shape = (18, 10, 35)
-    p = _params(Tr=0.8, K_int=1.0)
+    if eos == "vdw":
+        p = _params(Tr=0.8, K_int=1.0)
+        lkw = dict(Tr=0.8, K_int=1.0)
+    else:
+        p = _params(eos="cs", a=1.0, b=4.0, Tr=0.8, K_int=1.5)
+        lkw = dict(eos="cs", eos_a=1.0, eos_b=4.0, Tr=0.8, K_int=1.5)
     rho0 = _sphere(shape, 5.0, 4.0, p.rho_g, p.rho_l)
     u = [rng.uniform(-0.03, 0.03, shape) for _ in range(3)]
     f0 = o3.init_eq(p, rho0, *u)
-    lat = _lattice(rho0, "fp64", Tr=0.8, K_int=1.0)
+    lat = _lattice(rho0, "fp64", **lkw)
     w = np.array([1 / 3 if sum(c * c for c in e) == 0 else (1 / 18 if sum(c * c for c in e) == 1 else 1 / 36)
                   for e in lat.velocities])
     lat.set_state(torch.from_numpy(f0[_perm(o3)] - lat.rho_ref * w[:, None, None, None]).cuda())
