@@ -46,6 +46,12 @@ NCU_TRAFFIC = {
     # 2048^2 capture (profiles/k_step_tma_dyn_fp32_rows_2048_full.md) scaled x4 to 4096^2.
     ("k_step_tma_dyn<f2>", "rows", "6ce1a8b1aef1d2b0"): 1021228032,
 }
+# The same for the D3Q19 step, keyed by the hash of csrc/lbm3d.cu: the 192^3 capture
+# (profiles/k_d3_step_fp32_192cubed_full.md) scaled by the node count to 256^3.
+KERNEL_SOURCES_D3Q19 = ["paper_1809_02390_gb300/csrc/lbm3d.cu"]
+NCU_TRAFFIC_D3Q19 = {
+    ("k_d3_step<float, true>", "52fa22a0ef3581d6"): 2510889870,
+}
 
 
 def code_only(text: str) -> str:
@@ -57,9 +63,9 @@ def code_only(text: str) -> str:
     return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES if sources is None else sources:
         with open(os.path.join(ROOT, rel), encoding="utf-8") as fh:
             h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -673,10 +679,15 @@ def run_ours(args):
         lt.step(3)
         m = time_steps(lt, k, torch) / k
         gbs = BYTES_PER_LU_D3Q19[prec] * n3 ** 3 / (m * 1e-3) / 1e9
+        kern = "k_d3_step<%s>" % ("float, true" if prec == "fp32" else "double, false")
+        sha3 = kernel_source_hash(KERNEL_SOURCES_D3Q19)
+        tr3 = NCU_TRAFFIC_D3Q19.get((kern, sha3))
         variants["d3q19_%s_256cubed" % prec] = {
             "MLUPS": round(n3 ** 3 / (m * 1e-3) / 1e6, 1), "ms_per_step": round(m, 4),
             "algorithmic_GBps": round(gbs, 1), "frac_of_measured_hbm": round(gbs / pk["hbm_gbs"], 4),
-            "kernel": "k_d3_step<%s>" % ("float, true" if prec == "fp32" else "double, false")}
+            "algorithmic_bytes_per_launch": BYTES_PER_LU_D3Q19[prec] * n3 ** 3, "traffic": tr3,
+            "traffic_note": "ncu dram bytes read + written, 192^3 capture scaled by nodes" if tr3 else None,
+            "kernel": kern, "kernel_source_sha": sha3}
         lt.close()
         del lt
         torch.cuda.empty_cache()

@@ -29,3 +29,10 @@ def test_traffic_table_matches_the_current_kernel_code():
     the table holds one for the kernel the benchmark times in its layout."""
     keys = {k for k in bench.NCU_TRAFFIC if k[0] == "k_step_tma_dyn<f2>" and k[1] == "rows"}
     assert (("k_step_tma_dyn<f2>", "rows", bench.kernel_source_hash()) in keys)
+
+
+def test_d3q19_traffic_table_matches_the_current_kernel_code():
+    """The D3Q19 step's stored ncu traffic is keyed by the hash of csrc/lbm3d.cu."""
+    sha = bench.kernel_source_hash(bench.KERNEL_SOURCES_D3Q19)
+    assert ("k_d3_step<float, true>", sha) in bench.NCU_TRAFFIC_D3Q19
+    assert sha != bench.kernel_source_hash()
