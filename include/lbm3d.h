@@ -69,8 +69,11 @@ size_t lb_d3_state_bytes(const lb_params* p, int32_t nz);
 int lb_d3_init(lb_d3_handle** out, const lb_params* p, int32_t nz, void* f_a, void* f_b, const double* rho0,
                int rho0_on_device, void* stream);
 
-/* Advances nsteps >= 0 time steps on the handle's stream (asynchronous), each one
- * launch of the fused step: pull streaming, density with its one-node ring,
+/* Advances nsteps >= 0 time steps on the handle's stream (asynchronous).  Runs of
+ * 64 steps replay a CUDA graph captured on first use (one per starting buffer, on a
+ * private stream); the remaining steps, and all steps while the handle's stream is
+ * being captured into the caller's own graph, are plain launches; the results are
+ * the same bits either way.  Each step is the fused kernel: pull streaming, density with its one-node ring,
  * force stencil (Eq. 12 with omega = 1/6 on the axes, 1/12 on the edges),
  * velocity (Eq. 5), EOS, equilibrium, forcing, Q_m, collision (Eq. 13 without R,
  * T, X) and store. */

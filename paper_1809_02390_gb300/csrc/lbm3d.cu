@@ -39,7 +39,7 @@ __constant__ int cEX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 
 __constant__ int cEY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ int cEZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 
-constexpr int TX = 32, TY = 4, TZ = 32;
+constexpr int TX = 32, TY = 4, TZ = 32;  // TZ: the longest z-chunk (see chunk_planes)
 constexpr int HX = TX + 2, HY = TY + 2;
 constexpr int kRing = 2 * HX + 2 * TY;  // ring slots of one density plane (76)
 static_assert(kRing <= TX * TY, "every ring slot needs a thread of the block");
@@ -287,7 +287,8 @@ __device__ __forceinline__ void stencil_collide_store(const C3<T>& c, const T (*
   for (int i = 0; i < Q; ++i) fout[i * N + idx] = o[i];
 }
 
-// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/32)), block (32, 4).
+// The fused step.  Grid (ceil(nx/32), ceil(ny/4), ceil(nz/tz)), block (32, 4); each
+// block marches a chunk of tz <= 32 planes (chunk_planes picks tz).
 // Threads of ragged tiles that lie outside the lattice fill their ring-buffer
 // slot with the density of the wrapped node and do not collide.
 //   KEEP (FP32, 3 blocks per SM, up to 170 registers): software pipeline in
@@ -297,11 +298,11 @@ __device__ __forceinline__ void stencil_collide_store(const C3<T>& c, const T (*
 //   collision of plane z, whose populations are read again (L1 / L2).
 template <typename T, bool KEEP>
 __global__ void __launch_bounds__(TX* TY, KEEP ? 3 : 4)
-    k_d3_step(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nz, C3<T> c) {
+    k_d3_step(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nz, int tz, C3<T> c) {
   __shared__ T pl[3][HY][HX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-  const int z1 = min(z0 + TZ, nz);
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
+  const int z1 = min(z0 + tz, nz);
   const int N = nx * ny * nz;
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < nx && y < ny;
@@ -473,6 +474,14 @@ struct lb_d3_handle {
   cudaStream_t stream;
   C3<double> c64;
   C3<float> c32;
+  int tz;  // planes per z-chunk of the step kernel
+  // Graphs of kD3GraphSteps steps starting from buffer 0 and 1 (captured on first
+  // use on the handle's private stream, launched on `stream`); graph_failed: a
+  // capture failed once, so plain launches are used from then on.
+  cudaStream_t cstream = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  bool graph_failed = false;
   char err[512];
 };
 
@@ -558,18 +567,56 @@ C3<T> make_c3(const lb_params& p, const lb_derived& d) {
   return c;
 }
 
+// Planes per z-chunk: 32 (fewest halo planes) unless that leaves fewer than two
+// waves of resident blocks (3 per SM); then halved down to 2, because a block walks
+// its chunk plane after plane and a short grid leaves the GPU waiting on that chain.
+int chunk_planes(int nx, int ny, int nz, int sms) {
+  const long long xy = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+  int tz = TZ;
+  while (tz > 2 && xy * ((nz + tz - 1) / tz) < 2LL * 3 * sms) tz /= 2;
+  return tz;
+}
+
 void launch_step(lb_d3_handle* h) {
   const lb_params& p = h->p;
-  const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (h->nz + TZ - 1) / TZ), block(TX, TY);
+  const int tz = h->tz;
+  const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (h->nz + tz - 1) / tz), block(TX, TY);
   const void* in = h->f[h->cur];
   void* out = h->f[1 - h->cur];
   if (p.precision == LB_FP64)
     k_d3_step<double, false><<<grid, block, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out),
-                                                            p.nx, p.ny, h->nz, h->c64);
+                                                            p.nx, p.ny, h->nz, tz, h->c64);
   else
     k_d3_step<float, true><<<grid, block, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out),
-                                                          p.nx, p.ny, h->nz, h->c32);
+                                                          p.nx, p.ny, h->nz, tz, h->c32);
   h->cur = 1 - h->cur;
+}
+
+constexpr int64_t kD3GraphSteps = 64;
+static_assert(kD3GraphSteps % 2 == 0, "a graph must end in the buffer it starts from");
+
+// Captures (once) the graph of kD3GraphSteps steps that starts from buffer h->cur.
+// Returns false, and leaves plain launches in use, if the capture fails.
+bool ensure_graph(lb_d3_handle* h) {
+  const int c = h->cur;
+  if (h->exec[c]) return true;
+  if (h->graph_failed) return false;
+  bool ok = h->cstream || cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) ok = cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    cudaStream_t keep = h->stream;
+    h->stream = h->cstream;
+    for (int64_t k = 0; k < kD3GraphSteps; ++k) launch_step(h);
+    h->stream = keep;
+    ok = cudaStreamEndCapture(h->cstream, &h->graph[c]) == cudaSuccess && h->graph[c];
+    if (ok) ok = cudaGraphInstantiate(&h->exec[c], h->graph[c], 0) == cudaSuccess;
+  }
+  h->cur = c;  // the captured launches flipped it an even number of times
+  if (!ok) {
+    cudaGetLastError();
+    h->graph_failed = true;
+  }
+  return ok;
 }
 
 }  // namespace
@@ -668,6 +715,12 @@ int lb_d3_init(lb_d3_handle** out, const lb_params* p, int32_t nz, void* f_a, vo
   h->stream = s;
   h->c64 = c;
   h->c32 = make_c3<float>(q, d);
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  h->tz = chunk_planes(q.nx, q.ny, nz, sms);
   h->err[0] = 0;
   *out = h;
   return LB_OK;
@@ -676,6 +729,18 @@ int lb_d3_init(lb_d3_handle** out, const lb_params* p, int32_t nz, void* f_a, vo
 int lb_d3_step(lb_d3_handle* h, int64_t nsteps) {
   if (!h) return fail3(nullptr, LB_EINVAL, "null handle");
   if (nsteps < 0) return fail3(h, LB_EINVAL, "nsteps must be >= 0");
+  // Runs of kD3GraphSteps steps replay a graph, unless the caller's stream is being
+  // captured itself (then the steps go into the caller's graph as plain launches).
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (h->stream != nullptr && cudaStreamIsCapturing(h->stream, &capture) != cudaSuccess) {
+    cudaGetLastError();
+    capture = cudaStreamCaptureStatusActive;
+  }
+  while (capture == cudaStreamCaptureStatusNone && nsteps >= kD3GraphSteps && ensure_graph(h)) {
+    const cudaError_t e = cudaGraphLaunch(h->exec[h->cur], h->stream);
+    if (e != cudaSuccess) return fail3(h, LB_ECUDA, "step graph launch: %s", cudaGetErrorString(e));
+    nsteps -= kD3GraphSteps;  // an even number of steps: the state is back in the same buffer
+  }
   for (int64_t k = 0; k < nsteps; ++k) launch_step(h);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail3(h, LB_ECUDA, "step launch: %s", cudaGetErrorString(e));
@@ -734,6 +799,14 @@ int lb_d3_get_params(const lb_d3_handle* h, lb_params* out, lb_derived* derived)
 
 const char* lb_d3_last_error(const lb_d3_handle* h) { return h ? h->err : thread_error(); }
 
-void lb_d3_free(lb_d3_handle* h) { delete h; }
+void lb_d3_free(lb_d3_handle* h) {
+  if (!h) return;
+  for (int c = 0; c < 2; ++c) {
+    if (h->exec[c]) cudaGraphExecDestroy(h->exec[c]);
+    if (h->graph[c]) cudaGraphDestroy(h->graph[c]);
+  }
+  if (h->cstream) cudaStreamDestroy(h->cstream);
+  delete h;
+}
 
 }  // extern "C"

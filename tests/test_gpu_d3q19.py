@@ -360,3 +360,25 @@ def test_coexistence_curve_in_3d(Tr):
     assert prof3[n // 2] == pytest.approx(prof2[n // 2], rel=1e-3)
     assert prof3[n // 2] == pytest.approx(p.rho_l, rel=3e-3)
     assert prof3[0] == pytest.approx(p.rho_g, rel=1e-2 if Tr >= 0.7 else 7e-2)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_graph_replayed_steps_equal_single_launches(precision):
+    """lb_d3_step replays 64-step graphs for long calls (one per starting buffer);
+    130 steps as 1 + 129 (two replays from the odd buffer, one plain step) and as
+    130 single calls give the same bits."""
+    p = _params(Tr=0.85)
+    rho0 = _sphere((20, 9, 35), 4.0, 4.0, p.rho_g, p.rho_l)
+    a = _lattice(rho0, precision, Tr=0.85)
+    b = _lattice(rho0, precision, Tr=0.85)
+    a.step(1)
+    a.step(129)
+    for _ in range(130):
+        b.step(1)
+    torch.cuda.synchronize()
+    assert torch.equal(a.state(), b.state())
+    a.step(64)
+    for _ in range(64):
+        b.step(1)
+    torch.cuda.synchronize()
+    assert torch.equal(a.state(), b.state())
