@@ -46,11 +46,12 @@ NCU_TRAFFIC = {
     # 2048^2 capture (profiles/k_step_tma_dyn_fp32_rows_2048_full.md) scaled x4 to 4096^2.
     ("k_step_tma_dyn<f2>", "rows", "6ce1a8b1aef1d2b0"): 1021228032,
 }
-# The same for the D3Q19 step, keyed by the hash of csrc/lbm3d.cu: the 192^3 capture
-# (profiles/k_d3_step_fp32_192cubed_full.md) scaled by the node count to 256^3.
-KERNEL_SOURCES_D3Q19 = ["paper_1809_02390_gb300/csrc/lbm3d.cu"]
+# The same for the D3Q19 step, keyed by the hash of its step code (csrc/lbm3d_step.cuh):
+# the 192^3 capture (profiles/k_d3_step_fp32_192cubed_full.md) scaled by the node
+# count to 256^3.
+KERNEL_SOURCES_D3Q19 = ["paper_1809_02390_gb300/csrc/lbm3d_step.cuh"]
 NCU_TRAFFIC_D3Q19 = {
-    ("k_d3_step<float, true>", "1349c7a5ea1272ae"): 2512661163,
+    ("k_d3_step<float, true>", "d3e529c5ce8dcc89"): 2512661163,
 }
 
 

@@ -86,6 +86,15 @@ int lb_d3_step(lb_d3_handle* h, int64_t nsteps);
  * post-collision populations).  Asynchronous on the handle's stream. */
 int lb_d3_moments(lb_d3_handle* h, void* rho, void* ux, void* uy, void* uz);
 
+/* FP64 diagnostics of the current state, computed on the device and copied to out
+ * (synchronous): out[0] mass = sum rho, out[1..3] sum_i e_i fbar_i over the lattice
+ * (the total momentum: the interaction forces sum to zero on a periodic lattice),
+ * out[4] nodes with rho above (rho_g + rho_l)/2, out[5] min rho, out[6] max rho,
+ * out[7] nodes whose density is not finite (excluded from 0-6).  Returns
+ * LB_ENONFINITE when out[7] > 0 (out is filled).  Uses a workspace of about 33 KB
+ * that lb_d3_init allocates. */
+int lb_d3_reduce(lb_d3_handle* h, double out[8]);
+
 /* Device buffer holding the current state (f_a or f_b). */
 void* lb_d3_state(const lb_d3_handle* h);
 

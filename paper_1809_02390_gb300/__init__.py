@@ -235,6 +235,12 @@ class Lattice3:
         capi.lb_d3_moments(self.h, rho.data_ptr(), *[t.data_ptr() if t is not None else None for t in u])
         return (rho, *u) if velocity else rho
 
+    def reduce(self) -> dict:
+        """FP64 diagnostics of the current state (lb_d3_reduce)."""
+        v = capi.lb_d3_reduce(self.h)
+        keys = ("mass", "mom_x", "mom_y", "mom_z", "n_liquid", "rho_min", "rho_max")
+        return dict(zip(keys, v))
+
     def close(self) -> None:
         if getattr(self, "h", None):
             capi.lb_d3_free(self.h)

@@ -14,7 +14,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lbm_capi.cu", "lbm_static.cu", "lbm_adjoint.cu", "lbm_batch.cu", "lbm3d.cu", "lbm_thermo.cpp"]
 HEADERS = ["lbm_internal.h", "lbm_device.cuh", "lbm_kernels.cuh", "lbm_handle.cuh", "lbm_adjoint.cuh", "lbm_tma.cuh",
-           "lbm_fields.cuh"]
+           "lbm_fields.cuh", "lbm3d_step.cuh"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(HERE, "..", "include")]
 
 

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("lb_d3_init", ctypes.c_int, [ctypes.POINTER(_V), _P, ctypes.c_int32, _V, _V, _V, ctypes.c_int, _V]),
     ("lb_d3_step", ctypes.c_int, [_V, ctypes.c_int64]),
     ("lb_d3_moments", ctypes.c_int, [_V, _V, _V, _V, _V]),
+    ("lb_d3_reduce", ctypes.c_int, [_V, _D]),
     ("lb_d3_state", _V, [_V]),
     ("lb_d3_get_state", ctypes.c_int, [_V, _V]),
     ("lb_d3_set_state", ctypes.c_int, [_V, _V]),
@@ -422,6 +423,12 @@ def lb_d3_step(h: int, nsteps: int) -> None:
 
 def lb_d3_moments(h: int, rho: int, ux: int | None, uy: int | None, uz: int | None) -> None:
     check_d3(lib().lb_d3_moments(h, rho, ux, uy, uz), h)
+
+
+def lb_d3_reduce(h: int) -> list[float]:
+    out = (ctypes.c_double * 8)()
+    check_d3(lib().lb_d3_reduce(h, out), h)
+    return list(out)
 
 
 def lb_d3_state(h: int) -> int:

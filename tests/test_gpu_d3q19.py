@@ -382,3 +382,30 @@ def test_graph_replayed_steps_equal_single_launches(precision):
         b.step(1)
     torch.cuda.synchronize()
     assert torch.equal(a.state(), b.state())
+
+
+def test_reduce_conserves_mass_and_reports_nonfinite_nodes():
+    """lb_d3_reduce: FP64 mass of a droplet is conserved over 200 steps (FP64 storage:
+    to 1e-13), the momentum sum stays at its start, min / max / liquid count match the
+    moments; a state holding a NaN node gives LB_ENONFINITE with the node counted."""
+    from paper_1809_02390_gb300 import LBError, capi
+
+    p = _params(Tr=0.85)
+    rho0 = _sphere((20, 12, 36), 5.0, 4.0, p.rho_g, p.rho_l)
+    lat = _lattice(rho0, "fp64", Tr=0.85)
+    r0 = lat.reduce()
+    assert r0["mass"] == pytest.approx(rho0.sum(), rel=1e-14)
+    lat.step(200)
+    r1 = lat.reduce()
+    assert r1["mass"] == pytest.approx(r0["mass"], rel=1e-13)
+    for k in ("mom_x", "mom_y", "mom_z"):
+        assert abs(r1[k] - r0[k]) < 1e-10 * r0["mass"]
+    rho = lat.moments(velocity=False).cpu().numpy()
+    assert r1["rho_min"] == rho.min() and r1["rho_max"] == rho.max()
+    assert r1["n_liquid"] == (rho > 0.5 * (p.rho_g + p.rho_l)).sum()
+    f = lat.state().clone()
+    f[3, 7, 5, 11] = float("nan")
+    lat.set_state(f)
+    with pytest.raises(LBError) as ei:
+        lat.reduce()
+    assert ei.value.code == capi.LB_ENONFINITE and "1 nodes" in str(ei.value)
