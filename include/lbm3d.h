@@ -49,7 +49,8 @@ void lb_d3_velocities(int* ex, int* ey, int* ez);
 /* As lb_derive for the D3Q19 model: coexistence densities, lam, G2, c^2, W1 and
  * sigma1 as for D2Q9 (Eqs. 17-22); s_q, s_e from the 3-D closure above when
  * given as <= 0; k, h, b, beta2 the 3-D coefficients; s_eps = 1.75 when <= 0.
- * nx, ny, nz >= 1 and 19 nx ny nz < 2^31 (32-bit offsets).  precision: LB_FP64 or LB_FP32 (FP16
+ * nx, ny, nz >= 1 and nx ny nz < 2^31 (32-bit node indices; population planes
+ * are addressed with 64-bit offsets once 19 nx ny nz reaches 2^31).  precision: LB_FP64 or LB_FP32 (FP16
  * storage: LB_ENOTSUP); layout must be LB_LAYOUT_PLANES; variant LB_AUTO or
  * LB_FUSED; varpi 7/18 (singular b and h) and 1 are rejected. */
 int lb_d3_derive(const lb_params* p, int32_t nz, lb_derived* out);

@@ -45,7 +45,7 @@ __global__ void k_d3_init(const double* __restrict__ rho0, T* __restrict__ f, in
   const double ax = r_ - 11.0 * e_ - 4.0 * p_, ce = r_ + 8.0 * e_ + p_;
   for (int i = 1; i < 7; ++i) o[i] = ax;
   for (int i = 7; i < Q; ++i) o[i] = ce;
-  for (int i = 0; i < Q; ++i) f[i * N + n] = T(o[i]);
+  for (int i = 0; i < Q; ++i) f[size_t(i) * N + n] = T(o[i]);
 }
 
 // rho = sum_i fbar_i + rho_ref into an FP64 array.
@@ -54,7 +54,7 @@ __global__ void k_d3_rho(const T* __restrict__ f, double* __restrict__ rho, int 
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   double a = 0.0;
-  for (int i = 0; i < Q; ++i) a += double(f[i * N + n]);
+  for (int i = 0; i < Q; ++i) a += double(f[size_t(i) * N + n]);
   rho[n] = a + rho_ref;
 }
 
@@ -74,7 +74,7 @@ __global__ void k_d3_vel(const T* __restrict__ f, const double* __restrict__ rho
     s[0] += w * r * cEX[i];
     s[1] += w * r * cEY[i];
     s[2] += w * r * cEZ[i];
-    const double v = double(f[i * N + n]);
+    const double v = double(f[size_t(i) * N + n]);
     j[0] += cEX[i] * v;
     j[1] += cEY[i] * v;
     j[2] += cEZ[i] * v;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_d3_reduce_partial(const T* __restrict__
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
     double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
     for (int i = 0; i < Q; ++i) {
-      const double v = double(f[i * N + n]);
+      const double v = double(f[size_t(i) * N + n]);
       r += v;
       jx += cEX[i] * v;
       jy += cEY[i] * v;
@@ -193,8 +193,8 @@ int derive3(const lb_params* p, int nz, lb_derived* d, char* err, size_t n) {
   };
   if (!p || !d) return bad(LB_EINVAL, "null argument");
   if (p->nx < 1 || p->ny < 1 || nz < 1) return bad(LB_EINVAL, "nx, ny and nz must be >= 1");
-  if (int64_t(Q) * p->nx * p->ny * nz >= (int64_t(1) << 31))
-    return bad(LB_EINVAL, "lattice too large: 19 nx ny nz must be below 2^31");
+  if (int64_t(p->nx) * p->ny * nz >= (int64_t(1) << 31))
+    return bad(LB_EINVAL, "lattice too large: nx ny nz must be below 2^31");
   if (p->precision == LB_FP16S) return bad(LB_ENOTSUP, "the D3Q19 step stores FP64 or FP32 populations");
   if (p->layout != LB_LAYOUT_PLANES) return bad(LB_ENOTSUP, "the D3Q19 step uses the planes layout");
   if (p->variant != LB_AUTO && p->variant != LB_FUSED) return bad(LB_ENOTSUP, "the D3Q19 step is the fused one");
@@ -263,12 +263,25 @@ void launch_step(lb_d3_handle* h) {
   const dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (h->nz + tz - 1) / tz), block(TX, TY);
   const void* in = h->f[h->cur];
   void* out = h->f[1 - h->cur];
-  if (p.precision == LB_FP64)
-    k_d3_step<double, false><<<grid, block, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out),
-                                                            p.nx, p.ny, h->nz, tz, h->c64);
-  else
-    k_d3_step<float, true><<<grid, block, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out),
-                                                          p.nx, p.ny, h->nz, tz, h->c32);
+  // 32-bit plane offsets while 19 nx ny nz < 2^31 (the common case), 64-bit above.
+  const bool wide = int64_t(Q) * p.nx * p.ny * h->nz >= (int64_t(1) << 31);
+  const double* i64 = static_cast<const double*>(in);
+  const float* i32 = static_cast<const float*>(in);
+  if (p.precision == LB_FP64) {
+    if (wide)
+      k_d3_step<double, false, long long><<<grid, block, 0, h->stream>>>(i64, static_cast<double*>(out), p.nx, p.ny,
+                                                                         h->nz, tz, h->c64);
+    else
+      k_d3_step<double, false, int><<<grid, block, 0, h->stream>>>(i64, static_cast<double*>(out), p.nx, p.ny, h->nz,
+                                                                   tz, h->c64);
+  } else {
+    if (wide)
+      k_d3_step<float, true, long long><<<grid, block, 0, h->stream>>>(i32, static_cast<float*>(out), p.nx, p.ny,
+                                                                       h->nz, tz, h->c32);
+    else
+      k_d3_step<float, true, int><<<grid, block, 0, h->stream>>>(i32, static_cast<float*>(out), p.nx, p.ny, h->nz, tz,
+                                                                 h->c32);
+  }
   h->cur = 1 - h->cur;
 }
 

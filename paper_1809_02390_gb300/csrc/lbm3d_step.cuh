@@ -218,9 +218,11 @@ __device__ __forceinline__ void collide3(const C3<T>& c, const T* f, T delta, T 
 }
 
 // Populations arriving at node (x, y, z) (pull streaming): f_i from x - e_i.
-// Neighbour coordinates are precomputed with periodic wrap.
-template <typename T>
-__device__ __forceinline__ void pull19(const T* __restrict__ f, int N, int nx, int ny, int xm, int x, int xp, int ym,
+// Neighbour coordinates are precomputed with periodic wrap.  N: the node count,
+// the stride between population planes, in the type S of the plane offsets (int
+// when 19 N < 2^31, else long long; node indices are int).
+template <typename T, typename S>
+__device__ __forceinline__ void pull19(const T* __restrict__ f, S N, int nx, int ny, int xm, int x, int xp, int ym,
                                        int y, int yp, int zm, int z, int zp, T* v) {
   const int r00 = (z * ny + y) * nx, rm0 = (z * ny + ym) * nx, rp0 = (z * ny + yp) * nx;
   const int r0m = (zm * ny + y) * nx, r0p = (zp * ny + y) * nx;
@@ -264,10 +266,10 @@ __device__ __forceinline__ int inc(int a, int n) { return a == n - 1 ? 0 : a + 1
 
 // Force stencil of node (ly, lx) from the density planes of z - 1 (a), z (b) and
 // z + 1 (e), collision and store of its 19 outputs.
-template <typename T>
+template <typename T, typename S>
 __device__ __forceinline__ void stencil_collide_store(const C3<T>& c, const T (*a)[HX], const T (*b)[HX],
                                                       const T (*e)[HX], int ly, int lx, const T* fc, T* __restrict__ fout,
-                                                      int N, int idx) {
+                                                      S N, int idx) {
   const T sxv = T(1.0 / 6.0) * (b[ly][lx + 1] - b[ly][lx - 1]) +
                 T(1.0 / 12.0) * ((b[ly + 1][lx + 1] - b[ly - 1][lx - 1]) + (b[ly - 1][lx + 1] - b[ly + 1][lx - 1]) +
                                  (e[ly][lx + 1] - a[ly][lx - 1]) + (a[ly][lx + 1] - e[ly][lx - 1]));
@@ -292,14 +294,14 @@ __device__ __forceinline__ void stencil_collide_store(const C3<T>& c, const T (*
 //   plane z + 1 is summed and held, plane z is in fc.
 //   !KEEP (FP64, 4 blocks per SM): plane z + 1 is pulled and summed before the
 //   collision of plane z, whose populations are read again (L1 / L2).
-template <typename T, bool KEEP>
+template <typename T, bool KEEP, typename S>
 __global__ void __launch_bounds__(TX* TY, KEEP ? 3 : 4)
     k_d3_step(const T* __restrict__ fin, T* __restrict__ fout, int nx, int ny, int nz, int tz, C3<T> c) {
   __shared__ T pl[3][HY][HX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * tz;
   const int z1 = min(z0 + tz, nz);
-  const int N = nx * ny * nz;
+  const S N = S(nx) * ny * nz;
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < nx && y < ny;
   const int xg = x % nx, yg = y % ny;

@@ -226,13 +226,13 @@ def test_d3_derived_parameters_match_the_3d_oracle(capi, varpi, s_p):
 @pytest.mark.parametrize("field,value,nz,code,needle", [
     ("precision", 2, 4, "ENOTSUP", "FP64 or FP32"), ("layout", 1, 4, "ENOTSUP", "planes"),
     ("variant", 2, 4, "ENOTSUP", "fused"), ("varpi", 7 / 18, 4, "EINVAL", "7/18"), ("varpi", 1.0, 4, "EINVAL", "varpi"),
-    ("nx", 0, 4, "EINVAL", ">= 1"), ("nx", 40, 0, "EINVAL", ">= 1"), ("nx", 1024, 128, "EINVAL", "too large"),
+    ("nx", 0, 4, "EINVAL", ">= 1"), ("nx", 40, 0, "EINVAL", ">= 1"), ("nx", 2048, 512, "EINVAL", "too large"),
     ("s_p", 2.0, 4, "EINVAL", "s_p"), ("Tr", 1.2, 4, "EINVAL", "coexistence")])
 def test_d3_invalid_parameters_are_rejected(capi, field, value, nz, code, needle):
     p = capi.make_params(40, 20)
     setattr(p, field, value)
-    if field == "nx" and value == 1024:
-        p.ny = 1024
+    if field == "nx" and value == 2048:
+        p.ny = 2048  # 2048^2 x 512 = 2^31 nodes
     with pytest.raises(capi.LBError) as ei:
         capi.lb_d3_derive(p, nz)
     assert ei.value.code == getattr(capi, "LB_" + code) and needle in str(ei.value)

@@ -409,3 +409,43 @@ def test_reduce_conserves_mass_and_reports_nonfinite_nodes():
     with pytest.raises(LBError) as ei:
         lat.reduce()
     assert ei.value.code == capi.LB_ENONFINITE and "1 nodes" in str(ei.value)
+
+
+def test_large_lattice_with_64_bit_plane_offsets(o3):
+    """512^3 FP32 (134 M nodes, 19 nx ny nz > 2^31: the step addresses population
+    planes with 64-bit offsets; 10 GB per buffer): after 3 steps one more is taken and
+    48 sampled nodes, including the last node of the lattice, are recomputed by the
+    oracle's node collision from the stored state (values gathered on the device)."""
+    n = 512
+    p = _params(Tr=0.8, K_int=1.0)
+    rng = np.random.default_rng(4)
+    mean = 0.5 * (p.rho_g + p.rho_l)
+    rho0 = torch.from_numpy(mean * (1 + 0.01 * rng.uniform(-1, 1, (n, n, n)))).cuda()
+    lat = _lattice(rho0, "fp32", Tr=0.8, K_int=1.0)
+    del rho0
+    lat.step(3)
+    before = lat.state().clone()
+    lat.step(1)
+    after = lat.state()
+    e = [tuple(v) for v in lat.velocities]
+    w = np.array([1 / 3 if sum(c * c for c in v) == 0 else (1 / 18 if sum(c * c for c in v) == 1 else 1 / 36) for v in e])
+    perm = _perm(o3)
+    inv = np.argsort(perm)
+    picks = [(n - 1, n - 1, n - 1), (0, 0, 0), (n - 1, 0, 255), (300, 17, 511)]
+    picks += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(44)]
+    # every node whose pulled populations are needed: the pick and its 18 neighbours
+    nodes = [(z + c[2], y + c[1], x + c[0]) for (z, y, x) in picks for c in e]
+    idx = [(i, (zz - e[i][2]) % n, (yy - e[i][1]) % n, (xx - e[i][0]) % n) for (zz, yy, xx) in nodes for i in range(19)]
+    ii, zi, yi, xi = [torch.tensor(col, device="cuda") for col in zip(*idx)]
+    vals = before[ii, zi, yi, xi].double().cpu().numpy().reshape(len(picks), 19, 19) + lat.rho_ref * w[None, None, :]
+    pz, py, px = [torch.tensor(col, device="cuda") for col in zip(*picks)]
+    got = after[:, pz, py, px].cpu().numpy().T
+    scale = float(after.abs().max()) + lat.rho_ref / 3
+    for k, (z, y, x) in enumerate(picks):
+        g = vals[k, 0]  # the pick itself is the rest-velocity entry (c = 0) of its list
+        s = np.zeros(3)
+        for j in range(1, 19):
+            wt = 1 / 6 if sum(c * c for c in e[j]) == 1 else 1 / 12
+            s += wt * vals[k, j].sum() * np.array(e[j], dtype=float)
+        out = o3.collide_node(p, g[inv], s)[perm] - w * lat.rho_ref
+        assert np.abs(got[k] - out).max() <= 2e-5 * scale, (z, y, x)
