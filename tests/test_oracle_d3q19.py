@@ -378,3 +378,22 @@ def test_laplace_law_of_a_liquid_column(o3, orc):
         out.append(dp * radius / (sigma * p.lam))
     assert out[0] == pytest.approx(1.0, rel=4e-2)
     assert out[0] == pytest.approx(out[1], rel=5e-3)
+
+
+def test_carnahan_starling_interface_at_the_papers_setting(o3, orc):
+    """The paper's EOS and setting of supplement Fig. 2 (Carnahan-Starling, a = 1,
+    b = 4, Tr = 0.8, K_INT = 2.2949, so W = 10): a flat 3-D interface has the Maxwell
+    densities and the pressure-tensor thickness (measured: gas -0.03%, liquid +0.14%,
+    W +1.0%), and the same densities as the D2Q9 oracle on the same slab."""
+    Tr, K, L = 0.8, 2.2949, 160
+    e = thermo.make_eos("cs", 1.0, 4.0, 1.0, Tr)
+    W = thermo.interface(e, K)["W"]
+    p3 = op.from_physical_3d(eos="cs", a=1.0, b=4.0, Tr=Tr, K_int=K)
+    p2 = op.from_physical(eos="cs", a=1.0, b=4.0, Tr=Tr, K_int=K)
+    slab = inputs.slab(L, 2, L // 2, W, p3.rho_g, p3.rho_l)
+    r3 = o3.macro(p3, o3.step(p3, o3.init_eq(p3, slab[0][None, None, :]), 10000))[0][0, 0]
+    r2 = orc.macro(p2, orc.step(p2, orc.init_feq(p2, slab), 10000))[0][0]
+    assert r3[0] == pytest.approx(p3.rho_g, rel=3e-3)
+    assert r3[L // 2] == pytest.approx(p3.rho_l, rel=3e-3)
+    assert _thickness(r3[: L // 2], r3[0], r3[L // 2]) == pytest.approx(W, rel=2e-2)
+    assert r3[0] == pytest.approx(r2[0], rel=3e-3) and r3[L // 2] == pytest.approx(r2[L // 2], rel=1e-3)
