@@ -50,9 +50,10 @@ void lb_d3_velocities(int* ex, int* ey, int* ez);
  * sigma1 as for D2Q9 (Eqs. 17-22); s_q, s_e from the 3-D closure above when
  * given as <= 0; k, h, b, beta2 the 3-D coefficients; s_eps = 1.75 when <= 0.
  * nx, ny, nz >= 1 and nx ny nz < 2^31 (32-bit node indices; population planes
- * are addressed with 64-bit offsets once 19 nx ny nz reaches 2^31).  precision: LB_FP64 or LB_FP32 (FP16
- * storage: LB_ENOTSUP); layout must be LB_LAYOUT_PLANES; variant LB_AUTO or
- * LB_FUSED; varpi 7/18 (singular b and h) and 1 are rejected. */
+ * are addressed with 64-bit offsets once 19 nx ny nz reaches 2^31).  precision:
+ * LB_FP64 or LB_FP32 (FP16 storage: LB_ENOTSUP); layout must be
+ * LB_LAYOUT_PLANES; variant LB_AUTO or LB_FUSED; varpi 7/18 (singular b and h)
+ * and 1 are rejected. */
 int lb_d3_derive(const lb_params* p, int32_t nz, lb_derived* out);
 
 /* Bytes of one population buffer: 19 nx ny nz times the element size. */
@@ -66,7 +67,9 @@ size_t lb_d3_state_bytes(const lb_params* p, int32_t nz);
  * (rho0_on_device = 0; copied through f_b) or the device (1).  rho_ref = NaN takes
  * the mean of rho0 (computed in FP64).  Densities that are not positive and
  * finite, or for vdW not below 1/b, are reported as LB_EINVAL (checked on the
- * device; the handle is not created).  Synchronous. */
+ * device; the handle is not created).  The handle owns a 33 KB device workspace
+ * for lb_d3_reduce (LB_ENOMEM if it cannot be allocated), its graphs and a
+ * private capture stream, all released by lb_d3_free.  Synchronous. */
 int lb_d3_init(lb_d3_handle** out, const lb_params* p, int32_t nz, void* f_a, void* f_b, const double* rho0,
                int rho0_on_device, void* stream);
 
@@ -76,8 +79,7 @@ int lb_d3_init(lb_d3_handle** out, const lb_params* p, int32_t nz, void* f_a, vo
  * being captured into the caller's own graph, are plain launches; the results are
  * the same bits either way.  Each step is the fused kernel: pull streaming,
  * density with its one-node ring, force stencil (Eq. 12 with omega = 1/6 on the
- * axes, 1/12 on the edges),
- * velocity (Eq. 5), EOS, equilibrium, forcing, Q_m, collision (Eq. 13 without R,
+ * axes, 1/12 on the edges), velocity (Eq. 5), EOS, equilibrium, forcing, Q_m, collision (Eq. 13 without R,
  * T, X) and store. */
 int lb_d3_step(lb_d3_handle* h, int64_t nsteps);
 
