@@ -79,8 +79,8 @@ int lb_d3_init(lb_d3_handle** out, const lb_params* p, int32_t nz, void* f_a, vo
  * being captured into the caller's own graph, are plain launches; the results are
  * the same bits either way.  Each step is the fused kernel: pull streaming,
  * density with its one-node ring, force stencil (Eq. 12 with omega = 1/6 on the
- * axes, 1/12 on the edges), velocity (Eq. 5), EOS, equilibrium, forcing, Q_m, collision (Eq. 13 without R,
- * T, X) and store. */
+ * axes, 1/12 on the edges), velocity (Eq. 5), EOS, equilibrium, forcing, Q_m,
+ * collision (Eq. 13 without R, T, X) and store. */
 int lb_d3_step(lb_d3_handle* h, int64_t nsteps);
 
 /* rho (required) and the velocity components (each may be NULL) of the current
