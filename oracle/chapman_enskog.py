@@ -222,11 +222,15 @@ def d3q19_ns(varpi, k, h, b, beta2):
 
 # --- steady third order -----------------------------------------------------------------
 
-def steady_eta_residual(D, E, rows, meq0, fm0, S, order=3):
+def steady_eta_residual(D, E, rows, meq0, fm0, S, order=3, q_rows=()):
     """Momentum residual of a steady state at u = 0 through third order in the
     gradients, with F replaced by grad p_LBE (p_LBE = c_s^2 (rho + eta)) in the
     third-order terms, minus the lattice term -(1/12) c_s^2 lap grad(rho + eta).
-    Returns the list of its eta parts (one per component) and of its rho parts."""
+    Returns the list of its eta parts (one per component) and of its rho parts.
+    q_rows: moments that carry an independent second-order term Q_r of the collision's
+    + S Q_m (symbol 'Q_<row>'); with them a third list holds the part linear in the
+    Q symbols, and a fourth the divergence of the second-order tensor of Q_m,
+    div Pi(M^-1 Q), for comparison."""
     lam = sp.Symbol("lam")
     n = len(E)
     d = sp.symbols("dx dy dz")[:D]
@@ -252,26 +256,36 @@ def steady_eta_residual(D, E, rows, meq0, fm0, S, order=3):
         G[names.index(j)] = -lam * F[a] / 2
     Snn_inv = S.extract(noncons, noncons).inv()
     half = (sp.eye(n) - S / 2) * fm
+    Qsym = {r: sp.Symbol("Q_" + r) for r in q_rows}
+    Qm = sp.Matrix([lam ** 2 * Qsym[nm] if nm in Qsym else 0 for nm in names])
+    SQ = S * Qm
     for _ in range(order + 1):
         fpop = Minv * (meq + G)
         mD = M * sp.Matrix([trunc(shift[i] * fpop[i]) for i in range(n)])
-        Gn = Snn_inv * sp.Matrix([-mD[i] + half[i] for i in noncons])
+        Gn = Snn_inv * sp.Matrix([-mD[i] + half[i] + SQ[i] for i in noncons])
         for k, i in enumerate(noncons):
             G[i] = trunc(Gn[k])
     fpop = Minv * (meq + G)
     mD = M * sp.Matrix([trunc(shift[i] * fpop[i]) for i in range(n)])
     p0 = CS2 * (rho + eta)
     lap = sum(x * x for x in d)
-    eta_parts, rho_parts = [], []
+    eta_parts, rho_parts, q_parts, q_div = [], [], [], []
+    qv = Minv * sp.Matrix([Qsym[nm] if nm in Qsym else 0 for nm in names])  # M^-1 Q in velocity space
+    Pi_Q = [[sum(E[i][a] * E[i][b] * qv[i] for i in range(n)) for b in range(D)] for a in range(D)]
     for a, j in enumerate(js):
         r3 = sp.expand(mD[names.index(j)]).coeff(lam, 3)
         canon = sp.expand(r3.subs({F[b]: d[b] * p0 for b in range(D)}) + sp.Rational(1, 12) * lap * d[a] * p0)
         eta_parts.append(sp.factor(canon.coeff(eta)))
         rho_parts.append(sp.factor(canon.coeff(rho)))
+        if Qsym:
+            q_parts.append(sp.expand(sum(canon.coeff(q) * q for q in Qsym.values())))
+            q_div.append(sp.expand(sum(d[b] * Pi_Q[a][b] for b in range(D))))
+    if Qsym:
+        return eta_parts, rho_parts, d, q_parts, q_div
     return eta_parts, rho_parts, d
 
 
-def d2q9_steady(varpi, se, seps, sq, sp_):
+def d2q9_steady(varpi, se, seps, sq, sp_, q_rows=()):
     D, E, rows, W = d2q9()
     k = 1 - varpi
     beta2 = -2 / (1 - varpi)
@@ -279,10 +293,10 @@ def d2q9_steady(varpi, se, seps, sq, sp_):
     S[1, 2] = k * seps * (se / 2 - 1)
     meq0 = lambda rho, eta: [rho, -2 * rho + 2 * eta, rho + beta2 * eta, 0, 0, 0, 0, 0, 0]
     fm0 = lambda F: [0, 0, 0, F[0], -F[0], F[1], -F[1], 0, 0]
-    return steady_eta_residual(D, E, rows, meq0, fm0, S)
+    return steady_eta_residual(D, E, rows, meq0, fm0, S, q_rows=q_rows)
 
 
-def d3q19_steady(k, se, seps, sq, sp_, sm, spi):
+def d3q19_steady(k, se, seps, sq, sp_, sm, spi, q_rows=()):
     D, E, rows, W = d3q19()
     names = [nm for nm, _ in rows]
     beta2 = -19 / k
@@ -304,4 +318,4 @@ def d3q19_steady(k, se, seps, sq, sp_, sm, spi):
             m[names.index(q)] = -sp.Rational(2, 3) * F[a]
         return m
 
-    return steady_eta_residual(D, E, rows, meq0, fm0, S)
+    return steady_eta_residual(D, E, rows, meq0, fm0, S, q_rows=q_rows)

@@ -78,3 +78,24 @@ def test_d3q19_rate_closure_removes_the_steady_eta_terms(kind):
     eta_parts, rho_parts, _ = ce.d3q19_steady(k, se, sp.Rational(7, 4), sq, sp_, sp.Rational(13, 10), sp.Rational(7, 4))
     assert all(r == 0 for r in rho_parts)
     assert all(e == 0 for e in eta_parts) == (kind is None)
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19"])
+def test_q_m_enters_the_steady_balance_through_its_second_order_tensor(lattice):
+    """At third order the term S Q_m (Eq. 13) adds div Pi(M^-1 Q_m) to the steady
+    momentum balance and nothing else, whatever its fourth-order components are:
+    the paper's R_add is -div of (2 F~F~ + |F~|^2 I)/24, the second-order tensor of
+    its Q_m, and a 3-D Q_m with that tensor gives the same pressure tensor (the
+    reading of the 3-D Q_m)."""
+    if lattice == "d2q9":
+        w = sp.Rational(1, 6)
+        res = ce.d2q9_steady(w, sp.Rational(22, 17), sp.Rational(3, 2), sp.Rational(3, 2), sp.Integer(1),
+                             q_rows=("e", "eps", "pxx", "pxy"))
+    else:
+        k, se, sq, sp_ = _rates(None)
+        res = ce.d3q19_steady(k, se, sp.Rational(7, 4), sq, sp_, sp.Rational(13, 10), sp.Rational(7, 4),
+                              q_rows=("e", "eps", "pxx3", "pww", "pxy", "pyz", "pxz", "pixx3", "piww"))
+    _, _, _, q_parts, q_div = res
+    for qp, qd in zip(q_parts, q_div):
+        assert sp.simplify(qp - qd) == 0
+        assert qd != 0
